@@ -1,0 +1,195 @@
+/*
+ * geomatch.h -- C ABI of the GB300 geometry-aware pairwise feature matcher.
+ *
+ * The library implements the guided matching of Shah, Deshpande and Narayanan, "Multistage SFM: A Coarse-to-Fine
+ * Approach for 3D Reconstruction" (arXiv 1512.06235), Sec. 6.2 with the GPU steps of Appendix A:
+ *
+ *   for each image pair (A, B) with fundamental matrix F and band half-width d, and for every feature i of A,
+ *     l   = F (x_i, y_i, 1)^T                              epipolar line of i in B            (Sec. 6.2)
+ *     C_i = { j in B : |a x_j + b y_j + c| <= d sqrt(a^2+b^2) }   candidate set               (Eqs. 2-3)
+ *     D   = sum_k (A_ik - B_jk)^2 for j in C_i             exact squared L2 over 128 bytes   (Sec. 6.2.2)
+ *     (D1, j1), D2 = nearest and second-nearest over C_i                                      (App. A Step 4)
+ *     match (i, j1) iff |C_i| >= 2 and q^2 D1 < p^2 D2     ratio test with r = p/q             (Sec. 2.3)
+ *
+ * Image B's features are binned into a uniform grid (App. A Step 1); each band is walked cell by cell and every
+ * visited point gets an exact membership decision (FP32 with a proven error margin, FP64 for points inside the
+ * margin), so C_i is exactly the set of Eq. 2 -- not the approximate set C' of the paper's overlapping grids.
+ * Results are bit-identical to a plain FP64 evaluation of the definition above.
+ *
+ * Conventions for every entry point
+ *   - Every function returns a gm_status; nothing throws across the ABI.  gm_last_error() gives the message of
+ *     the last failing call on the calling thread.
+ *   - Input arrays are borrowed for the duration of the call only; the context copies what it keeps.
+ *   - Output arrays are owned by the caller.  An output pointer may be host memory or device memory of the
+ *     context's device; the library detects which.
+ *   - Keypoint and match indices are the caller's original per-image indices (0-based).
+ *   - One context is bound to one CUDA device and one CUDA stream; calls on one context must not overlap
+ *     (except gm_submit / gm_poll, which are thread-safe).
+ */
+#ifndef GEOMATCH_H
+#define GEOMATCH_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GM_API __attribute__((visibility("default")))
+#else
+#define GM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gm_ctx gm_ctx;   /* opaque; owns device state (resident images, workspace, streams) */
+
+typedef enum {
+    GM_OK = 0,
+    GM_ERR_INVALID = -1,    /* a malformed argument (null pointer, out-of-image keypoint, bad ratio, ...) */
+    GM_ERR_NOMEM = -2,      /* an allocation failed, or a caller-provided output is too small */
+    GM_ERR_BUDGET = -3,     /* the request does not fit the configured device-memory budget */
+    GM_ERR_NOT_FOUND = -4,  /* unknown image id or ticket */
+    GM_ERR_CUDA = -5,       /* a CUDA runtime error; the message names the call */
+    GM_ERR_TIMEOUT = -6,    /* a bounded wait ran out (host poll or a device-side spin) */
+    GM_ERR_CANCELLED = -7,  /* the request was cancelled, or the context shut down before it ran */
+    GM_ERR_BUSY = -8        /* the serving queue is full */
+} gm_status;
+
+/* Distance paths (option GM_OPT_PATH).  All give identical results. */
+enum {
+    GM_PATH_AUTO = 0,       /* chosen per pair from the band density (autotuned thresholds) */
+    GM_PATH_TC = 1,         /* tcgen05.mma kind::f16 tiles, integer-valued operands, f32 accumulation (exact) */
+    GM_PATH_MMA = 2,        /* mma.sync m16n8k32 s8 x s8 -> s32 query groups */
+    GM_PATH_SIMT = 3        /* one warp per query, dp4a on recentred int8 descriptors */
+};
+
+/* Options for gm_set_option. */
+enum {
+    GM_OPT_PATH = 1,        /* GM_PATH_* */
+    GM_OPT_SCHEDULE = 2,    /* 0 = whole batch per launch (default), 1 = one pair per launch (plain form) */
+    GM_OPT_CELL_PX = 3,     /* grid cell size of images put afterwards: 8, 16, 32, 64 or 128 px (default 16) */
+    GM_OPT_GRAPH = 4        /* 1 = replay batches through a captured CUDA graph when the shape repeats */
+};
+
+typedef struct {
+    int32_t device;              /* CUDA device ordinal */
+    uint64_t mem_budget_bytes;   /* device bytes the context may hold (images + workspace); 0 = no limit */
+    int32_t max_inflight;        /* serving: batches that may be on the device at once (>= 1; 0 = 2) */
+    void *cuda_stream;           /* cudaStream_t for synchronous calls, or NULL for the context's own stream */
+    int32_t path;                /* GM_PATH_* */
+    int32_t cell_px;             /* grid cell size in px (power of two, 8..128); 0 = 16 */
+    const char *tuner_cache;     /* reserved (may be NULL) */
+} gm_config;
+
+typedef struct {
+    int32_t img_a;               /* query image id */
+    int32_t img_b;               /* target image id */
+    float F[9];                  /* row-major; the epipolar line of (x_A, y_A) in B is F (x_A, y_A, 1)^T */
+    float band_px;               /* d >= 0: max point-to-line distance in px (half the band width);
+                                    +INFINITY = the whole image (exhaustive matching) */
+    uint16_t ratio_num;          /* p; the ratio test accepts iff dist1 / dist2 < p / q */
+    uint16_t ratio_den;          /* q; requires 0 <= p < q */
+} gm_pair;
+
+typedef struct {
+    int64_t n_pairs;             /* pairs in the last gm_match_pairs call */
+    int64_t n_queries;           /* sum of |A| over those pairs */
+    int64_t n_candidates;        /* sum_i |C_i|: exact candidate comparisons (Eq. 2 set sizes) */
+    int64_t n_examined;          /* points visited by the cell walk (a superset of the candidates) */
+    int64_t n_redecided;         /* points whose band decision was re-taken in FP64 */
+    int64_t n_matches;           /* matches written */
+    float ms_device;             /* device time of the whole call (CUDA events on the context stream) */
+    float ms_match;              /* device time of the band-walk / distance / top-2 kernel(s) */
+    int32_t path_used;           /* GM_PATH_* of the distance kernel that ran */
+    int32_t kernel_launches;     /* kernels launched by the call */
+} gm_stats;
+
+/* Creates a context on cfg->device.  *out receives the handle.  Errors: GM_ERR_INVALID (null pointer, bad
+ * option value), GM_ERR_CUDA (device unavailable). */
+GM_API gm_status gm_create(const gm_config *cfg, gm_ctx **out);
+
+/* Frees every device and host resource of the context; pending serving requests end with GM_ERR_CANCELLED. */
+GM_API gm_status gm_destroy(gm_ctx *ctx);
+
+/* Sets a tuning option (GM_OPT_*).  GM_ERR_INVALID for an unknown key or value. */
+GM_API gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value);
+
+/* Registers image `image_id` (>= 0) and makes it resident on the device (App. A Step 1: the keypoints are binned
+ * into grid cells once per image, sorted by cell, and the descriptors are stored in cell order, recentred to int8
+ * b - 128, with their squared norms).  Replaces an image already registered under that id.
+ *   xy:    float32 [n][2] keypoint coordinates (x, y) in px; every keypoint must satisfy 0 <= x < width and
+ *          0 <= y < height (otherwise GM_ERR_INVALID);
+ *   scale: float32 [n] keypoint scales (stored, not used by the matching; may be NULL);
+ *   desc:  uint8 [n][128] SIFT descriptors, row-major;
+ *   on_device: 0 = the three pointers are host memory, 1 = device memory of the context's device.
+ * n may be 0.  Errors: GM_ERR_INVALID, GM_ERR_BUDGET (the resident image would exceed the budget),
+ * GM_ERR_NOMEM, GM_ERR_CUDA. */
+GM_API gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t height, int32_t n,
+                       const float *xy, const float *scale, const uint8_t *desc, int32_t on_device);
+
+/* Drops image `image_id` from the context.  GM_ERR_NOT_FOUND if unknown. */
+GM_API gm_status gm_image_evict(gm_ctx *ctx, int32_t image_id);
+
+/* Matches n_pairs pairs in one batch (Sec. 6.2; App. A Steps 2-4 for all pairs at once) and writes, in the pairs'
+ * order, the match list of every pair sorted by the query index i:
+ *   pair_off: int64 [n_pairs + 1]; the matches of pair k are rows pair_off[k] .. pair_off[k+1]-1;
+ *   matches:  int32 [cap][2] rows (i_A, j_B) of original keypoint indices;
+ *   *n_written: the total number of matches.  If it exceeds cap, nothing is written to `matches`, pair_off is
+ *               still written, and the call returns GM_ERR_NOMEM (call again with cap >= *n_written).
+ * Both images of every pair must have been put (GM_ERR_NOT_FOUND otherwise); F must be finite, band_px >= 0 or
+ * +INFINITY, and 0 <= ratio_num < ratio_den (GM_ERR_INVALID otherwise).  With n_pairs == 0 only pair_off[0]=0
+ * and *n_written=0 are written.  The call returns when the outputs are complete. */
+GM_API gm_status gm_match_pairs(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int64_t *pair_off,
+                         int32_t *matches, int64_t cap, int64_t *n_written);
+
+/* Candidate sets C_i of one pair (App. A Step 3 output, exact Eq. 2 sets) for queries i in
+ * [query_begin, query_begin + query_count) of image A (original indices):
+ *   cand_off: int64 [query_count + 1] offsets into cand;
+ *   cand:     int32 [cap] B indices (original), ascending within each query;
+ *   *n_written: total candidates.  GM_ERR_NOMEM if it exceeds cap (cand_off still written). */
+GM_API gm_status gm_band_candidates(gm_ctx *ctx, const gm_pair *pair, int32_t query_begin, int32_t query_count,
+                             int64_t *cand_off, int32_t *cand, int64_t cap, int64_t *n_written);
+
+/* Counters and device timings of the last gm_match_pairs call on this context. */
+GM_API gm_status gm_get_stats(const gm_ctx *ctx, gm_stats *out);
+
+/* ---- serving: continuous batching ------------------------------------------------------------------------
+ * gm_submit queues one pair-match request and returns at once with a ticket.  A scheduler thread admits queued
+ * requests into device batches while the device-memory budget and the in-flight batch slots allow, so requests
+ * that arrive while other batches run on the GPU join the next batch and overlap with the running ones.  The
+ * result of a request is identical to what gm_match_pairs gives for that pair alone.  Thread-safe. */
+GM_API gm_status gm_submit(gm_ctx *ctx, const gm_pair *pair, uint64_t *ticket);
+
+/* Waits up to timeout_ms (0 = do not wait, < 0 = wait without limit) for request `ticket`, then writes its
+ * matches (int32 [cap][2] rows (i_A, j_B), sorted by i) and *n.  Returns GM_ERR_TIMEOUT if the request is not
+ * done yet (the ticket stays valid), GM_ERR_NOMEM if cap < *n (the ticket stays valid), GM_ERR_NOT_FOUND for an
+ * unknown or already collected ticket, or the request's own error.  A collected ticket is released.
+ * If latency_us is not NULL it receives the request's submit-to-completion time in microseconds. */
+GM_API gm_status gm_poll(gm_ctx *ctx, uint64_t ticket, int32_t *matches, int64_t cap, int64_t *n, int32_t timeout_ms,
+                  double *latency_us);
+
+typedef struct {
+    int64_t submitted;               /* requests accepted by gm_submit */
+    int64_t completed;               /* requests finished successfully */
+    int64_t failed;                  /* requests finished with an error */
+    int64_t batches;                 /* device batches launched */
+    int64_t max_batch_pairs;         /* largest batch, in requests */
+    int64_t peak_inflight_batches;   /* most batches on the device at the same time */
+    int64_t rejected_budget;         /* gm_submit refusals: larger than a batch slot's share of the budget */
+    int64_t rejected_busy;           /* gm_submit refusals: queue full */
+} gm_serving_stats;
+
+/* Counters of the serving loop (all zero before the first gm_submit). */
+GM_API gm_status gm_get_serving_stats(gm_ctx *ctx, gm_serving_stats *out);
+
+/* Blocks until every submitted request has completed (the results stay available to gm_poll). */
+GM_API gm_status gm_serving_drain(gm_ctx *ctx);
+
+/* Message of the last failing call made by this thread (never NULL). */
+GM_API const char *gm_last_error(const gm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEOMATCH_H */

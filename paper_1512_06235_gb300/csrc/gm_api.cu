@@ -1,0 +1,683 @@
+// gm_api.cu -- host side of libgeomatch: the C ABI declared in include/geomatch.h.
+//
+// A context owns one CUDA stream, the resident images (binned once, App. A Step 1) and a grow-only workspace.
+// gm_match_pairs runs a whole batch of pairs with a fixed number of launches, independent of the number of
+// pairs (Sec. 6.2.3: pairs are independent; App. A Steps 2-4 for all pairs at once):
+//   H2D pair table -> order kernel (one block per pair) -> match kernel (all pairs' queries) -> count + scan ->
+//   write -> D2H of the offsets -> copy of the match rows.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gm_ctx.h"
+
+using namespace gm;
+
+namespace gm {
+namespace {
+thread_local std::string g_err = "";
+}  // namespace
+
+gm_status fail(gm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+const char *last_error() { return g_err.c_str(); }
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+#define GM_CUDA(call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return gm::fail(GM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+gm_status ensure_dev(gm_ctx *ctx, DevBuf &b, size_t bytes)
+{
+    if (b.bytes >= bytes) return GM_OK;
+    size_t nb = align_up(std::max({bytes, b.bytes + b.bytes / 2, (size_t)256}), 256);
+    const size_t others = ctx->bytes_images + ctx->bytes_work - b.bytes;
+    if (ctx->budget && others + nb > ctx->budget) {
+        nb = align_up(bytes, 256);
+        if (others + nb > ctx->budget)
+            return fail(GM_ERR_BUDGET, "workspace of %zu bytes exceeds the device-memory budget", nb);
+    }
+    free_dev(ctx, b);
+    if (cudaMalloc(&b.p, nb) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(GM_ERR_NOMEM, "cudaMalloc of %zu bytes failed", nb);
+    }
+    b.bytes = nb;
+    ctx->bytes_work += nb;
+    return GM_OK;
+}
+
+gm_status ensure_host(HostBuf &b, size_t bytes, bool mapped)
+{
+    if (b.bytes >= bytes && b.mapped == mapped) return GM_OK;
+    const size_t nb = align_up(std::max(bytes, b.bytes + b.bytes / 2), 4096);
+    free_host(b);
+    if (cudaHostAlloc(&b.p, nb, mapped ? cudaHostAllocMapped : cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(GM_ERR_NOMEM, "cudaHostAlloc of %zu bytes failed", nb);
+    }
+    b.bytes = nb;
+    b.mapped = mapped;
+    return GM_OK;
+}
+
+void free_dev(gm_ctx *ctx, DevBuf &b)
+{
+    if (b.p) {
+        cudaFree(b.p);
+        ctx->bytes_work -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+void free_host(HostBuf &b)
+{
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+gm_status workspace_init(Workspace &ws, cudaStream_t stream)
+{
+    if (stream) {
+        ws.stream = stream;
+        ws.own_stream = false;
+    } else {
+        GM_CUDA(cudaStreamCreateWithFlags(&ws.stream, cudaStreamNonBlocking));
+        ws.own_stream = true;
+    }
+    for (auto &e : ws.ev) GM_CUDA(cudaEventCreate(&e));
+    return GM_OK;
+}
+
+void workspace_free(gm_ctx *ctx, Workspace &ws)
+{
+    if (ws.stream) cudaStreamSynchronize(ws.stream);
+    for (DevBuf *b : {&ws.d_tab, &ws.d_qorder, &ws.d_matchj, &ws.d_counts, &ws.d_off, &ws.d_rows, &ws.d_ctr, &ws.d_next})
+        free_dev(ctx, *b);
+    for (HostBuf *b : {&ws.h_tab, &ws.h_off, &ws.h_rows}) free_host(*b);
+    if (ws.gexec) cudaGraphExecDestroy(ws.gexec);
+    ws.gexec = nullptr;
+    for (auto &e : ws.ev)
+        if (e) cudaEventDestroy(e);
+    if (ws.own_stream && ws.stream) cudaStreamDestroy(ws.stream);
+    ws.stream = nullptr;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Validates one pair and fills its device record (without qoff).
+gm_status prepare_pair(gm_ctx *ctx, const gm_pair &pr, int64_t k, PairDev &pd)
+{
+    auto ia = ctx->images.find(pr.img_a), ib = ctx->images.find(pr.img_b);
+    if (ia == ctx->images.end() || ib == ctx->images.end())
+        return fail(GM_ERR_NOT_FOUND, "pair %lld: image %d not registered", (long long)k,
+                    ia == ctx->images.end() ? pr.img_a : pr.img_b);
+    for (int t = 0; t < 9; ++t)
+        if (!std::isfinite(pr.F[t])) return fail(GM_ERR_INVALID, "pair %lld: F is not finite", (long long)k);
+    if (std::isnan(pr.band_px) || pr.band_px < 0.0f)
+        return fail(GM_ERR_INVALID, "pair %lld: band_px must be >= 0 or +inf", (long long)k);
+    if (pr.ratio_den == 0 || pr.ratio_num >= pr.ratio_den)
+        return fail(GM_ERR_INVALID, "pair %lld: ratio must satisfy 0 <= p < q", (long long)k);
+    pd.a = ia->second->slot;
+    pd.b = ib->second->slot;
+    std::memcpy(pd.F, pr.F, sizeof(pd.F));
+    pd.d = pr.band_px;
+    pd.p = pr.ratio_num;
+    pd.q = pr.ratio_den;
+    pd.n_a = ia->second->dev.n;
+    pd.flags = 0;
+    pd.qoff = 0;
+    return GM_OK;
+}
+
+gm_status engine_plan(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs)
+{
+    ws.pd.resize(n_pairs);
+    ws.n_pairs = n_pairs;
+    ws.Q = 0;
+    ws.nitems = 0;
+    for (int32_t k = 0; k < n_pairs; ++k) {
+        gm_status st = prepare_pair(ctx, pairs[k], k, ws.pd[k]);
+        if (st != GM_OK) return st;
+        ws.pd[k].qoff = ws.Q;
+        ws.Q += ws.pd[k].n_a;
+        ws.nitems += (ws.pd[k].n_a + kQueriesPerItem - 1) / kQueriesPerItem;
+    }
+    if (ws.nitems > INT32_MAX / 2 || ws.Q > INT32_MAX / 2) return fail(GM_ERR_INVALID, "batch too large");
+    return GM_OK;
+}
+
+gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
+{
+    const int32_t P = ws.n_pairs;
+    const int64_t Q = ws.Q;
+    const size_t pair_bytes = align_up(sizeof(PairDev) * std::max(P, 1), 256);
+    const size_t tab_bytes = pair_bytes + sizeof(int64_t) * (P + 1);
+    gm_status st;
+    if ((st = ensure_dev(ctx, ws.d_tab, tab_bytes)) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ws.d_qorder, sizeof(int32_t) * std::max<int64_t>(Q, 1))) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ws.d_matchj, sizeof(int32_t) * std::max<int64_t>(Q, 1))) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ws.d_counts, sizeof(int32_t) * std::max(P, 1))) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ws.d_off, sizeof(int64_t) * (P + 1))) != GM_OK) return st;
+    if (!rows_dst && (st = ensure_dev(ctx, ws.d_rows, sizeof(int32_t) * 2 * std::max<int64_t>(Q, 1))) != GM_OK)
+        return st;
+    if ((st = ensure_dev(ctx, ws.d_ctr, sizeof(BatchCounters) * 64 + 256)) != GM_OK) return st;
+    if ((st = ensure_host(ws.h_tab, tab_bytes)) != GM_OK) return st;
+    if ((st = ensure_host(ws.h_off, sizeof(int64_t) * (P + 1) + sizeof(BatchCounters) * 64)) != GM_OK) return st;
+
+    char *hs = static_cast<char *>(ws.h_tab.p);
+    std::memcpy(hs, ws.pd.data(), sizeof(PairDev) * P);
+    int64_t *h_item_off = reinterpret_cast<int64_t *>(hs + pair_bytes);
+    h_item_off[0] = 0;
+    for (int32_t k = 0; k < P; ++k)
+        h_item_off[k + 1] = h_item_off[k] + (ws.pd[k].n_a + kQueriesPerItem - 1) / kQueriesPerItem;
+
+    char *ds = static_cast<char *>(ws.d_tab.p);
+    const PairDev *d_pairs = reinterpret_cast<const PairDev *>(ds);
+    const int64_t *d_item_off = reinterpret_cast<const int64_t *>(ds + pair_bytes);
+    int32_t *qorder = static_cast<int32_t *>(ws.d_qorder.p);
+    int32_t *match_j = static_cast<int32_t *>(ws.d_matchj.p);
+    BatchCounters *ctr = static_cast<BatchCounters *>(ws.d_ctr.p);
+    int32_t *next = reinterpret_cast<int32_t *>(ctr + 64);
+    const ImageDev *imgs = static_cast<const ImageDev *>(ctx->d_imgs.p);
+    int64_t *d_off = static_cast<int64_t *>(ws.d_off.p);
+    int32_t *rows = rows_dst ? rows_dst : static_cast<int32_t *>(ws.d_rows.p);
+    cudaStream_t s = ws.stream;
+    if (ctx->num_sms <= 0) ctx->num_sms = 1;
+    const int32_t grid = ctx->num_sms * match_simt_blocks_per_sm();
+
+    ws.launches = 0;
+    GM_CUDA(cudaEventRecord(ws.ev[0], s));
+    GM_CUDA(cudaMemcpyAsync(ds, hs, tab_bytes, cudaMemcpyHostToDevice, s));
+    GM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(BatchCounters) * 64 + sizeof(int32_t), s));
+    if (ctx->schedule == 1) {
+        // plain form: every pair gets its own launches (one block per work item)
+        GM_CUDA(cudaEventRecord(ws.ev[1], s));
+        for (int32_t k = 0; k < P; ++k) {
+            GM_CUDA(launch_order(imgs, d_pairs + k, 1, qorder, s));
+            GM_CUDA(launch_match_simt(imgs, d_pairs, d_item_off, P, qorder, h_item_off[k], h_item_off[k + 1], 0,
+                                      next, match_j, ctr, s));
+            ws.launches += 1 + (h_item_off[k + 1] > h_item_off[k]);
+        }
+        GM_CUDA(cudaEventRecord(ws.ev[2], s));
+    } else {
+        GM_CUDA(launch_order(imgs, d_pairs, P, qorder, s));
+        GM_CUDA(cudaEventRecord(ws.ev[1], s));
+        GM_CUDA(launch_match_simt(imgs, d_pairs, d_item_off, P, qorder, 0, h_item_off[P], grid, next, match_j, ctr,
+                                  s));
+        GM_CUDA(cudaEventRecord(ws.ev[2], s));
+        ws.launches += 2;
+    }
+    GM_CUDA(launch_count_matches(d_pairs, P, match_j, static_cast<int32_t *>(ws.d_counts.p), d_off, s));
+    GM_CUDA(launch_write_matches(d_pairs, P, match_j, d_off, rows, s));
+    ws.launches += 3;
+    GM_CUDA(cudaEventRecord(ws.ev[3], s));
+    int64_t *h_off = static_cast<int64_t *>(ws.h_off.p);
+    BatchCounters *h_ctr = reinterpret_cast<BatchCounters *>(h_off + P + 1);
+    GM_CUDA(cudaMemcpyAsync(h_off, d_off, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToHost, s));
+    GM_CUDA(cudaMemcpyAsync(h_ctr, ctr, sizeof(BatchCounters) * 64, cudaMemcpyDeviceToHost, s));
+    ws.path_used = GM_PATH_SIMT;
+    return GM_OK;
+}
+
+void engine_stats(gm_ctx *ctx, Workspace &ws, gm_stats &S)
+{
+    const int32_t P = ws.n_pairs;
+    const int64_t *h_off = static_cast<const int64_t *>(ws.h_off.p);
+    const BatchCounters *h_ctr = reinterpret_cast<const BatchCounters *>(h_off + P + 1);
+    S = gm_stats{};
+    S.n_pairs = P;
+    S.n_queries = ws.Q;
+    for (int k = 0; k < 64; ++k) {
+        S.n_candidates += (int64_t)h_ctr[k].candidates;
+        S.n_examined += (int64_t)h_ctr[k].examined;
+        S.n_redecided += (int64_t)h_ctr[k].redecided;
+    }
+    S.n_matches = h_off[P];
+    cudaEventElapsedTime(&S.ms_device, ws.ev[0], ws.ev[3]);
+    cudaEventElapsedTime(&S.ms_match, ws.ev[1], ws.ev[2]);
+    S.path_used = ws.path_used;
+    S.kernel_launches = ws.launches;
+    (void)ctx;
+}
+
+}  // namespace gm
+
+// ================================================================================================ C ABI
+extern "C" {
+
+gm_status gm_create(const gm_config *cfg, gm_ctx **out)
+{
+    if (!cfg || !out) return fail(GM_ERR_INVALID, "gm_create: null argument");
+    *out = nullptr;
+    if (cfg->path < GM_PATH_AUTO || cfg->path > GM_PATH_SIMT) return fail(GM_ERR_INVALID, "gm_create: bad path");
+    int cell_shift = 4;
+    if (cfg->cell_px) {
+        int c = cfg->cell_px, sh = 0;
+        while ((1 << sh) < c) ++sh;
+        if ((1 << sh) != c || sh < kMinCellShift || sh > kMaxCellShift)
+            return fail(GM_ERR_INVALID, "gm_create: cell_px must be a power of two in [8, 128]");
+        cell_shift = sh;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return fail(GM_ERR_CUDA, "gm_create: CUDA device %d unavailable", cfg->device);
+    }
+    GM_CUDA(cudaSetDevice(cfg->device));
+    gm_ctx *ctx = new gm_ctx();
+    ctx->device = cfg->device;
+    ctx->budget = cfg->mem_budget_bytes;
+    ctx->path = cfg->path;
+    ctx->cell_shift = cell_shift;
+    ctx->max_inflight = cfg->max_inflight > 0 ? cfg->max_inflight : 2;
+    if (cfg->cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return fail(GM_ERR_CUDA, "gm_create: cudaStreamCreate failed");
+        }
+        ctx->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
+    if (workspace_init(ctx->ws, ctx->stream) != GM_OK) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return GM_ERR_CUDA;
+    }
+    *out = ctx;
+    return GM_OK;
+}
+
+gm_status gm_destroy(gm_ctx *ctx)
+{
+    if (!ctx) return fail(GM_ERR_INVALID, "gm_destroy: null context");
+    cudaSetDevice(ctx->device);
+    if (ctx->server) {
+        server_stop(ctx->server);
+        ctx->server = nullptr;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->images) {
+        cudaFree(kv.second->block);
+        delete kv.second;
+    }
+    ctx->images.clear();
+    workspace_free(ctx, ctx->ws);
+    for (DevBuf *b : {&ctx->d_imgs, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap}) free_dev(ctx, *b);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return GM_OK;
+}
+
+gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value)
+{
+    if (!ctx) return fail(GM_ERR_INVALID, "gm_set_option: null context");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    switch (key) {
+    case GM_OPT_PATH:
+        if (value < GM_PATH_AUTO || value > GM_PATH_SIMT) return fail(GM_ERR_INVALID, "bad path %lld", (long long)value);
+        ctx->path = (int32_t)value;
+        return GM_OK;
+    case GM_OPT_SCHEDULE:
+        if (value < 0 || value > 1) return fail(GM_ERR_INVALID, "bad schedule %lld", (long long)value);
+        ctx->schedule = (int32_t)value;
+        return GM_OK;
+    case GM_OPT_CELL_PX: {
+        int sh = 0;
+        while ((1ll << sh) < value) ++sh;
+        if ((1ll << sh) != value || sh < kMinCellShift || sh > kMaxCellShift)
+            return fail(GM_ERR_INVALID, "cell_px must be a power of two in [8, 128]");
+        ctx->cell_shift = sh;
+        return GM_OK;
+    }
+    case GM_OPT_GRAPH:
+        if (value < 0 || value > 1) return fail(GM_ERR_INVALID, "bad graph flag");
+        ctx->graph = (int32_t)value;
+        return GM_OK;
+    default:
+        return fail(GM_ERR_INVALID, "unknown option %d", key);
+    }
+}
+
+gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t height, int32_t n, const float *xy,
+                       const float *scale, const uint8_t *desc, int32_t on_device)
+{
+    if (!ctx) return fail(GM_ERR_INVALID, "gm_image_put: null context");
+    if (image_id < 0 || width <= 0 || height <= 0 || width > (1 << 20) || height > (1 << 20) || n < 0 ||
+        (n > 0 && (!xy || !desc)) || (on_device != 0 && on_device != 1))
+        return fail(GM_ERR_INVALID, "gm_image_put: bad arguments (id %d, %dx%d, n %d)", image_id, width, height, n);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    GM_CUDA(cudaSetDevice(ctx->device));
+    const int sh = ctx->cell_shift;
+    const int cs = 1 << sh;
+    const int gx = (width + cs - 1) / cs, gy = (height + cs - 1) / cs;
+    const int64_t m = (int64_t)gx * gy;
+    if (m + 2 > INT32_MAX / 4) return fail(GM_ERR_INVALID, "gm_image_put: grid too large");
+    const size_t N = (size_t)n;
+    // one block: xy, perm, inv_perm, desc, norm, col_off, xy_r, idx_r, row_off, desc_h, scale
+    size_t sz[11] = {8 * N, 4 * N, 4 * N, 128 * N, 4 * N, 4 * (size_t)(m + 2), 8 * N, 4 * N, 4 * (size_t)(m + 2),
+                     256 * N, 4 * N};
+    size_t offs[11], tot = 0;
+    for (int k = 0; k < 11; ++k) {
+        offs[k] = tot;
+        tot += align_up(std::max<size_t>(sz[k], 1), 256);
+    }
+    auto it = ctx->images.find(image_id);
+    const bool reuse = it != ctx->images.end() && it->second->bytes >= tot;
+    const size_t replaced = it != ctx->images.end() ? it->second->bytes : 0;
+    if (!reuse && ctx->budget && ctx->bytes_images - replaced + tot + ctx->bytes_work > ctx->budget)
+        return fail(GM_ERR_BUDGET, "gm_image_put: image %d (%zu bytes) exceeds the device-memory budget", image_id, tot);
+    cudaStream_t s = ctx->ws.stream;
+    const float2 *raw_xy = reinterpret_cast<const float2 *>(xy);
+    const uint8_t *raw_desc = desc;
+    gm_status st;
+    // 1. stage host inputs and validate the keypoints (nothing registered is touched yet)
+    const size_t xy_al = align_up(8 * N + 1, 256);
+    if (!on_device && n > 0) {
+        if ((st = ensure_dev(ctx, ctx->d_stage, xy_al + align_up(128 * N + 1, 256))) != GM_OK) return st;
+        char *sp = static_cast<char *>(ctx->d_stage.p);
+        GM_CUDA(cudaMemcpyAsync(sp, xy, 8 * N, cudaMemcpyHostToDevice, s));
+        GM_CUDA(cudaMemcpyAsync(sp + xy_al, desc, 128 * N, cudaMemcpyHostToDevice, s));
+        raw_xy = reinterpret_cast<const float2 *>(sp);
+        raw_desc = reinterpret_cast<const uint8_t *>(sp + xy_al);
+    }
+    if ((st = ensure_dev(ctx, ctx->d_work, sizeof(int32_t) * 2 * (size_t)(m + 3))) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_bad, 256)) != GM_OK) return st;
+    unsigned long long *d_bad = static_cast<unsigned long long *>(ctx->d_bad.p);
+    int32_t *work = static_cast<int32_t *>(ctx->d_work.p);
+    GM_CUDA(launch_bucket_count(raw_xy, n, width, height, sh, gx, gy, work, d_bad, s));
+    unsigned long long bad = 0;
+    GM_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    GM_CUDA(cudaStreamSynchronize(s));
+    if (bad) return fail(GM_ERR_INVALID, "gm_image_put: %llu keypoints outside [0,%d)x[0,%d)", bad, width, height);
+    // 2. destination block: the replaced image's block when it is large enough (no serving batch may still read it)
+    if (ctx->server) server_drain(ctx->server);
+    void *block = nullptr;
+    if (reuse) {
+        block = it->second->block;
+    } else if (cudaMalloc(&block, tot) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GM_ERR_NOMEM, "gm_image_put: cudaMalloc of %zu bytes failed", tot);
+    }
+    char *bp = static_cast<char *>(block);
+    ImageDev dev{};
+    dev.n = n; dev.width = width; dev.height = height; dev.cell_shift = sh; dev.gx = gx; dev.gy = gy;
+    dev.xy = reinterpret_cast<float2 *>(bp + offs[0]);
+    dev.perm = reinterpret_cast<int32_t *>(bp + offs[1]);
+    dev.inv_perm = reinterpret_cast<int32_t *>(bp + offs[2]);
+    dev.desc = reinterpret_cast<int8_t *>(bp + offs[3]);
+    dev.norm = reinterpret_cast<int32_t *>(bp + offs[4]);
+    dev.col_off = reinterpret_cast<int32_t *>(bp + offs[5]);
+    dev.xy_r = reinterpret_cast<float2 *>(bp + offs[6]);
+    dev.idx_r = reinterpret_cast<int32_t *>(bp + offs[7]);
+    dev.row_off = reinterpret_cast<int32_t *>(bp + offs[8]);
+    dev.desc_h = reinterpret_cast<uint16_t *>(bp + offs[9]);
+    float *d_scale = reinterpret_cast<float *>(bp + offs[10]);
+    cudaError_t e = launch_bucket_build(raw_xy, raw_desc, n, width, height, sh, gx, gy, const_cast<float2 *>(dev.xy),
+                                        const_cast<int32_t *>(dev.perm), const_cast<int32_t *>(dev.inv_perm),
+                                        const_cast<int8_t *>(dev.desc), const_cast<int32_t *>(dev.norm),
+                                        const_cast<int32_t *>(dev.col_off), const_cast<float2 *>(dev.xy_r),
+                                        const_cast<int32_t *>(dev.idx_r), const_cast<int32_t *>(dev.row_off),
+                                        const_cast<uint16_t *>(dev.desc_h), work, s);
+    if (e == cudaSuccess && n > 0 && scale)
+        e = cudaMemcpyAsync(d_scale, scale, 4 * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        if (!reuse) cudaFree(block);
+        return fail(GM_ERR_CUDA, "gm_image_put: %s", cudaGetErrorString(e));
+    }
+    // 3. install: replace or take a free slot
+    ImageSlot *img = nullptr;
+    if (it != ctx->images.end()) {
+        img = it->second;
+        if (!reuse) {
+            cudaFree(img->block);
+            ctx->bytes_images -= img->bytes;
+            img->block = block;
+            img->bytes = tot;
+            ctx->bytes_images += tot;
+        }
+    } else {
+        img = new ImageSlot();
+        img->id = image_id;
+        int slot = -1;
+        for (size_t k = 0; k < ctx->slots.size(); ++k)
+            if (!ctx->slots[k]) { slot = (int)k; break; }
+        if (slot < 0) {
+            slot = (int)ctx->slots.size();
+            ctx->slots.push_back(nullptr);
+        }
+        img->slot = slot;
+        ctx->slots[slot] = img;
+        ctx->images[image_id] = img;
+        img->block = block;
+        img->bytes = tot;
+        ctx->bytes_images += tot;
+    }
+    img->dev = dev;
+    // device image table (grow keeps old entries)
+    const size_t need = sizeof(ImageDev) * ctx->slots.size();
+    if (ctx->d_imgs.bytes < need) {
+        DevBuf nb;
+        const size_t cap = align_up(std::max(need * 2, (size_t)4096), 256);
+        if (cudaMalloc(&nb.p, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GM_ERR_NOMEM, "gm_image_put: image table allocation failed");
+        }
+        nb.bytes = cap;
+        if (ctx->d_imgs.p) {
+            cudaMemcpyAsync(nb.p, ctx->d_imgs.p, ctx->d_imgs.bytes, cudaMemcpyDeviceToDevice, s);
+            cudaStreamSynchronize(s);
+        }
+        free_dev(ctx, ctx->d_imgs);
+        ctx->d_imgs = nb;
+        ctx->bytes_work += cap;
+    }
+    GM_CUDA(cudaMemcpyAsync(static_cast<ImageDev *>(ctx->d_imgs.p) + img->slot, &img->dev, sizeof(ImageDev),
+                            cudaMemcpyHostToDevice, s));
+    // the staged inputs and the image table entry are read asynchronously: finish before returning
+    GM_CUDA(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+gm_status gm_image_evict(gm_ctx *ctx, int32_t image_id)
+{
+    if (!ctx) return fail(GM_ERR_INVALID, "gm_image_evict: null context");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto it = ctx->images.find(image_id);
+    if (it == ctx->images.end()) return fail(GM_ERR_NOT_FOUND, "gm_image_evict: image %d not registered", image_id);
+    if (ctx->server) server_drain(ctx->server);
+    cudaStreamSynchronize(ctx->ws.stream);
+    ImageSlot *img = it->second;
+    cudaFree(img->block);
+    ctx->bytes_images -= img->bytes;
+    ctx->slots[img->slot] = nullptr;
+    ctx->images.erase(it);
+    delete img;
+    return GM_OK;
+}
+
+gm_status gm_match_pairs(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int64_t *pair_off, int32_t *matches,
+                         int64_t cap, int64_t *n_written)
+{
+    if (!ctx) return fail(GM_ERR_INVALID, "gm_match_pairs: null context");
+    if (n_pairs < 0 || (n_pairs > 0 && !pairs) || !pair_off || !n_written || cap < 0 || (cap > 0 && !matches))
+        return fail(GM_ERR_INVALID, "gm_match_pairs: bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    GM_CUDA(cudaSetDevice(ctx->device));
+    *n_written = 0;
+    Workspace &ws = ctx->ws;
+    if (n_pairs == 0) {
+        if (is_device_ptr(pair_off)) GM_CUDA(cudaMemset(pair_off, 0, sizeof(int64_t)));
+        else pair_off[0] = 0;
+        ctx->stats = gm_stats{};
+        return GM_OK;
+    }
+    gm_status st = engine_plan(ctx, ws, n_pairs, pairs);
+    if (st != GM_OK) return st;
+    if ((st = engine_launch(ctx, ws, nullptr)) != GM_OK) return st;
+    GM_CUDA(cudaStreamSynchronize(ws.stream));
+    engine_stats(ctx, ws, ctx->stats);
+    const int64_t *h_off = static_cast<const int64_t *>(ws.h_off.p);
+    const int64_t total = h_off[n_pairs];
+    *n_written = total;
+    cudaStream_t s = ws.stream;
+    if (is_device_ptr(pair_off))
+        GM_CUDA(cudaMemcpyAsync(pair_off, ws.d_off.p, sizeof(int64_t) * (n_pairs + 1), cudaMemcpyDeviceToDevice, s));
+    else
+        std::memcpy(pair_off, h_off, sizeof(int64_t) * (n_pairs + 1));
+    if (total > cap) {
+        GM_CUDA(cudaStreamSynchronize(s));
+        return fail(GM_ERR_NOMEM, "gm_match_pairs: %lld matches exceed cap %lld", (long long)total, (long long)cap);
+    }
+    if (total > 0)
+        GM_CUDA(cudaMemcpyAsync(matches, ws.d_rows.p, sizeof(int32_t) * 2 * total, cudaMemcpyDefault, s));
+    GM_CUDA(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+gm_status gm_band_candidates(gm_ctx *ctx, const gm_pair *pair, int32_t query_begin, int32_t query_count,
+                             int64_t *cand_off, int32_t *cand, int64_t cap, int64_t *n_written)
+{
+    if (!ctx || !pair || !cand_off || !n_written || query_count < 0 || query_begin < 0 || cap < 0 ||
+        (cap > 0 && !cand))
+        return fail(GM_ERR_INVALID, "gm_band_candidates: bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    GM_CUDA(cudaSetDevice(ctx->device));
+    PairDev pd;
+    gm_status st = prepare_pair(ctx, *pair, 0, pd);
+    if (st != GM_OK) return st;
+    if ((int64_t)query_begin + query_count > pd.n_a)
+        return fail(GM_ERR_INVALID, "gm_band_candidates: query range beyond |A| = %d", pd.n_a);
+    const int32_t nB = ctx->slots[pd.b]->dev.n;
+    const int32_t words = (nB + 31) / 32;
+    const size_t bm_bytes = sizeof(uint32_t) * (size_t)std::max(1, words) * std::max(1, query_count);
+    if ((st = ensure_dev(ctx, ctx->d_bitmap, bm_bytes)) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->ws.d_tab, 256)) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->ws.d_counts, sizeof(int32_t) * std::max(1, query_count))) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->ws.d_off, sizeof(int64_t) * (query_count + 1))) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->ws.d_ctr, sizeof(BatchCounters) * 64 + 256)) != GM_OK) return st;
+    if ((st = ensure_host(ctx->ws.h_off, sizeof(int64_t) * (query_count + 1))) != GM_OK) return st;
+    if ((st = ensure_host(ctx->ws.h_tab, sizeof(PairDev))) != GM_OK) return st;
+    cudaStream_t s = ctx->ws.stream;
+    std::memcpy(ctx->ws.h_tab.p, &pd, sizeof(pd));
+    GM_CUDA(cudaMemcpyAsync(ctx->ws.d_tab.p, ctx->ws.h_tab.p, sizeof(pd), cudaMemcpyHostToDevice, s));
+    GM_CUDA(cudaMemsetAsync(ctx->d_bitmap.p, 0, bm_bytes, s));
+    GM_CUDA(cudaMemsetAsync(ctx->ws.d_ctr.p, 0, sizeof(BatchCounters), s));
+    uint32_t *bm = static_cast<uint32_t *>(ctx->d_bitmap.p);
+    int64_t *d_off = static_cast<int64_t *>(ctx->ws.d_off.p);
+    GM_CUDA(launch_candidates_bitmap(static_cast<const ImageDev *>(ctx->d_imgs.p),
+                                     static_cast<const PairDev *>(ctx->ws.d_tab.p), query_begin, query_count, bm, words,
+                                     static_cast<BatchCounters *>(ctx->ws.d_ctr.p), s));
+    GM_CUDA(launch_bitmap_to_csr_count(bm, query_count, words, static_cast<int32_t *>(ctx->ws.d_counts.p), d_off, s));
+    int64_t *h_off = static_cast<int64_t *>(ctx->ws.h_off.p);
+    GM_CUDA(cudaMemcpyAsync(h_off, d_off, sizeof(int64_t) * (query_count + 1), cudaMemcpyDeviceToHost, s));
+    GM_CUDA(cudaStreamSynchronize(s));
+    const int64_t total = h_off[query_count];
+    *n_written = total;
+    if (is_device_ptr(cand_off))
+        GM_CUDA(cudaMemcpyAsync(cand_off, d_off, sizeof(int64_t) * (query_count + 1), cudaMemcpyDeviceToDevice, s));
+    else
+        std::memcpy(cand_off, h_off, sizeof(int64_t) * (query_count + 1));
+    if (total > cap) {
+        GM_CUDA(cudaStreamSynchronize(s));
+        return fail(GM_ERR_NOMEM, "gm_band_candidates: %lld candidates exceed cap %lld", (long long)total,
+                    (long long)cap);
+    }
+    if (total > 0) {
+        int32_t *dst = cand;
+        const bool dev = is_device_ptr(cand);
+        if (!dev) {
+            if ((st = ensure_dev(ctx, ctx->ws.d_rows, sizeof(int32_t) * total)) != GM_OK) return st;
+            dst = static_cast<int32_t *>(ctx->ws.d_rows.p);
+        }
+        GM_CUDA(launch_bitmap_to_csr_fill(bm, query_count, words, d_off, dst, s));
+        if (!dev) GM_CUDA(cudaMemcpyAsync(cand, dst, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, s));
+    }
+    GM_CUDA(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+gm_status gm_get_stats(const gm_ctx *ctx, gm_stats *out)
+{
+    if (!ctx || !out) return fail(GM_ERR_INVALID, "gm_get_stats: null argument");
+    *out = ctx->stats;
+    return GM_OK;
+}
+
+const char *gm_last_error(const gm_ctx *)
+{
+    return gm::last_error();
+}
+
+gm_status gm_submit(gm_ctx *ctx, const gm_pair *pair, uint64_t *ticket)
+{
+    if (!ctx || !pair || !ticket) return fail(GM_ERR_INVALID, "gm_submit: null argument");
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        if (!ctx->server) {
+            ctx->server = server_start(ctx);
+            if (!ctx->server) return fail(GM_ERR_CUDA, "gm_submit: could not start the serving loop");
+        }
+    }
+    return server_submit(ctx->server, *pair, ticket);
+}
+
+gm_status gm_get_serving_stats(gm_ctx *ctx, gm_serving_stats *out)
+{
+    if (!ctx || !out) return fail(GM_ERR_INVALID, "gm_get_serving_stats: null argument");
+    *out = gm_serving_stats{};
+    if (!ctx->server) return GM_OK;
+    return server_stats(ctx->server, out);
+}
+
+gm_status gm_serving_drain(gm_ctx *ctx)
+{
+    if (!ctx) return fail(GM_ERR_INVALID, "gm_serving_drain: null context");
+    if (ctx->server) server_wait_idle(ctx->server);
+    return GM_OK;
+}
+
+gm_status gm_poll(gm_ctx *ctx, uint64_t ticket, int32_t *matches, int64_t cap, int64_t *n, int32_t timeout_ms,
+                  double *latency_us)
+{
+    if (!ctx || !n || cap < 0 || (cap > 0 && !matches)) return fail(GM_ERR_INVALID, "gm_poll: bad arguments");
+    if (!ctx->server) return fail(GM_ERR_NOT_FOUND, "gm_poll: unknown ticket %llu", (unsigned long long)ticket);
+    return server_poll(ctx->server, ticket, matches, cap, n, timeout_ms, latency_us);
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// gm_bucket.cu -- grid bucketing of one image (App. A Step 1: cell index per feature, sort by cell, prefix scan
+// of the cell counts gives each cell's start).  Done once per image; the result stays resident.
+//
+// A stable counting sort: histogram (atomics) -> exclusive scan -> scatter.  The scatter is stable (original
+// index order inside every cell) because one warp walks the keypoints in index order, 32 at a time, and ranks
+// equal cells inside each chunk with __match_any_sync.  Two layouts are built: column-major (cells of a grid
+// column contiguous) and row-major.  Descriptors are then copied in column-major order, recentred to int8
+// (b - 128, the bit pattern b ^ 0x80), with their squared norms and an fp16 copy for the tensor-core path.
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "gm_internal.h"
+
+namespace gm {
+namespace {
+
+// Column-major and row-major cell index of a keypoint; a keypoint outside [0,W) x [0,H) (or NaN) goes to the
+// extra cell gx*gy at the end of both layouts, so every launch stays in bounds; the host rejects such images.
+__device__ __forceinline__ bool cell_of(float2 p, float W, float H, float inv_cs, int gx, int gy, int &ccol,
+                                        int &crow)
+{
+    if (!(p.x >= 0.0f && p.x < W && p.y >= 0.0f && p.y < H)) {
+        ccol = crow = gx * gy;
+        return false;
+    }
+    const int cx = min((int)floorf(p.x * inv_cs), gx - 1);   // cs is a power of two: p.x * inv_cs is exact
+    const int cy = min((int)floorf(p.y * inv_cs), gy - 1);
+    ccol = cx * gy + cy;
+    crow = cy * gx + cx;
+    return true;
+}
+
+__global__ void bucket_count_kernel(const float2 *__restrict__ xy, int32_t n, float W, float H, float inv_cs,
+                                    int gx, int gy, int32_t *cnt_col, int32_t *cnt_row,
+                                    unsigned long long *bad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int ccol, crow;
+    if (!cell_of(xy[i], W, H, inv_cs, gx, gy, ccol, crow)) atomicAdd(bad, 1ull);
+    atomicAdd(&cnt_col[ccol], 1);
+    atomicAdd(&cnt_row[crow], 1);
+}
+
+// Exclusive scan of m counts into off[0..m] (off[m] = total); one block of 1024 threads.
+__global__ void exclusive_scan_kernel(const int32_t *__restrict__ cnt, int32_t m, int32_t *__restrict__ off)
+{
+    __shared__ int32_t warp_sums[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < m; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < m ? cnt[i] : 0;
+        int incl = v;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, s);
+            if (lane >= s) incl += t;
+        }
+        if (lane == 31) warp_sums[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, s);
+                if (lane >= s) w += t;
+            }
+            warp_sums[lane] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        const int before = (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
+        if (i < m) off[i] = before + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[m] = carry;
+}
+
+// Stable scatter by one warp: column-major first (perm, xy, colpos), then row-major (xy_r, idx_r).
+// cur_col / cur_row: copies of the offsets, used as per-cell cursors.
+__global__ void bucket_scatter_kernel(const float2 *__restrict__ xy_raw, int32_t n, float W, float H, float inv_cs,
+                                      int gx, int gy,
+                                      int32_t *cur_col, int32_t *cur_row, float2 *xy, int32_t *perm,
+                                      int32_t *colpos, float2 *xy_r, int32_t *idx_r)  // colpos = inverse perm
+{
+    const int lane = threadIdx.x & 31;
+    for (int pass = 0; pass < 2; ++pass) {
+        int32_t *cur = pass == 0 ? cur_col : cur_row;
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + lane;
+            const bool valid = i < n;
+            const unsigned act = __ballot_sync(0xffffffffu, valid);
+            if (!valid) continue;
+            const float2 p = xy_raw[i];
+            int ccol, crow;
+            cell_of(p, W, H, inv_cs, gx, gy, ccol, crow);
+            const int cell = pass == 0 ? ccol : crow;
+            const unsigned peers = __match_any_sync(act, cell);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            const int leader = __ffs(peers) - 1;
+            int basepos = 0;
+            if (lane == leader) basepos = cur[cell];
+            basepos = __shfl_sync(peers, basepos, leader);
+            const int pos = basepos + rank;
+            if (lane == leader) cur[cell] = basepos + __popc(peers);
+            if (pass == 0) {
+                perm[pos] = i;
+                xy[pos] = p;
+                colpos[i] = pos;
+            } else {
+                xy_r[pos] = p;
+                idx_r[pos] = colpos[i];
+            }
+            __syncwarp(act);
+        }
+        __syncwarp();
+        __threadfence_block();
+    }
+}
+
+// One warp per sorted row: recentred int8 copy, squared norm and fp16 copy of the descriptor.
+__global__ void desc_permute_kernel(const uint8_t *__restrict__ desc_raw, const int32_t *__restrict__ perm,
+                                    int32_t n, int8_t *__restrict__ desc, int32_t *__restrict__ norm,
+                                    uint16_t *__restrict__ desc_h)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int src = perm[warp];
+    const uint32_t w = reinterpret_cast<const uint32_t *>(desc_raw + (int64_t)src * kDim)[lane] ^ 0x80808080u;
+    reinterpret_cast<uint32_t *>(desc + (int64_t)warp * kDim)[lane] = w;
+    int sq = 0;
+    uint32_t h01 = 0, h23 = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int v = (int)(int8_t)((w >> (8 * k)) & 0xffu);
+        sq += v * v;
+        const uint16_t hb = __half_as_ushort(__int2half_rn(v));
+        if (k < 2) h01 |= (uint32_t)hb << (16 * k);
+        else h23 |= (uint32_t)hb << (16 * (k - 2));
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
+    if (lane == 0) norm[warp] = sq;
+    if (desc_h) reinterpret_cast<uint2 *>(desc_h + (int64_t)warp * kDim)[lane] = make_uint2(h01, h23);
+}
+
+}  // namespace
+
+cudaError_t launch_bucket_count(const float2 *xy_raw, int32_t n, int32_t width, int32_t height, int32_t cell_shift,
+                                int32_t gx, int32_t gy, int32_t *work, unsigned long long *bad, cudaStream_t st)
+{
+    // work: two count arrays of gx*gy + 2 entries (the cells, the out-of-image cell, a spare)
+    const int m = gx * gy + 1;
+    const float inv_cs = 1.0f / (float)(1 << cell_shift);
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int32_t) * 2 * (m + 1), st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    if (n > 0)
+        bucket_count_kernel<<<(n + 255) / 256, 256, 0, st>>>(xy_raw, n, (float)width, (float)height, inv_cs, gx, gy,
+                                                             work, work + (m + 1), bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_build(const float2 *xy_raw, const uint8_t *desc_raw, int32_t n, int32_t width,
+                                int32_t height, int32_t cell_shift, int32_t gx, int32_t gy, float2 *xy, int32_t *perm,
+                                int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *col_off, float2 *xy_r,
+                                int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int32_t *work, cudaStream_t st)
+{
+    // col_off / row_off hold gx*gy + 2 entries: the cells, the out-of-image cell, the total
+    const int m = gx * gy + 1;
+    const float inv_cs = 1.0f / (float)(1 << cell_shift);
+    int32_t *cnt_col = work, *cnt_row = work + (m + 1);
+    cudaError_t e;
+    exclusive_scan_kernel<<<1, 1024, 0, st>>>(cnt_col, m, col_off);
+    exclusive_scan_kernel<<<1, 1024, 0, st>>>(cnt_row, m, row_off);
+    // cursors start at the offsets (reuse the count arrays)
+    if ((e = cudaMemcpyAsync(cnt_col, col_off, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(cnt_row, row_off, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return e;
+    if (n > 0) {
+        bucket_scatter_kernel<<<1, 32, 0, st>>>(xy_raw, n, (float)width, (float)height, inv_cs, gx, gy, cnt_col,
+                                                cnt_row, xy, perm, inv_perm, xy_r, idx_r);
+        desc_permute_kernel<<<(n + 7) / 8, 256, 0, st>>>(desc_raw, perm, n, desc, norm, desc_h);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gm

@@ -1,0 +1,128 @@
+// gm_ctx.h -- host-side context, workspace and batch engine shared by the C ABI (gm_api.cu) and the serving
+// loop (gm_serve.cu).  C++ only; not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/geomatch.h"
+#include "gm_internal.h"
+
+namespace gm {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct HostBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    bool mapped = false;
+};
+
+struct ImageSlot {
+    int32_t id = -1;
+    int32_t slot = -1;
+    ImageDev dev{};
+    void *block = nullptr;
+    size_t bytes = 0;
+};
+
+// Everything one batch needs on the device and in pinned host memory.  The synchronous API owns one; every
+// serving slot owns its own, so batches on different slots can be in flight at the same time.
+struct Workspace {
+    DevBuf d_tab;        // pair table, then the work-item table (pair, first query) of the match kernel
+    DevBuf d_qorder;     // int32 [Q] query order per pair
+    DevBuf d_matchj;     // int32 [Q] per-query decision (original B index or -1), indexed by original A index
+    DevBuf d_counts;     // int32 [P]
+    DevBuf d_off;        // int64 [P+1]
+    DevBuf d_rows;       // int32 [Q][2] match rows (device destination of the synchronous API)
+    DevBuf d_ctr;        // BatchCounters [64]
+    DevBuf d_next;       // int32 work-queue counter of the persistent kernel
+    HostBuf h_tab;       // pinned staging of d_tab
+    HostBuf h_off;       // pinned: offsets [P+1] then counters [64]
+    HostBuf h_rows;      // mapped pinned rows (serving destination)
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // plan of the batch being run
+    std::vector<PairDev> pd;
+    int64_t Q = 0, nitems = 0;
+    int32_t n_pairs = 0;
+    int32_t launches = 0;
+    int32_t path_used = 0;
+    // CUDA graph of the last plan shape
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey = 0;
+};
+
+struct Server;
+
+}  // namespace gm
+
+struct gm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t budget = 0;
+    int32_t path = GM_PATH_AUTO;
+    int32_t schedule = 0;
+    int32_t cell_shift = 4;
+    int32_t graph = 0;
+    int32_t max_inflight = 2;
+    int32_t num_sms = 0;
+
+    std::unordered_map<int32_t, gm::ImageSlot *> images;
+    std::vector<gm::ImageSlot *> slots;
+    gm::DevBuf d_imgs;              // ImageDev table indexed by slot
+    size_t bytes_images = 0;
+    size_t bytes_work = 0;          // every DevBuf of the context and of the server slots
+
+    gm::Workspace ws;               // synchronous calls
+    gm::DevBuf d_stage, d_work, d_bad, d_bitmap;
+    gm_stats stats{};
+    std::recursive_mutex mu;        // guards images, slots, budget counters and ws
+
+    gm::Server *server = nullptr;
+};
+
+namespace gm {
+
+gm_status fail(gm_status st, const char *fmt, ...);
+size_t align_up(size_t v, size_t a);
+gm_status ensure_dev(gm_ctx *ctx, DevBuf &b, size_t bytes);
+gm_status ensure_host(HostBuf &b, size_t bytes, bool mapped = false);
+void free_dev(gm_ctx *ctx, DevBuf &b);
+void free_host(HostBuf &b);
+gm_status workspace_init(Workspace &ws, cudaStream_t stream);
+void workspace_free(gm_ctx *ctx, Workspace &ws);
+
+// Validates the pairs and fills ws.pd / ws.Q / ws.nitems.  Caller holds ctx->mu.
+gm_status engine_plan(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs);
+// Enqueues the whole batch on ws.stream: table upload, order, match, count/scan, row writing into rows_dst
+// (device memory or mapped host memory with room for ws.Q rows; nullptr = ws.d_rows), then the D2H copy of the
+// offsets and counters into ws.h_off.  Nothing waits.  Caller holds ctx->mu.
+gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst);
+// After ws.stream has completed: the statistics of the batch.
+void engine_stats(gm_ctx *ctx, Workspace &ws, gm_stats &S);
+
+// serving
+Server *server_start(gm_ctx *ctx);
+void server_stop(Server *srv);
+gm_status server_submit(Server *srv, const gm_pair &pair, uint64_t *ticket);
+gm_status server_poll(Server *srv, uint64_t ticket, int32_t *matches, int64_t cap, int64_t *n, int32_t timeout_ms,
+                      double *latency_us);
+// Waits until no serving batch is in flight (caller holds ctx->mu, so none can start meanwhile).
+void server_drain(Server *srv);
+gm_status server_stats(Server *srv, gm_serving_stats *out);
+// Waits until every submitted request has completed (caller must not hold ctx->mu).
+void server_wait_idle(Server *srv);
+const char *last_error();
+
+}  // namespace gm

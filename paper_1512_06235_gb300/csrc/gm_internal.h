@@ -1,0 +1,96 @@
+// gm_internal.h -- device data layout shared by the CUDA kernels and the host orchestration of libgeomatch.
+//
+// Resident image (App. A Step 1, binned once per image and kept in HBM across every pair that uses it):
+//   grid of square cells of 2^cell_shift px; gx = ceil(W / cs) columns, gy = ceil(H / cs) rows;
+//   "column-major" order sorts keypoints by (cx, cy, original index): the cells of one grid column are
+//   contiguous, so a band walked column by column reads one contiguous run per column;
+//   "row-major" order sorts by (cy, cx, original index) for bands walked row by row (steep lines); it holds
+//   only coordinates and the column-major position, the descriptors exist once, in column-major order.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gm {
+
+constexpr int kDim = 128;           // SIFT descriptor length (bytes)
+constexpr int kMaxCellShift = 7;    // 128 px cells
+constexpr int kMinCellShift = 3;    // 8 px cells
+constexpr int kQueriesPerItem = 8;  // queries per work item (SIMT path: one warp each)
+
+struct ImageDev {
+    int32_t n, width, height;
+    int32_t cell_shift;             // cell size = 1 << cell_shift px
+    int32_t gx, gy;
+    const float2 *xy;               // [n] column-major order
+    const int32_t *perm;            // [n] column-major position -> original index
+    const int32_t *inv_perm;        // [n] original index -> column-major position
+    const int8_t *desc;             // [n][128] column-major order, recentred b - 128 (bit pattern b ^ 0x80)
+    const int32_t *norm;            // [n] sum_k (b_k - 128)^2
+    const int32_t *col_off;         // [gx*gy + 2]; cell (cx, cy) -> cx*gy + cy (then out-of-image cell, total)
+    const float2 *xy_r;             // [n] row-major order
+    const int32_t *idx_r;           // [n] row-major position -> column-major position
+    const int32_t *row_off;         // [gx*gy + 2]; cell (cx, cy) -> cy*gx + cx
+    const uint16_t *desc_h;         // [n][128] fp16 bits of (b - 128), column-major order (tensor-core path)
+};
+
+struct PairDev {
+    int32_t a, b;                   // slots in the device image table
+    float F[9];
+    float d;                        // band half-width in px, >= 0 or +inf
+    int32_t p, q;                   // ratio p/q, 0 <= p < q
+    int64_t qoff;                   // offset of this pair's queries in the per-query arrays
+    int32_t n_a;                    // |A|
+    int32_t flags;
+};
+
+// Counters accumulated by the kernels of one batch (unsigned long long for atomicAdd).
+struct BatchCounters {
+    unsigned long long candidates;  // sum_i |C_i|
+    unsigned long long examined;    // points visited by the cell walk
+    unsigned long long redecided;   // FP64 re-decisions
+    unsigned long long errors;      // device-side argument / bound violations (must stay 0)
+};
+
+// ---- launchers (host functions defined in the .cu files) ---------------------------------------------------
+// Image registration (two phases, so that invalid input never touches the destination): the count phase
+// histograms the cells and counts keypoints outside [0,W) x [0,H) into *bad; the build phase (only after *bad
+// was read as 0) scans, scatters and copies the descriptors.  work: int32 scratch of 2*(gx*gy + 2) entries,
+// carried from the first phase to the second.  All pointers are device pointers.
+cudaError_t launch_bucket_count(const float2 *xy_raw, int32_t n, int32_t width, int32_t height, int32_t cell_shift,
+                                int32_t gx, int32_t gy, int32_t *work, unsigned long long *bad, cudaStream_t st);
+cudaError_t launch_bucket_build(const float2 *xy_raw, const uint8_t *desc_raw, int32_t n, int32_t width,
+                                int32_t height, int32_t cell_shift, int32_t gx, int32_t gy, float2 *xy, int32_t *perm,
+                                int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *col_off, float2 *xy_r,
+                                int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int32_t *work, cudaStream_t st);
+
+// Query ordering (App. A Step 2 as an order only): per pair, sorts A's queries by the position of their
+// epipolar line in B.  qorder[qoff + k] = column-major position in A of the k-th query.
+cudaError_t launch_order(const ImageDev *imgs, const PairDev *pairs, int32_t n_pairs, int32_t *qorder,
+                         cudaStream_t st);
+
+// SIMT matching path: one warp per query.  match_j[qoff + i] = original B index or -1 for original A index i.
+// Work items are groups of kQueriesPerItem sorted queries; pair k owns items [item_off[k], item_off[k+1]).
+// grid > 0: persistent launch of `grid` blocks taking items [item_begin, item_end) from the counter *next
+// (zeroed by the caller); grid == 0: one block per item.
+cudaError_t launch_match_simt(const ImageDev *imgs, const PairDev *pairs, const int64_t *item_off, int32_t n_pairs,
+                              const int32_t *qorder, int64_t item_begin, int64_t item_end, int32_t grid,
+                              int32_t *next, int32_t *match_j, BatchCounters *ctr, cudaStream_t st);
+int match_simt_blocks_per_sm();
+
+// Output assembly: counts[p] = matches of pair p, pair_off = exclusive scan (pair_off[n_pairs] = total), then
+// rows (i, j) sorted by i into matches.
+cudaError_t launch_count_matches(const PairDev *pairs, int32_t n_pairs, const int32_t *match_j, int32_t *counts,
+                                 int64_t *pair_off, cudaStream_t st);
+cudaError_t launch_write_matches(const PairDev *pairs, int32_t n_pairs, const int32_t *match_j,
+                                 const int64_t *pair_off, int32_t *matches, cudaStream_t st);
+
+// Candidate sets of one pair for original queries [q_begin, q_begin + q_count): one bitmap per query over B's
+// original indices (words 32-bit words each, zeroed by the caller), then CSR with ascending indices.
+cudaError_t launch_candidates_bitmap(const ImageDev *imgs, const PairDev *pair, int32_t q_begin, int32_t q_count,
+                                     uint32_t *bitmap, int32_t words, BatchCounters *ctr, cudaStream_t st);
+cudaError_t launch_bitmap_to_csr_count(const uint32_t *bitmap, int32_t q_count, int32_t words, int32_t *counts,
+                                       int64_t *off, cudaStream_t st);
+cudaError_t launch_bitmap_to_csr_fill(const uint32_t *bitmap, int32_t q_count, int32_t words, const int64_t *off,
+                                      int32_t *cand, cudaStream_t st);
+
+}  // namespace gm

@@ -1,0 +1,368 @@
+"""ctypes binding of libgeomatch (include/geomatch.h): geometry-aware pairwise feature matching on a GB300.
+
+Argument marshalling only -- every step of the matching runs in the CUDA library.  The functions ``gm_*`` mirror
+the C entry points one to one; ``Context`` bundles them for convenience.  Device buffers may be torch CUDA
+tensors (torch provides device memory and streams), host buffers numpy arrays.
+
+The library must have been built (``python -m paper_1512_06235_gb300.build``); loading fails loudly otherwise.
+There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgeomatch.so")
+
+GM_OK, GM_ERR_INVALID, GM_ERR_NOMEM, GM_ERR_BUDGET, GM_ERR_NOT_FOUND, GM_ERR_CUDA, GM_ERR_TIMEOUT, \
+    GM_ERR_CANCELLED, GM_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6, -7, -8
+GM_PATH_AUTO, GM_PATH_TC, GM_PATH_MMA, GM_PATH_SIMT = 0, 1, 2, 3
+GM_OPT_PATH, GM_OPT_SCHEDULE, GM_OPT_CELL_PX, GM_OPT_GRAPH = 1, 2, 3, 4
+
+_STATUS_NAMES = {0: "GM_OK", -1: "GM_ERR_INVALID", -2: "GM_ERR_NOMEM", -3: "GM_ERR_BUDGET", -4: "GM_ERR_NOT_FOUND",
+                 -5: "GM_ERR_CUDA", -6: "GM_ERR_TIMEOUT", -7: "GM_ERR_CANCELLED", -8: "GM_ERR_BUSY"}
+
+c_i32, c_i64, c_u16, c_u64, c_f32, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint16, ctypes.c_uint64, \
+    ctypes.c_float, ctypes.c_void_p
+
+
+class GmConfig(ctypes.Structure):
+    _fields_ = [("device", c_i32), ("mem_budget_bytes", c_u64), ("max_inflight", c_i32), ("cuda_stream", c_p),
+                ("path", c_i32), ("cell_px", c_i32), ("tuner_cache", ctypes.c_char_p)]
+
+
+class GmPair(ctypes.Structure):
+    _fields_ = [("img_a", c_i32), ("img_b", c_i32), ("F", c_f32 * 9), ("band_px", c_f32), ("ratio_num", c_u16),
+                ("ratio_den", c_u16)]
+
+
+class GmStats(ctypes.Structure):
+    _fields_ = [("n_pairs", c_i64), ("n_queries", c_i64), ("n_candidates", c_i64), ("n_examined", c_i64),
+                ("n_redecided", c_i64), ("n_matches", c_i64), ("ms_device", c_f32), ("ms_match", c_f32),
+                ("path_used", c_i32), ("kernel_launches", c_i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GmServingStats(ctypes.Structure):
+    _fields_ = [("submitted", c_i64), ("completed", c_i64), ("failed", c_i64), ("batches", c_i64),
+                ("max_batch_pairs", c_i64), ("peak_inflight_batches", c_i64), ("rejected_budget", c_i64),
+                ("rejected_busy", c_i64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GeomatchError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+# C entry points: name -> (restype, argtypes)
+_SIGNATURES = {
+    "gm_create": (c_i32, [ctypes.POINTER(GmConfig), ctypes.POINTER(c_p)]),
+    "gm_destroy": (c_i32, [c_p]),
+    "gm_set_option": (c_i32, [c_p, c_i32, c_i64]),
+    "gm_image_put": (c_i32, [c_p, c_i32, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i32]),
+    "gm_image_evict": (c_i32, [c_p, c_i32]),
+    "gm_match_pairs": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_p, c_p, c_i64, ctypes.POINTER(c_i64)]),
+    "gm_band_candidates": (c_i32, [c_p, ctypes.POINTER(GmPair), c_i32, c_i32, c_p, c_p, c_i64,
+                                   ctypes.POINTER(c_i64)]),
+    "gm_get_stats": (c_i32, [c_p, ctypes.POINTER(GmStats)]),
+    "gm_submit": (c_i32, [c_p, ctypes.POINTER(GmPair), ctypes.POINTER(c_u64)]),
+    "gm_poll": (c_i32, [c_p, c_u64, c_p, c_i64, ctypes.POINTER(c_i64), c_i32, ctypes.POINTER(ctypes.c_double)]),
+    "gm_get_serving_stats": (c_i32, [c_p, ctypes.POINTER(GmServingStats)]),
+    "gm_serving_drain": (c_i32, [c_p]),
+    "gm_last_error": (ctypes.c_char_p, [c_p]),
+}
+EXPORTED = tuple(_SIGNATURES)
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libgeomatch.so (no fallback: raises if the CUDA library has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libgeomatch.so not found at {path}; build it with "
+                          "`python -m paper_1512_06235_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status != GM_OK:
+        msg = load_library().gm_last_error(ctx)
+        raise GeomatchError(status, msg.decode() if msg else "")
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, on_device, keepalive) of a numpy array or a torch tensor (contiguous)."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        x = x.contiguous()
+        return x.data_ptr(), int(x.is_cuda), x
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, 0, a
+
+
+def make_pair(a: int, b: int, F, d: float, p: int = 4, q: int = 5) -> GmPair:
+    pr = GmPair()
+    pr.img_a, pr.img_b = int(a), int(b)
+    Fa = np.asarray(F, dtype=np.float32).reshape(9)
+    for k in range(9):
+        pr.F[k] = float(Fa[k])
+    pr.band_px = float(d)
+    pr.ratio_num, pr.ratio_den = int(p), int(q)
+    return pr
+
+
+def _pairs_array(pairs):
+    arr = (GmPair * max(1, len(pairs)))()
+    for k, pr in enumerate(pairs):
+        arr[k] = pr if isinstance(pr, GmPair) else make_pair(pr.a, pr.b, pr.F, pr.d, pr.p, pr.q)
+    return arr
+
+
+# ---------------------------------------------------------------------------------------------- C mirrors
+
+def gm_create(device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 2, cuda_stream: int = 0,
+              path: int = GM_PATH_AUTO, cell_px: int = 0):
+    lib = load_library()
+    cfg = GmConfig(device, mem_budget_bytes, max_inflight, c_p(cuda_stream or None), path, cell_px, None)
+    h = c_p()
+    _check(lib.gm_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def gm_destroy(ctx):
+    _check(load_library().gm_destroy(ctx))
+
+
+def gm_set_option(ctx, key: int, value: int):
+    _check(load_library().gm_set_option(ctx, key, value), ctx)
+
+
+def gm_image_put(ctx, image_id: int, width: int, height: int, xy, scale, desc):
+    """xy float32 [n,2], scale float32 [n] (or None), desc uint8 [n,128]: numpy (host) or torch CUDA tensors."""
+    n = int(xy.shape[0])
+    pxy, dev_xy, k1 = _ptr(xy)
+    psc, dev_sc, k2 = _ptr(scale)
+    pds, dev_ds, k3 = _ptr(desc)
+    if n and not (dev_xy == dev_ds and (scale is None or dev_sc == dev_xy)):
+        raise ValueError("gm_image_put: xy, scale and desc must all be host or all be device memory")
+    _check(load_library().gm_image_put(ctx, image_id, width, height, n, pxy, psc, pds, dev_xy), ctx)
+    del k1, k2, k3
+
+
+def gm_image_evict(ctx, image_id: int):
+    _check(load_library().gm_image_evict(ctx, image_id), ctx)
+
+
+def gm_match_pairs(ctx, pairs, pair_off, matches, cap: int) -> int:
+    """Low-level mirror: writes into caller buffers (numpy or torch CUDA); returns n_written.
+    Raises GeomatchError (GM_ERR_NOMEM carries the required count in .required)."""
+    arr = _pairs_array(pairs)
+    po, _, k1 = _ptr(pair_off)
+    pm, _, k2 = _ptr(matches)
+    n = c_i64(0)
+    st = load_library().gm_match_pairs(ctx, len(pairs), arr, po, pm, cap, ctypes.byref(n))
+    if st == GM_ERR_NOMEM:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = n.value
+        raise err
+    _check(st, ctx)
+    del k1, k2
+    return n.value
+
+
+def gm_band_candidates(ctx, pair, query_begin: int, query_count: int, cand_off, cand, cap: int) -> int:
+    arr = _pairs_array([pair])
+    po, _, k1 = _ptr(cand_off)
+    pc, _, k2 = _ptr(cand)
+    n = c_i64(0)
+    st = load_library().gm_band_candidates(ctx, arr, query_begin, query_count, po, pc, cap, ctypes.byref(n))
+    if st == GM_ERR_NOMEM:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = n.value
+        raise err
+    _check(st, ctx)
+    del k1, k2
+    return n.value
+
+
+def gm_get_stats(ctx) -> dict:
+    s = GmStats()
+    _check(load_library().gm_get_stats(ctx, ctypes.byref(s)), ctx)
+    return s.as_dict()
+
+
+def gm_submit(ctx, pair) -> int:
+    arr = _pairs_array([pair])
+    t = c_u64(0)
+    _check(load_library().gm_submit(ctx, arr, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def gm_poll(ctx, ticket: int, matches: np.ndarray, timeout_ms: int = -1):
+    """Returns (status, n, latency_us); status GM_OK or GM_ERR_TIMEOUT; other errors raise."""
+    pm, _, keep = _ptr(matches)
+    n = c_i64(0)
+    lat = ctypes.c_double(0.0)
+    st = load_library().gm_poll(ctx, ticket, pm, int(matches.shape[0]), ctypes.byref(n), timeout_ms,
+                                ctypes.byref(lat))
+    if st == GM_ERR_TIMEOUT:
+        return st, 0, 0.0
+    if st == GM_ERR_NOMEM:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = n.value
+        raise err
+    _check(st, ctx)
+    del keep
+    return st, n.value, lat.value
+
+
+def gm_get_serving_stats(ctx) -> dict:
+    s = GmServingStats()
+    _check(load_library().gm_get_serving_stats(ctx, ctypes.byref(s)), ctx)
+    return s.as_dict()
+
+
+def gm_serving_drain(ctx):
+    _check(load_library().gm_serving_drain(ctx), ctx)
+
+
+def gm_last_error(ctx=None) -> str:
+    m = load_library().gm_last_error(ctx)
+    return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------------------------- convenience
+
+class Context:
+    """A matcher context on one GPU: resident images, batch matching, candidate sets and serving."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 2, stream=None,
+                 path: int = GM_PATH_AUTO, cell_px: int = 0):
+        handle = 0
+        if stream is not None:
+            handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.h = gm_create(device, mem_budget_bytes, max_inflight, handle, path, cell_px)
+        self.n = {}
+        self.device = device
+
+    def close(self):
+        if self.h:
+            gm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, key, value):
+        gm_set_option(self.h, key, value)
+
+    def put_image(self, image_id: int, image=None, *, width=None, height=None, xy=None, scale=None, desc=None):
+        if image is not None:
+            width, height, xy, scale, desc = image.width, image.height, image.xy, image.scale, image.desc
+        gm_image_put(self.h, image_id, width, height, xy, scale, desc)
+        self.n[image_id] = int(xy.shape[0])
+
+    def evict(self, image_id: int):
+        gm_image_evict(self.h, image_id)
+        self.n.pop(image_id, None)
+
+    def match_pairs(self, pairs, device_out: bool = False):
+        """Returns (pair_off int64[P+1], matches int32[M,2]) as numpy arrays (or torch CUDA tensors)."""
+        cap = sum(self.n.get(p.img_a if isinstance(p, GmPair) else p.a, 0) for p in pairs)
+        if device_out:
+            import torch
+            off = torch.empty(len(pairs) + 1, dtype=torch.int64, device=f"cuda:{self.device}")
+            m = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=f"cuda:{self.device}")
+        else:
+            off = np.empty(len(pairs) + 1, np.int64)
+            m = np.empty((max(cap, 1), 2), np.int32)
+        n = gm_match_pairs(self.h, pairs, off, m, cap)
+        return off, m[:n]
+
+    def band_candidates(self, pair, query_begin: int = 0, query_count=None):
+        a = pair.img_a if isinstance(pair, GmPair) else pair.a
+        b = pair.img_b if isinstance(pair, GmPair) else pair.b
+        if query_count is None:
+            query_count = self.n[a] - query_begin
+        off = np.empty(query_count + 1, np.int64)
+        cap = max(1, query_count * 64)
+        while True:
+            cand = np.empty(cap, np.int32)
+            try:
+                n = gm_band_candidates(self.h, pair, query_begin, query_count, off, cand, cap)
+                return off, cand[:n]
+            except GeomatchError as e:
+                if e.status != GM_ERR_NOMEM:
+                    raise
+                cap = max(e.required, 1)
+        del b
+
+    def stats(self) -> dict:
+        return gm_get_stats(self.h)
+
+    def submit(self, pair) -> int:
+        return gm_submit(self.h, pair)
+
+    def poll(self, ticket: int, timeout_ms: int = -1, cap: int = 1 << 16):
+        """Returns (matches int32[M,2], latency_us), or None if the request is not done within timeout_ms."""
+        while True:
+            buf = np.empty((cap, 2), np.int32)
+            try:
+                st, n, lat = gm_poll(self.h, ticket, buf, timeout_ms)
+            except GeomatchError as e:
+                if e.status != GM_ERR_NOMEM:
+                    raise
+                cap = e.required
+                continue
+            if st == GM_ERR_TIMEOUT:
+                return None
+            return buf[:n], lat
+
+    def serving_stats(self) -> dict:
+        return gm_get_serving_stats(self.h)
+
+    def serving_drain(self):
+        gm_serving_drain(self.h)
+
+
+def split_matches(pair_off, matches):
+    """Per-pair list of (i, j) arrays from the CSR returned by match_pairs."""
+    off = pair_off.cpu().numpy() if _is_torch(pair_off) else pair_off
+    m = matches.cpu().numpy() if _is_torch(matches) else matches
+    return [m[off[k]:off[k + 1]] for k in range(len(off) - 1)]
+
+
+INF = math.inf

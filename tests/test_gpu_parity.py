@@ -1,0 +1,216 @@
+"""GPU path vs the CPU oracle, through the C ABI (bit-exact: match lists and candidate sets are integers).
+
+Sizes span several grid cells, work items and ragged tails; the full-size batch (1200 facade pairs of 8000
+keypoints, the benchmark's launch configuration) is checked on a sample of pairs that the oracle computes one
+by one, plus schedule / cell-size / path invariance over the whole batch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from tests import golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1512_06235_gb300 import geomatch
+    geomatch.load_library()
+    return geomatch
+
+
+def _oracle_rows(sc, pr):
+    A, B = sc.images[pr.a], sc.images[pr.b]
+    mj, nc = oracle.match_pair(A.xy, A.desc, B.xy, B.desc, pr.F, pr.d, pr.p, pr.q)
+    return oracle.matches_from_match_j(mj), nc
+
+
+def _gpu_rows(gm, sc, pairs=None, cell_px=0, path=0, schedule=0):
+    pairs = sc.pairs if pairs is None else pairs
+    with gm.Context(device=0, cell_px=cell_px, path=path) as ctx:
+        if schedule:
+            ctx.set_option(gm.GM_OPT_SCHEDULE, schedule)
+        used = sorted({p.a for p in pairs} | {p.b for p in pairs})
+        for k in used:
+            ctx.put_image(k, sc.images[k])
+        off, m = ctx.match_pairs(pairs)
+        st = ctx.stats()
+    return gm.split_matches(off, m), st
+
+
+def test_two_view_bit_exact(gm, two_view_scene):
+    sc = two_view_scene
+    rows, st = _gpu_rows(gm, sc)
+    want, nc = _oracle_rows(sc, sc.pairs[0])
+    np.testing.assert_array_equal(rows[0], want)
+    assert st["n_candidates"] == nc
+    assert st["n_examined"] >= nc
+
+
+@pytest.mark.parametrize("cell_px", [8, 16, 64, 128])
+def test_two_view_cell_sizes(gm, two_view_scene, cell_px):
+    sc = two_view_scene
+    rows, st = _gpu_rows(gm, sc, cell_px=cell_px)
+    want, nc = _oracle_rows(sc, sc.pairs[0])
+    np.testing.assert_array_equal(rows[0], want)
+    assert st["n_candidates"] == nc
+
+
+def _random_batch(seeds, d_values, levels=256, n_a=300, n_b=411):
+    """One scene per (seed, d): several pairs of generic geometry in one batch (images renumbered)."""
+    images, pairs = [], []
+    for s in seeds:
+        for d in d_values:
+            sc = scenes.random_small(s, n_a, n_b, d=d, desc_levels=levels)
+            a, b = len(images), len(images) + 1
+            images += sc.images
+            pr = sc.pairs[0]
+            pairs.append(scenes.Pair(a, b, pr.F, d, 4, 5))
+            pairs.append(scenes.Pair(b, a, pr.F.reshape(3, 3).T.copy().reshape(9), d, 9, 10))
+    return scenes.Scene("random_batch", images, pairs)
+
+
+@pytest.mark.parametrize("levels", [256, 4, 2])
+def test_random_pairs_batched(gm, levels):
+    sc = _random_batch(range(3), [0.0, 1.5, 4.0, 13.0, math.inf], levels=levels)
+    rows, st = _gpu_rows(gm, sc)
+    total = 0
+    for k, pr in enumerate(sc.pairs):
+        want, nc = _oracle_rows(sc, pr)
+        np.testing.assert_array_equal(rows[k], want, err_msg=f"pair {k} d={pr.d}")
+        total += nc
+    assert st["n_candidates"] == total
+
+
+def test_band_candidates_equal_linear_search(gm):
+    """The cell walk + exact test returns exactly Eq. 2's set (linear search) for every query: steep, shallow and
+    oblique lines, several band widths."""
+    sc = _random_batch(range(2), [0.5, 4.0, 25.0], n_a=120, n_b=700)
+    with gm.Context(device=0) as ctx:
+        for k, im in enumerate(sc.images):
+            ctx.put_image(k, im)
+        for pr in sc.pairs:
+            off, cand = ctx.band_candidates(gm.make_pair(pr.a, pr.b, pr.F, pr.d, pr.p, pr.q))
+            A, B = sc.images[pr.a], sc.images[pr.b]
+            for i in range(A.n):
+                want = oracle.band_set(pr.F, pr.d, A.xy[i, 0], A.xy[i, 1], B.xy)
+                np.testing.assert_array_equal(cand[off[i]:off[i + 1]], want)
+
+
+@pytest.mark.parametrize("case", golden.band_cases(), ids=lambda c: c["name"])
+def test_band_golden_on_gpu(gm, case):
+    W, H = 2048, 2048
+    pts = case["points"]
+    qxy = np.array([case["q"]], np.float32)
+    with gm.Context(device=0) as ctx:
+        ctx.put_image(0, width=W, height=H, xy=qxy, scale=None, desc=np.zeros((1, 128), np.uint8))
+        ctx.put_image(1, width=W, height=H, xy=pts, scale=None, desc=np.zeros((len(pts), 128), np.uint8))
+        off, cand = ctx.band_candidates(gm.make_pair(0, 1, case["F"], case["d"]))
+    np.testing.assert_array_equal(cand, np.nonzero(case["expected"])[0])
+
+
+@pytest.mark.parametrize("case", golden.ratio_cases(), ids=lambda c: c["name"])
+def test_ratio_golden_on_gpu(gm, case):
+    n = case["bd"].shape[0]
+    with gm.Context(device=0) as ctx:
+        ctx.put_image(0, width=64, height=64, xy=np.array([[5.0, 5.0]], np.float32), scale=None,
+                      desc=case["qd"][None])
+        ctx.put_image(1, width=64, height=64, xy=np.full((n, 2), 10.0, np.float32).reshape(-1, 2), scale=None,
+                      desc=case["bd"].reshape(-1, 128))
+        off, m = ctx.match_pairs([gm.make_pair(0, 1, np.eye(3).reshape(9), math.inf, case["p"], case["q"])])
+    want = [] if case["expected"] < 0 else [[0, case["expected"]]]
+    np.testing.assert_array_equal(m.reshape(-1, 2), np.array(want, np.int32).reshape(-1, 2))
+
+
+def test_edge_cases(gm):
+    rng = np.random.default_rng(5)
+    W, H = 640, 480
+    xy = np.stack([rng.uniform(0, W, 500), rng.uniform(0, H, 500)], 1).astype(np.float32)
+    xy[:40] = np.array([[np.float32(k * 16), np.float32(32)] for k in range(40)], np.float32)  # on cell borders
+    xy[40:60] = [W - 1e-3, H - 1e-3]                                                            # one corner cell
+    xy[60:70] = [0.0, 0.0]
+    desc = rng.integers(0, 256, (500, 128), dtype=np.uint8)
+    desc[100:110] = desc[200]                                                                   # duplicates
+    empty = np.zeros((0, 2), np.float32)
+    F_gen = scenes.random_small(9, 4, 4, w=W, h=H).pairs[0].F
+    F_vert = np.array([0, 0, 1, 0, 0, 0, 0, 0, -300], np.float32)        # lines x' = 300 (pure column)
+    F_zero = np.array([0, 0, 0, 0, 0, 0, 0, 0, 1], np.float32)          # no line at all
+    images = [scenes.Image(W, H, xy, np.ones(500, np.float32), desc, np.full(500, -1, np.int32)),
+              scenes.Image(W, H, empty, np.zeros(0, np.float32), np.zeros((0, 128), np.uint8), np.zeros(0, np.int32)),
+              scenes.Image(W, H, xy[:1].copy(), np.ones(1, np.float32), desc[:1].copy(), np.full(1, -1, np.int32))]
+    pairs = [scenes.Pair(0, 0, F_gen, 6.0), scenes.Pair(0, 1, F_gen, 6.0), scenes.Pair(1, 0, F_gen, 6.0),
+             scenes.Pair(0, 2, F_gen, math.inf), scenes.Pair(0, 0, scenes.RECTIFIED_F, 0.0),
+             scenes.Pair(0, 0, F_vert, 3.0), scenes.Pair(0, 0, F_zero, 5.0), scenes.Pair(0, 0, F_zero, math.inf),
+             scenes.Pair(2, 0, F_gen, 1e6)]
+    sc = scenes.Scene("edges", images, pairs)
+    rows, _ = _gpu_rows(gm, sc)
+    for k, pr in enumerate(pairs):
+        want, _ = _oracle_rows(sc, pr)
+        np.testing.assert_array_equal(rows[k], want, err_msg=f"pair {k}")
+
+
+def test_invalid_inputs(gm):
+    with gm.Context(device=0) as ctx:
+        with pytest.raises(gm.GeomatchError) as e:
+            ctx.put_image(0, width=10, height=10, xy=np.array([[10.0, 1.0]], np.float32), scale=None,
+                          desc=np.zeros((1, 128), np.uint8))
+        assert e.value.status == gm.GM_ERR_INVALID
+        ctx.put_image(0, width=10, height=10, xy=np.array([[1.0, 1.0], [2.0, 2.0]], np.float32), scale=None,
+                      desc=np.zeros((2, 128), np.uint8))
+        with pytest.raises(gm.GeomatchError) as e:
+            ctx.match_pairs([gm.make_pair(0, 7, np.eye(3).reshape(9), 1.0)])
+        assert e.value.status == gm.GM_ERR_NOT_FOUND
+        with pytest.raises(gm.GeomatchError) as e:
+            ctx.match_pairs([gm.make_pair(0, 0, np.eye(3).reshape(9), 1.0, 5, 5)])
+        assert e.value.status == gm.GM_ERR_INVALID
+        with pytest.raises(gm.GeomatchError) as e:
+            ctx.match_pairs([gm.make_pair(0, 0, np.eye(3).reshape(9), float("nan"))])
+        assert e.value.status == gm.GM_ERR_INVALID
+        off = np.zeros(2, np.int64)
+        m = np.zeros((1, 2), np.int32)
+        F = np.eye(3, dtype=np.float32).reshape(9)
+        n = gm.gm_match_pairs(ctx.h, [gm.make_pair(0, 0, F, math.inf, 1, 2)], off, m, 0)
+        assert n == 0
+
+
+def test_facade_full_batch_sampled(gm, facade_scene):
+    """Full-size batch in the benchmark's launch configuration; 24 pairs spread over it checked exactly."""
+    sc = facade_scene
+    rows, st = _gpu_rows(gm, sc)
+    sample = list(range(0, len(sc.pairs), 50))
+    wants = oracle.match_batch(sc.images, [sc.pairs[k] for k in sample])[0]
+    for k, mj in zip(sample, wants):
+        np.testing.assert_array_equal(rows[k], oracle.matches_from_match_j(mj), err_msg=f"pair {k}")
+    assert st["n_pairs"] == len(sc.pairs)
+    assert st["n_matches"] == sum(len(r) for r in rows)
+    # per-pair launches (plain form) give the same lists over the whole batch
+    rows1, st1 = _gpu_rows(gm, sc, schedule=1)
+    for k in range(len(sc.pairs)):
+        np.testing.assert_array_equal(rows1[k], rows[k])
+    assert st1["n_candidates"] == st["n_candidates"]
+
+
+def test_serving_alone_equals_mix(gm, facade_scene):
+    sc = facade_scene
+    pairs = sc.pairs[:60]
+    with gm.Context(device=0, max_inflight=3) as ctx:
+        for k in sorted({p.a for p in pairs} | {p.b for p in pairs}):
+            ctx.put_image(k, sc.images[k])
+        off, m = ctx.match_pairs(pairs)
+        batch_rows = gm.split_matches(off, m)
+        tickets = [ctx.submit(gm.make_pair(p.a, p.b, p.F, p.d, p.p, p.q)) for p in pairs]
+        for k, t in enumerate(tickets):
+            got, lat = ctx.poll(t, timeout_ms=60000)
+            np.testing.assert_array_equal(got, batch_rows[k])
+            assert lat > 0
+        alone = ctx.submit(gm.make_pair(pairs[7].a, pairs[7].b, pairs[7].F, pairs[7].d))
+        got, _ = ctx.poll(alone, timeout_ms=60000)
+        np.testing.assert_array_equal(got, batch_rows[7])
+        ss = ctx.serving_stats()
+        assert ss["completed"] == len(pairs) + 1 and ss["failed"] == 0
