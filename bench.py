@@ -162,7 +162,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--path", type=int, default=0)
     ap.add_argument("--schedule", type=int, default=0)
+    ap.add_argument("--cell", type=int, default=0, help="grid cell size in px (0 = library default)")
+    ap.add_argument("--group", type=int, default=16, help="queries per group of the mma path (16 or 32)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--pairs", type=int, default=0, help="use only the first N pairs (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -186,11 +189,15 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc = scenes.facade()
+    if args.pairs:
+        sc.pairs = sc.pairs[:args.pairs]
     pairs = sc.pairs
     stream = torch.cuda.current_stream(dev)
-    ctx = gm.Context(device=local, stream=stream, path=args.path)
+    ctx = gm.Context(device=local, stream=stream, path=args.path, cell_px=args.cell)
     if args.schedule:
         ctx.set_option(gm.GM_OPT_SCHEDULE, args.schedule)
+    if args.group != 16:
+        ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
     # ---- device-resident measurement: images registered before the timed region
     for k, im in enumerate(sc.images):
         ctx.put_image(k, im)
@@ -244,7 +251,9 @@ def main():
     off_h = torch.empty(len(pairs) + 1, dtype=torch.int64).pin_memory()
     rows_h = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
     h2d += len(gp) * 48
-    e2e_ctx = gm.Context(device=local, stream=stream, path=args.path)
+    e2e_ctx = gm.Context(device=local, stream=stream, path=args.path, cell_px=args.cell)
+    if args.group != 16:
+        e2e_ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
 
     def e2e_step():
         for k, (w, h, xy, scl, ds) in enumerate(pinned):
@@ -276,11 +285,11 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs": len(pairs), "images": len(sc.images), "keypoints_per_image": 8000,
-                       "band_px": 4.0, "ratio": 0.8, "cell_px": 16, "l2": "flushed between steps (512 MB write)",
+            "config": {"workload": WORKLOAD if not args.pairs else f"{WORKLOAD}_first{args.pairs}", "pairs": len(pairs), "images": len(sc.images), "keypoints_per_image": 8000,
+                       "band_px": 4.0, "ratio": 0.8, "cell_px": args.cell or 16, "group": args.group, "l2": "flushed between steps (512 MB write)",
                        "path": st["path_used"], "schedule": "persistent batch" if not args.schedule else "one pair per launch"},
             "comparisons_per_s": comps_per_s, "candidates_per_step": st["n_candidates"],
-            "examined_per_step": st["n_examined"], "matches_per_step": st["n_matches"],
+            "examined_per_step": st["n_examined"], "redecided_per_step": st["n_redecided"], "matches_per_step": st["n_matches"],
             "ms_match_kernel": ms_match,
             "e2e": {"value": world * len(pairs) / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -57,7 +57,7 @@ typedef enum {
 
 /* Distance paths (option GM_OPT_PATH).  All give identical results. */
 enum {
-    GM_PATH_AUTO = 0,       /* chosen per pair from the band density (autotuned thresholds) */
+    GM_PATH_AUTO = 0,       /* the fastest path for the batch (currently GM_PATH_TC) */
     GM_PATH_TC = 1,         /* tcgen05.mma kind::f16 tiles, integer-valued operands, f32 accumulation (exact) */
     GM_PATH_MMA = 2,        /* mma.sync m16n8k32 s8 x s8 -> s32 query groups */
     GM_PATH_SIMT = 3        /* one warp per query, dp4a on recentred int8 descriptors */
@@ -67,8 +67,9 @@ enum {
 enum {
     GM_OPT_PATH = 1,        /* GM_PATH_* */
     GM_OPT_SCHEDULE = 2,    /* 0 = whole batch per launch (default), 1 = one pair per launch (plain form) */
-    GM_OPT_CELL_PX = 3,     /* grid cell size of images put afterwards: 8, 16, 32, 64 or 128 px (default 16) */
-    GM_OPT_GRAPH = 4        /* 1 = replay batches through a captured CUDA graph when the shape repeats */
+    GM_OPT_CELL_PX = 3,     /* grid cell size of images put afterwards: 4, 8, 16, 32, 64 or 128 px (default 16) */
+    GM_OPT_GRAPH = 4,       /* 1 = replay batches through a captured CUDA graph when the shape repeats */
+    GM_OPT_MMA_GROUP = 5    /* queries per group of the mma path: 16 (default) or 32 */
 };
 
 typedef struct {
@@ -77,7 +78,7 @@ typedef struct {
     int32_t max_inflight;        /* serving: batches that may be on the device at once (>= 1; 0 = 2) */
     void *cuda_stream;           /* cudaStream_t for synchronous calls, or NULL for the context's own stream */
     int32_t path;                /* GM_PATH_* */
-    int32_t cell_px;             /* grid cell size in px (power of two, 8..128); 0 = 16 */
+    int32_t cell_px;             /* grid cell size in px (power of two, 4..128); 0 = 16 */
     const char *tuner_cache;     /* reserved (may be NULL) */
 } gm_config;
 
@@ -102,6 +103,7 @@ typedef struct {
     float ms_match;              /* device time of the band-walk / distance / top-2 kernel(s) */
     int32_t path_used;           /* GM_PATH_* of the distance kernel that ran */
     int32_t kernel_launches;     /* kernels launched by the call */
+    int64_t n_device_errors;     /* device-side bounded waits that ran out (the call then fails with TIMEOUT) */
 } gm_stats;
 
 /* Creates a context on cfg->device.  *out receives the handle.  Errors: GM_ERR_INVALID (null pointer, bad

@@ -163,6 +163,55 @@ gm_status prepare_pair(gm_ctx *ctx, const gm_pair &pr, int64_t k, PairDev &pd)
     return GM_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time dependency on libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Descriptor rows: fp16 [n][128], box 64 x 1 (128 bytes, 128-byte swizzle).  Records: int32 [n + 1][4], box 4 x 1.
+gm_status encode_maps(const ImageDev &dev, TmaMaps &maps)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const cuuint32_t estride[2] = {1, 1};
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)kDim, (cuuint64_t)dev.n};
+        const cuuint64_t strides[1] = {(cuuint64_t)kDim * 2};
+        const cuuint32_t box[2] = {64, 1};
+        if (enc(&maps.desc, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<uint16_t *>(dev.desc_h), dims, strides, box,
+                estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled failed (descriptor rows)");
+    }
+    const cuuint64_t rdims[2] = {4, (cuuint64_t)dev.n + 1};
+    const cuuint64_t rstrides[1] = {16};
+    const cuuint32_t rbox[2] = {4, 1};
+    if (enc(&maps.rec, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, const_cast<int4 *>(dev.rec), rdims, rstrides, rbox, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&maps.rec_r, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, const_cast<int4 *>(dev.rec_r), rdims, rstrides, rbox, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled failed (records)");
+    return GM_OK;
+}
+
 gm_status engine_plan(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs)
 {
     ws.pd.resize(n_pairs);
@@ -198,12 +247,22 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     if ((st = ensure_host(ws.h_tab, tab_bytes)) != GM_OK) return st;
     if ((st = ensure_host(ws.h_off, sizeof(int64_t) * (P + 1) + sizeof(BatchCounters) * 64)) != GM_OK) return st;
 
+    // distance path and work-item size
+    int path = ctx->path == GM_PATH_AUTO ? GM_PATH_TC : ctx->path;
+    if (path == GM_PATH_TC) {   // the tcgen05 kernel's run table holds match_tc_max_grid_lines() grid lines
+        for (const PairDev &pd : ws.pd) {
+            const ImageDev &B = ctx->slots[pd.b]->dev;
+            if (std::max(B.gx, B.gy) > match_tc_max_grid_lines()) { path = GM_PATH_MMA; break; }
+        }
+    }
+    const int mt = ctx->mma_mt;
+    const int qpi = path == GM_PATH_SIMT ? kQueriesPerItem : path == GM_PATH_TC ? kTcQueriesPerItem : 16 * mt;
+
     char *hs = static_cast<char *>(ws.h_tab.p);
     std::memcpy(hs, ws.pd.data(), sizeof(PairDev) * P);
     int64_t *h_item_off = reinterpret_cast<int64_t *>(hs + pair_bytes);
     h_item_off[0] = 0;
-    for (int32_t k = 0; k < P; ++k)
-        h_item_off[k + 1] = h_item_off[k] + (ws.pd[k].n_a + kQueriesPerItem - 1) / kQueriesPerItem;
+    for (int32_t k = 0; k < P; ++k) h_item_off[k + 1] = h_item_off[k] + (ws.pd[k].n_a + qpi - 1) / qpi;
 
     char *ds = static_cast<char *>(ws.d_tab.p);
     const PairDev *d_pairs = reinterpret_cast<const PairDev *>(ds);
@@ -217,7 +276,17 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     int32_t *rows = rows_dst ? rows_dst : static_cast<int32_t *>(ws.d_rows.p);
     cudaStream_t s = ws.stream;
     if (ctx->num_sms <= 0) ctx->num_sms = 1;
-    const int32_t grid = ctx->num_sms * match_simt_blocks_per_sm();
+    const int bps = path == GM_PATH_SIMT ? match_simt_blocks_per_sm()
+                    : path == GM_PATH_TC ? match_tc_blocks_per_sm() : match_mma_blocks_per_sm(mt);
+    const int32_t grid = ctx->num_sms * bps;
+    auto launch_match = [&](int64_t i0, int64_t i1, int32_t gsz) -> cudaError_t {
+        if (path == GM_PATH_SIMT)
+            return launch_match_simt(imgs, d_pairs, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
+        if (path == GM_PATH_TC)
+            return launch_match_tc(imgs, d_pairs, static_cast<const TmaMaps *>(ctx->d_maps.p), d_item_off, P, qorder,
+                                   i0, i1, gsz > 0 ? gsz : ctx->num_sms, match_j, ctr, s);
+        return launch_match_mma(mt, imgs, d_pairs, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
+    };
 
     ws.launches = 0;
     GM_CUDA(cudaEventRecord(ws.ev[0], s));
@@ -228,16 +297,14 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
         GM_CUDA(cudaEventRecord(ws.ev[1], s));
         for (int32_t k = 0; k < P; ++k) {
             GM_CUDA(launch_order(imgs, d_pairs + k, 1, qorder, s));
-            GM_CUDA(launch_match_simt(imgs, d_pairs, d_item_off, P, qorder, h_item_off[k], h_item_off[k + 1], 0,
-                                      next, match_j, ctr, s));
+            GM_CUDA(launch_match(h_item_off[k], h_item_off[k + 1], 0));
             ws.launches += 1 + (h_item_off[k + 1] > h_item_off[k]);
         }
         GM_CUDA(cudaEventRecord(ws.ev[2], s));
     } else {
         GM_CUDA(launch_order(imgs, d_pairs, P, qorder, s));
         GM_CUDA(cudaEventRecord(ws.ev[1], s));
-        GM_CUDA(launch_match_simt(imgs, d_pairs, d_item_off, P, qorder, 0, h_item_off[P], grid, next, match_j, ctr,
-                                  s));
+        GM_CUDA(launch_match(0, h_item_off[P], grid));
         GM_CUDA(cudaEventRecord(ws.ev[2], s));
         ws.launches += 2;
     }
@@ -249,7 +316,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     BatchCounters *h_ctr = reinterpret_cast<BatchCounters *>(h_off + P + 1);
     GM_CUDA(cudaMemcpyAsync(h_off, d_off, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToHost, s));
     GM_CUDA(cudaMemcpyAsync(h_ctr, ctr, sizeof(BatchCounters) * 64, cudaMemcpyDeviceToHost, s));
-    ws.path_used = GM_PATH_SIMT;
+    ws.path_used = path;
     return GM_OK;
 }
 
@@ -267,6 +334,7 @@ void engine_stats(gm_ctx *ctx, Workspace &ws, gm_stats &S)
         S.n_redecided += (int64_t)h_ctr[k].redecided;
     }
     S.n_matches = h_off[P];
+    for (int k = 0; k < 64; ++k) S.n_device_errors += (int64_t)h_ctr[k].errors;
     cudaEventElapsedTime(&S.ms_device, ws.ev[0], ws.ev[3]);
     cudaEventElapsedTime(&S.ms_match, ws.ev[1], ws.ev[2]);
     S.path_used = ws.path_used;
@@ -289,7 +357,7 @@ gm_status gm_create(const gm_config *cfg, gm_ctx **out)
         int c = cfg->cell_px, sh = 0;
         while ((1 << sh) < c) ++sh;
         if ((1 << sh) != c || sh < kMinCellShift || sh > kMaxCellShift)
-            return fail(GM_ERR_INVALID, "gm_create: cell_px must be a power of two in [8, 128]");
+            return fail(GM_ERR_INVALID, "gm_create: cell_px must be a power of two in [4, 128]");
         cell_shift = sh;
     }
     int ndev = 0;
@@ -338,7 +406,8 @@ gm_status gm_destroy(gm_ctx *ctx)
     }
     ctx->images.clear();
     workspace_free(ctx, ctx->ws);
-    for (DevBuf *b : {&ctx->d_imgs, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap}) free_dev(ctx, *b);
+    for (DevBuf *b : {&ctx->d_imgs, &ctx->d_maps, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap})
+        free_dev(ctx, *b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return GM_OK;
@@ -361,10 +430,14 @@ gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value)
         int sh = 0;
         while ((1ll << sh) < value) ++sh;
         if ((1ll << sh) != value || sh < kMinCellShift || sh > kMaxCellShift)
-            return fail(GM_ERR_INVALID, "cell_px must be a power of two in [8, 128]");
+            return fail(GM_ERR_INVALID, "cell_px must be a power of two in [4, 128]");
         ctx->cell_shift = sh;
         return GM_OK;
     }
+    case GM_OPT_MMA_GROUP:
+        if (value != 16 && value != 32) return fail(GM_ERR_INVALID, "mma group must be 16 or 32 queries");
+        ctx->mma_mt = (int32_t)(value / 16);
+        return GM_OK;
     case GM_OPT_GRAPH:
         if (value < 0 || value > 1) return fail(GM_ERR_INVALID, "bad graph flag");
         ctx->graph = (int32_t)value;
@@ -389,11 +462,11 @@ gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t hei
     const int64_t m = (int64_t)gx * gy;
     if (m + 2 > INT32_MAX / 4) return fail(GM_ERR_INVALID, "gm_image_put: grid too large");
     const size_t N = (size_t)n;
-    // one block: xy, perm, inv_perm, desc, norm, col_off, xy_r, idx_r, row_off, desc_h, scale
-    size_t sz[11] = {8 * N, 4 * N, 4 * N, 128 * N, 4 * N, 4 * (size_t)(m + 2), 8 * N, 4 * N, 4 * (size_t)(m + 2),
-                     256 * N, 4 * N};
-    size_t offs[11], tot = 0;
-    for (int k = 0; k < 11; ++k) {
+    // one block: xy, perm, inv_perm, desc, norm, col_off, xy_r, idx_r, row_off, desc_h, scale, norm256, rec, rec_r
+    size_t sz[14] = {8 * N, 4 * N, 4 * N, 128 * N, 4 * N, 4 * (size_t)(m + 2), 8 * N, 4 * N, 4 * (size_t)(m + 2),
+                     256 * N, 4 * N, 4 * N, 16 * (N + 1), 16 * (N + 1)};
+    size_t offs[14], tot = 0;
+    for (int k = 0; k < 14; ++k) {
         offs[k] = tot;
         tot += align_up(std::max<size_t>(sz[k], 1), 256);
     }
@@ -448,12 +521,16 @@ gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t hei
     dev.row_off = reinterpret_cast<int32_t *>(bp + offs[8]);
     dev.desc_h = reinterpret_cast<uint16_t *>(bp + offs[9]);
     float *d_scale = reinterpret_cast<float *>(bp + offs[10]);
+    dev.norm256 = reinterpret_cast<int32_t *>(bp + offs[11]);
+    dev.rec = reinterpret_cast<int4 *>(bp + offs[12]);
+    dev.rec_r = reinterpret_cast<int4 *>(bp + offs[13]);
     cudaError_t e = launch_bucket_build(raw_xy, raw_desc, n, width, height, sh, gx, gy, const_cast<float2 *>(dev.xy),
                                         const_cast<int32_t *>(dev.perm), const_cast<int32_t *>(dev.inv_perm),
                                         const_cast<int8_t *>(dev.desc), const_cast<int32_t *>(dev.norm),
-                                        const_cast<int32_t *>(dev.col_off), const_cast<float2 *>(dev.xy_r),
+                                        const_cast<int32_t *>(dev.norm256), const_cast<int32_t *>(dev.col_off), const_cast<float2 *>(dev.xy_r),
                                         const_cast<int32_t *>(dev.idx_r), const_cast<int32_t *>(dev.row_off),
-                                        const_cast<uint16_t *>(dev.desc_h), work, s);
+                                        const_cast<uint16_t *>(dev.desc_h), const_cast<int4 *>(dev.rec),
+                                        const_cast<int4 *>(dev.rec_r), work, s);
     if (e == cudaSuccess && n > 0 && scale)
         e = cudaMemcpyAsync(d_scale, scale, 4 * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
@@ -509,7 +586,36 @@ gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t hei
     }
     GM_CUDA(cudaMemcpyAsync(static_cast<ImageDev *>(ctx->d_imgs.p) + img->slot, &img->dev, sizeof(ImageDev),
                             cudaMemcpyHostToDevice, s));
-    // the staged inputs and the image table entry are read asynchronously: finish before returning
+    // TMA descriptors of the image (tcgen05 path)
+    {
+        const size_t need_maps = sizeof(TmaMaps) * ctx->slots.size();
+        if (ctx->d_maps.bytes < need_maps) {
+            DevBuf nb;
+            const size_t cap = align_up(std::max(need_maps * 2, (size_t)(sizeof(TmaMaps) * 16)), 256);
+            if (cudaMalloc(&nb.p, cap) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(GM_ERR_NOMEM, "gm_image_put: TMA descriptor table allocation failed");
+            }
+            nb.bytes = cap;
+            if (ctx->d_maps.p) {
+                cudaMemcpyAsync(nb.p, ctx->d_maps.p, ctx->d_maps.bytes, cudaMemcpyDeviceToDevice, s);
+                cudaStreamSynchronize(s);
+            }
+            free_dev(ctx, ctx->d_maps);
+            ctx->d_maps = nb;
+            ctx->bytes_work += cap;
+        }
+        TmaMaps maps;
+        std::memset(&maps, 0, sizeof(maps));
+        if (n > 0) {
+            gm_status ms = encode_maps(dev, maps);
+            if (ms != GM_OK) return ms;
+        }
+        img->maps = maps;
+        GM_CUDA(cudaMemcpyAsync(static_cast<TmaMaps *>(ctx->d_maps.p) + img->slot, &img->maps, sizeof(TmaMaps),
+                                cudaMemcpyHostToDevice, s));
+    }
+    // the staged inputs and the table entries are read asynchronously: finish before returning
     GM_CUDA(cudaStreamSynchronize(s));
     return GM_OK;
 }
@@ -552,6 +658,8 @@ gm_status gm_match_pairs(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int
     if ((st = engine_launch(ctx, ws, nullptr)) != GM_OK) return st;
     GM_CUDA(cudaStreamSynchronize(ws.stream));
     engine_stats(ctx, ws, ctx->stats);
+    if (ctx->stats.n_device_errors)
+        return fail(GM_ERR_TIMEOUT, "gm_match_pairs: %lld device-side waits ran out", (long long)ctx->stats.n_device_errors);
     const int64_t *h_off = static_cast<const int64_t *>(ws.h_off.p);
     const int64_t total = h_off[n_pairs];
     *n_written = total;

@@ -80,6 +80,13 @@ __device__ __forceinline__ bool band_exact(const float F[9], float x, float y, f
     return fabs(s) <= thr;
 }
 
+// Out-of-line copy of band_exact for unrolled epilogues: the rare FP64 re-decision stays one call instead of
+// being inlined at every element (which would flood the instruction cache).
+static __device__ __noinline__ bool band_exact_call(const float *F, float x, float y, float d, float xp, float yp)
+{
+    return band_exact(F, x, y, d, xp, yp);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;

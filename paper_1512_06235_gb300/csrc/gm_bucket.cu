@@ -126,7 +126,7 @@ __global__ void bucket_scatter_kernel(const float2 *__restrict__ xy_raw, int32_t
 // One warp per sorted row: recentred int8 copy, squared norm and fp16 copy of the descriptor.
 __global__ void desc_permute_kernel(const uint8_t *__restrict__ desc_raw, const int32_t *__restrict__ perm,
                                     int32_t n, int8_t *__restrict__ desc, int32_t *__restrict__ norm,
-                                    uint16_t *__restrict__ desc_h)
+                                    int32_t *__restrict__ norm256, uint16_t *__restrict__ desc_h)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -146,8 +146,31 @@ __global__ void desc_permute_kernel(const uint8_t *__restrict__ desc_raw, const 
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
-    if (lane == 0) norm[warp] = sq;
+    if (lane == 0) {
+        norm[warp] = sq;
+        norm256[warp] = sq * 256;
+    }
     if (desc_h) reinterpret_cast<uint2 *>(desc_h + (int64_t)warp * kDim)[lane] = make_uint2(h01, h23);
+}
+
+// Point records for the tensor-core path: (x, y, |b'|^2 * 256, column-major position) in column-major and in
+// row-major order, each followed by a sentinel whose NaN coordinates fail every band test.
+__global__ void records_kernel(const float2 *__restrict__ xy, const float2 *__restrict__ xy_r,
+                               const int32_t *__restrict__ idx_r, const int32_t *__restrict__ norm256, int32_t n,
+                               int4 *__restrict__ rec, int4 *__restrict__ rec_r)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    if (i == n) {
+        const int nan = 0x7fc00000;
+        rec[n] = make_int4(nan, nan, 0, 0);
+        rec_r[n] = make_int4(nan, nan, 0, 0);
+        return;
+    }
+    const float2 p = xy[i], q = xy_r[i];
+    const int j = idx_r[i];
+    rec[i] = make_int4(__float_as_int(p.x), __float_as_int(p.y), norm256[i], i);
+    rec_r[i] = make_int4(__float_as_int(q.x), __float_as_int(q.y), norm256[j], j);
 }
 
 }  // namespace
@@ -169,8 +192,9 @@ cudaError_t launch_bucket_count(const float2 *xy_raw, int32_t n, int32_t width, 
 
 cudaError_t launch_bucket_build(const float2 *xy_raw, const uint8_t *desc_raw, int32_t n, int32_t width,
                                 int32_t height, int32_t cell_shift, int32_t gx, int32_t gy, float2 *xy, int32_t *perm,
-                                int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *col_off, float2 *xy_r,
-                                int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int32_t *work, cudaStream_t st)
+                                int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *norm256, int32_t *col_off,
+                                float2 *xy_r, int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int4 *rec,
+                                int4 *rec_r, int32_t *work, cudaStream_t st)
 {
     // col_off / row_off hold gx*gy + 2 entries: the cells, the out-of-image cell, the total
     const int m = gx * gy + 1;
@@ -187,8 +211,9 @@ cudaError_t launch_bucket_build(const float2 *xy_raw, const uint8_t *desc_raw, i
     if (n > 0) {
         bucket_scatter_kernel<<<1, 32, 0, st>>>(xy_raw, n, (float)width, (float)height, inv_cs, gx, gy, cnt_col,
                                                 cnt_row, xy, perm, inv_perm, xy_r, idx_r);
-        desc_permute_kernel<<<(n + 7) / 8, 256, 0, st>>>(desc_raw, perm, n, desc, norm, desc_h);
+        desc_permute_kernel<<<(n + 7) / 8, 256, 0, st>>>(desc_raw, perm, n, desc, norm, norm256, desc_h);
     }
+    records_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(xy, xy_r, idx_r, norm256, n, rec, rec_r);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct ImageSlot {
     int32_t id = -1;
     int32_t slot = -1;
     ImageDev dev{};
+    TmaMaps maps{};
     void *block = nullptr;
     size_t bytes = 0;
 };
@@ -77,10 +78,12 @@ struct gm_ctx {
     int32_t graph = 0;
     int32_t max_inflight = 2;
     int32_t num_sms = 0;
+    int32_t mma_mt = 1;             // m16 tiles per query group of the tensor-core path
 
     std::unordered_map<int32_t, gm::ImageSlot *> images;
     std::vector<gm::ImageSlot *> slots;
     gm::DevBuf d_imgs;              // ImageDev table indexed by slot
+    gm::DevBuf d_maps;              // TmaMaps table indexed by slot (tcgen05 path)
     size_t bytes_images = 0;
     size_t bytes_work = 0;          // every DevBuf of the context and of the server slots
 

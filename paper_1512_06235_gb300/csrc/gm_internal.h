@@ -8,13 +8,14 @@
 //   only coordinates and the column-major position, the descriptors exist once, in column-major order.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace gm {
 
 constexpr int kDim = 128;           // SIFT descriptor length (bytes)
 constexpr int kMaxCellShift = 7;    // 128 px cells
-constexpr int kMinCellShift = 3;    // 8 px cells
+constexpr int kMinCellShift = 2;    // 4 px cells
 constexpr int kQueriesPerItem = 8;  // queries per work item (SIMT path: one warp each)
 
 struct ImageDev {
@@ -26,11 +27,22 @@ struct ImageDev {
     const int32_t *inv_perm;        // [n] original index -> column-major position
     const int8_t *desc;             // [n][128] column-major order, recentred b - 128 (bit pattern b ^ 0x80)
     const int32_t *norm;            // [n] sum_k (b_k - 128)^2
+    const int32_t *norm256;         // [n] norm * 256 (the tensor-core epilogue's key term)
     const int32_t *col_off;         // [gx*gy + 2]; cell (cx, cy) -> cx*gy + cy (then out-of-image cell, total)
     const float2 *xy_r;             // [n] row-major order
     const int32_t *idx_r;           // [n] row-major position -> column-major position
     const int32_t *row_off;         // [gx*gy + 2]; cell (cx, cy) -> cy*gx + cx
     const uint16_t *desc_h;         // [n][128] fp16 bits of (b - 128), column-major order (tensor-core path)
+    const int4 *rec;                // [n + 1] (x, y, norm * 256, position) column-major; [n] = NaN sentinel
+    const int4 *rec_r;              // [n + 1] the same in row-major order (position = column-major position)
+};
+
+// TMA descriptors of one resident image (tcgen05 path): fp16 descriptor rows (box 64 x 1, 128-byte swizzle) and
+// the two record arrays (box 4 x 1 int32).  CUtensorMap carries the 64-byte alignment TMA requires.
+struct TmaMaps {
+    CUtensorMap desc;
+    CUtensorMap rec;
+    CUtensorMap rec_r;
 };
 
 struct PairDev {
@@ -60,8 +72,9 @@ cudaError_t launch_bucket_count(const float2 *xy_raw, int32_t n, int32_t width, 
                                 int32_t gx, int32_t gy, int32_t *work, unsigned long long *bad, cudaStream_t st);
 cudaError_t launch_bucket_build(const float2 *xy_raw, const uint8_t *desc_raw, int32_t n, int32_t width,
                                 int32_t height, int32_t cell_shift, int32_t gx, int32_t gy, float2 *xy, int32_t *perm,
-                                int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *col_off, float2 *xy_r,
-                                int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int32_t *work, cudaStream_t st);
+                                int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *norm256, int32_t *col_off,
+                                float2 *xy_r, int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int4 *rec,
+                                int4 *rec_r, int32_t *work, cudaStream_t st);
 
 // Query ordering (App. A Step 2 as an order only): per pair, sorts A's queries by the position of their
 // epipolar line in B.  qorder[qoff + k] = column-major position in A of the k-th query.
@@ -76,6 +89,22 @@ cudaError_t launch_match_simt(const ImageDev *imgs, const PairDev *pairs, const 
                               const int32_t *qorder, int64_t item_begin, int64_t item_end, int32_t grid,
                               int32_t *next, int32_t *match_j, BatchCounters *ctr, cudaStream_t st);
 int match_simt_blocks_per_sm();
+
+// Tensor-core matching path (mma.sync s8): groups of 16*mt sorted queries (mt = 1 or 2) per work item.
+cudaError_t launch_match_mma(int mt, const ImageDev *imgs, const PairDev *pairs, const int64_t *item_off,
+                             int32_t n_pairs, const int32_t *qorder, int64_t item_begin, int64_t item_end,
+                             int32_t grid, int32_t *next, int32_t *match_j, BatchCounters *ctr, cudaStream_t st);
+int match_mma_blocks_per_sm(int mt);
+
+// tcgen05 matching path (warp-specialised, TMA gather4 + tcgen05.mma): groups of kTcQueriesPerItem sorted
+// queries per work item, one persistent CTA per SM (grid CTAs take items item_begin + b, + grid, ...).
+// Every image of the batch must have max(gx, gy) <= match_tc_max_grid_lines().
+cudaError_t launch_match_tc(const ImageDev *imgs, const PairDev *pairs, const TmaMaps *maps, const int64_t *item_off,
+                            int32_t n_pairs, const int32_t *qorder, int64_t item_begin, int64_t item_end, int32_t grid,
+                            int32_t *match_j, BatchCounters *ctr, cudaStream_t st);
+int match_tc_blocks_per_sm();
+int match_tc_max_grid_lines();
+constexpr int kTcQueriesPerItem = 128;
 
 // Output assembly: counts[p] = matches of pair p, pair_off = exclusive scan (pair_off[n_pairs] = total), then
 // rows (i, j) sorted by i into matches.

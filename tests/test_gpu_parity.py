@@ -31,11 +31,16 @@ def _oracle_rows(sc, pr):
     return oracle.matches_from_match_j(mj), nc
 
 
-def _gpu_rows(gm, sc, pairs=None, cell_px=0, path=0, schedule=0):
+PATHS = [("tc", 1, 16), ("simt", 3, 16), ("mma16", 2, 16), ("mma32", 2, 32)]
+
+
+def _gpu_rows(gm, sc, pairs=None, cell_px=0, path=0, schedule=0, group=16):
     pairs = sc.pairs if pairs is None else pairs
     with gm.Context(device=0, cell_px=cell_px, path=path) as ctx:
         if schedule:
             ctx.set_option(gm.GM_OPT_SCHEDULE, schedule)
+        if group != 16:
+            ctx.set_option(gm.GM_OPT_MMA_GROUP, group)
         used = sorted({p.a for p in pairs} | {p.b for p in pairs})
         for k in used:
             ctx.put_image(k, sc.images[k])
@@ -44,19 +49,21 @@ def _gpu_rows(gm, sc, pairs=None, cell_px=0, path=0, schedule=0):
     return gm.split_matches(off, m), st
 
 
-def test_two_view_bit_exact(gm, two_view_scene):
+@pytest.mark.parametrize("path", PATHS, ids=lambda p: p[0])
+def test_two_view_bit_exact(gm, two_view_scene, path):
     sc = two_view_scene
-    rows, st = _gpu_rows(gm, sc)
+    rows, st = _gpu_rows(gm, sc, path=path[1], group=path[2])
     want, nc = _oracle_rows(sc, sc.pairs[0])
     np.testing.assert_array_equal(rows[0], want)
     assert st["n_candidates"] == nc
     assert st["n_examined"] >= nc
 
 
-@pytest.mark.parametrize("cell_px", [8, 16, 64, 128])
-def test_two_view_cell_sizes(gm, two_view_scene, cell_px):
+@pytest.mark.parametrize("path", PATHS, ids=lambda p: p[0])
+@pytest.mark.parametrize("cell_px", [4, 8, 16, 64, 128])
+def test_two_view_cell_sizes(gm, two_view_scene, cell_px, path):
     sc = two_view_scene
-    rows, st = _gpu_rows(gm, sc, cell_px=cell_px)
+    rows, st = _gpu_rows(gm, sc, cell_px=cell_px, path=path[1], group=path[2])
     want, nc = _oracle_rows(sc, sc.pairs[0])
     np.testing.assert_array_equal(rows[0], want)
     assert st["n_candidates"] == nc
@@ -76,10 +83,11 @@ def _random_batch(seeds, d_values, levels=256, n_a=300, n_b=411):
     return scenes.Scene("random_batch", images, pairs)
 
 
+@pytest.mark.parametrize("path", PATHS, ids=lambda p: p[0])
 @pytest.mark.parametrize("levels", [256, 4, 2])
-def test_random_pairs_batched(gm, levels):
+def test_random_pairs_batched(gm, levels, path):
     sc = _random_batch(range(3), [0.0, 1.5, 4.0, 13.0, math.inf], levels=levels)
-    rows, st = _gpu_rows(gm, sc)
+    rows, st = _gpu_rows(gm, sc, path=path[1], group=path[2])
     total = 0
     for k, pr in enumerate(sc.pairs):
         want, nc = _oracle_rows(sc, pr)
@@ -115,10 +123,11 @@ def test_band_golden_on_gpu(gm, case):
     np.testing.assert_array_equal(cand, np.nonzero(case["expected"])[0])
 
 
+@pytest.mark.parametrize("path", PATHS, ids=lambda p: p[0])
 @pytest.mark.parametrize("case", golden.ratio_cases(), ids=lambda c: c["name"])
-def test_ratio_golden_on_gpu(gm, case):
+def test_ratio_golden_on_gpu(gm, case, path):
     n = case["bd"].shape[0]
-    with gm.Context(device=0) as ctx:
+    with gm.Context(device=0, path=path[1]) as ctx:
         ctx.put_image(0, width=64, height=64, xy=np.array([[5.0, 5.0]], np.float32), scale=None,
                       desc=case["qd"][None])
         ctx.put_image(1, width=64, height=64, xy=np.full((n, 2), 10.0, np.float32).reshape(-1, 2), scale=None,
@@ -128,7 +137,8 @@ def test_ratio_golden_on_gpu(gm, case):
     np.testing.assert_array_equal(m.reshape(-1, 2), np.array(want, np.int32).reshape(-1, 2))
 
 
-def test_edge_cases(gm):
+@pytest.mark.parametrize("path", PATHS, ids=lambda p: p[0])
+def test_edge_cases(gm, path):
     rng = np.random.default_rng(5)
     W, H = 640, 480
     xy = np.stack([rng.uniform(0, W, 500), rng.uniform(0, H, 500)], 1).astype(np.float32)
@@ -149,7 +159,7 @@ def test_edge_cases(gm):
              scenes.Pair(0, 0, F_vert, 3.0), scenes.Pair(0, 0, F_zero, 5.0), scenes.Pair(0, 0, F_zero, math.inf),
              scenes.Pair(2, 0, F_gen, 1e6)]
     sc = scenes.Scene("edges", images, pairs)
-    rows, _ = _gpu_rows(gm, sc)
+    rows, _ = _gpu_rows(gm, sc, path=path[1], group=path[2])
     for k, pr in enumerate(pairs):
         want, _ = _oracle_rows(sc, pr)
         np.testing.assert_array_equal(rows[k], want, err_msg=f"pair {k}")
@@ -180,7 +190,8 @@ def test_invalid_inputs(gm):
 
 
 def test_facade_full_batch_sampled(gm, facade_scene):
-    """Full-size batch in the benchmark's launch configuration; 24 pairs spread over it checked exactly."""
+    """Full-size batch in the benchmark's launch configuration; 24 pairs spread over it checked exactly; the other
+    paths and the per-pair launch schedule give identical lists over the whole batch."""
     sc = facade_scene
     rows, st = _gpu_rows(gm, sc)
     sample = list(range(0, len(sc.pairs), 50))
@@ -194,6 +205,11 @@ def test_facade_full_batch_sampled(gm, facade_scene):
     for k in range(len(sc.pairs)):
         np.testing.assert_array_equal(rows1[k], rows[k])
     assert st1["n_candidates"] == st["n_candidates"]
+    for name, path, group in PATHS:
+        rows2, st2 = _gpu_rows(gm, sc, path=path, group=group)
+        assert st2["n_candidates"] == st["n_candidates"], name
+        for k in range(len(sc.pairs)):
+            np.testing.assert_array_equal(rows2[k], rows[k], err_msg=f"{name} pair {k}")
 
 
 def test_serving_alone_equals_mix(gm, facade_scene):
