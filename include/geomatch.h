@@ -69,7 +69,8 @@ enum {
     GM_OPT_SCHEDULE = 2,    /* 0 = whole batch per launch (default), 1 = one pair per launch (plain form) */
     GM_OPT_CELL_PX = 3,     /* grid cell size of images put afterwards: 4, 8, 16, 32, 64 or 128 px (default 16) */
     GM_OPT_GRAPH = 4,       /* 1 = replay batches through a captured CUDA graph when the shape repeats */
-    GM_OPT_MMA_GROUP = 5    /* queries per group of the mma path: 16 (default) or 32 */
+    GM_OPT_MMA_GROUP = 5,   /* queries per group of the mma path: 16 (default) or 32 */
+    GM_OPT_STREAM_CAP = 6   /* entries of the tcgen05 path's candidate-stream buffer (grown automatically) */
 };
 
 typedef struct {

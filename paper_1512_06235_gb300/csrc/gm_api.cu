@@ -116,7 +116,8 @@ gm_status workspace_init(Workspace &ws, cudaStream_t stream)
 void workspace_free(gm_ctx *ctx, Workspace &ws)
 {
     if (ws.stream) cudaStreamSynchronize(ws.stream);
-    for (DevBuf *b : {&ws.d_tab, &ws.d_qorder, &ws.d_matchj, &ws.d_counts, &ws.d_off, &ws.d_rows, &ws.d_ctr, &ws.d_next})
+    for (DevBuf *b : {&ws.d_tab, &ws.d_qorder, &ws.d_matchj, &ws.d_counts, &ws.d_off, &ws.d_rows, &ws.d_ctr, &ws.d_next,
+                      &ws.d_grec, &ws.d_grows, &ws.d_stream})
         free_dev(ctx, *b);
     for (HostBuf *b : {&ws.h_tab, &ws.h_off, &ws.h_rows}) free_host(*b);
     if (ws.gexec) cudaGraphExecDestroy(ws.gexec);
@@ -184,30 +185,31 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// Descriptor rows: fp16 [n][128], box 64 x 1 (128 bytes, 128-byte swizzle).  Records: int32 [n + 1][4], box 4 x 1.
+// Descriptor rows: fp16 [n][128], box 64 x 64 (128-byte swizzle).  Records: [n + 1][4] read as FP32, box 4 x 64,
+// out-of-range rows filled with NaN.
 gm_status encode_maps(const ImageDev &dev, TmaMaps &maps)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     const cuuint32_t estride[2] = {1, 1};
-    {
-        const cuuint64_t dims[2] = {(cuuint64_t)kDim, (cuuint64_t)dev.n};
-        const cuuint64_t strides[1] = {(cuuint64_t)kDim * 2};
-        const cuuint32_t box[2] = {64, 1};
-        if (enc(&maps.desc, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<uint16_t *>(dev.desc_h), dims, strides, box,
-                estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled failed (descriptor rows)");
-    }
+    const cuuint64_t dims[2] = {(cuuint64_t)kDim, (cuuint64_t)dev.n};
+    const cuuint64_t strides[1] = {(cuuint64_t)kDim * 2};
+    const cuuint32_t box[2] = {64, 64};
+    if (enc(&maps.desc_tile, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<uint16_t *>(dev.desc_h), dims, strides, box,
+            estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled failed (descriptor tiles)");
+    const cuuint32_t rowbox[2] = {64, 1};
+    if (enc(&maps.desc_row, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<uint16_t *>(dev.desc_h), dims, strides,
+            rowbox, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled failed (descriptor rows)");
     const cuuint64_t rdims[2] = {4, (cuuint64_t)dev.n + 1};
     const cuuint64_t rstrides[1] = {16};
-    const cuuint32_t rbox[2] = {4, 1};
-    if (enc(&maps.rec, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, const_cast<int4 *>(dev.rec), rdims, rstrides, rbox, estride,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        enc(&maps.rec_r, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, const_cast<int4 *>(dev.rec_r), rdims, rstrides, rbox, estride,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    const cuuint32_t rbox[2] = {4, 64};
+    if (enc(&maps.rec_tile, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<int4 *>(dev.rec), rdims, rstrides, rbox,
+            estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA) != CUDA_SUCCESS)
         return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled failed (records)");
     return GM_OK;
 }
@@ -245,7 +247,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
         return st;
     if ((st = ensure_dev(ctx, ws.d_ctr, sizeof(BatchCounters) * 64 + 256)) != GM_OK) return st;
     if ((st = ensure_host(ws.h_tab, tab_bytes)) != GM_OK) return st;
-    if ((st = ensure_host(ws.h_off, sizeof(int64_t) * (P + 1) + sizeof(BatchCounters) * 64)) != GM_OK) return st;
+    if ((st = ensure_host(ws.h_off, sizeof(int64_t) * (P + 1) + sizeof(BatchCounters) * 64 + 16)) != GM_OK) return st;
 
     // distance path and work-item size
     int path = ctx->path == GM_PATH_AUTO ? GM_PATH_TC : ctx->path;
@@ -271,10 +273,21 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     int32_t *match_j = static_cast<int32_t *>(ws.d_matchj.p);
     BatchCounters *ctr = static_cast<BatchCounters *>(ws.d_ctr.p);
     int32_t *next = reinterpret_cast<int32_t *>(ctr + 64);
+    unsigned long long *stream_used = reinterpret_cast<unsigned long long *>(ctr + 64) + 1;
     const ImageDev *imgs = static_cast<const ImageDev *>(ctx->d_imgs.p);
     int64_t *d_off = static_cast<int64_t *>(ws.d_off.p);
     int32_t *rows = rows_dst ? rows_dst : static_cast<int32_t *>(ws.d_rows.p);
     cudaStream_t s = ws.stream;
+    const int64_t n_items = h_item_off[P];
+    if (path == GM_PATH_TC) {
+        if ((st = ensure_dev(ctx, ws.d_grec, sizeof(GroupDesc) * std::max<int64_t>(n_items, 1))) != GM_OK) return st;
+        if ((st = ensure_dev(ctx, ws.d_grows, sizeof(int32_t) * kTcQueriesPerItem * std::max<int64_t>(n_items, 1))) !=
+            GM_OK)
+            return st;
+        if (ws.stream_cap == 0) ws.stream_cap = std::max<int64_t>(1 << 22, 8 * Q);
+        if ((st = ensure_dev(ctx, ws.d_stream, sizeof(int32_t) * ws.stream_cap)) != GM_OK) return st;
+        ws.stream_cap = (int64_t)(ws.d_stream.bytes / sizeof(int32_t));
+    }
     if (ctx->num_sms <= 0) ctx->num_sms = 1;
     const int bps = path == GM_PATH_SIMT ? match_simt_blocks_per_sm()
                     : path == GM_PATH_TC ? match_tc_blocks_per_sm() : match_mma_blocks_per_sm(mt);
@@ -283,7 +296,9 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
         if (path == GM_PATH_SIMT)
             return launch_match_simt(imgs, d_pairs, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
         if (path == GM_PATH_TC)
-            return launch_match_tc(imgs, d_pairs, static_cast<const TmaMaps *>(ctx->d_maps.p), d_item_off, P, qorder,
+            return launch_match_tc(static_cast<const TmaMaps *>(ctx->d_maps.p),
+                                   static_cast<const GroupDesc *>(ws.d_grec.p),
+                                   static_cast<const int32_t *>(ws.d_grows.p), static_cast<const int32_t *>(ws.d_stream.p),
                                    i0, i1, gsz > 0 ? gsz : ctx->num_sms, match_j, ctr, s);
         return launch_match_mma(mt, imgs, d_pairs, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
     };
@@ -291,18 +306,30 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     ws.launches = 0;
     GM_CUDA(cudaEventRecord(ws.ev[0], s));
     GM_CUDA(cudaMemcpyAsync(ds, hs, tab_bytes, cudaMemcpyHostToDevice, s));
-    GM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(BatchCounters) * 64 + sizeof(int32_t), s));
+    GM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(BatchCounters) * 64 + 16, s));
     if (ctx->schedule == 1) {
         // plain form: every pair gets its own launches (one block per work item)
         GM_CUDA(cudaEventRecord(ws.ev[1], s));
         for (int32_t k = 0; k < P; ++k) {
             GM_CUDA(launch_order(imgs, d_pairs + k, 1, qorder, s));
+            if (path == GM_PATH_TC) {
+                GM_CUDA(launch_stream(imgs, d_pairs, d_item_off, P, qorder, h_item_off[k], h_item_off[k + 1],
+                                      static_cast<GroupDesc *>(ws.d_grec.p), static_cast<int32_t *>(ws.d_grows.p),
+                                      static_cast<int32_t *>(ws.d_stream.p), ws.stream_cap, stream_used, ctr, s));
+                ++ws.launches;
+            }
             GM_CUDA(launch_match(h_item_off[k], h_item_off[k + 1], 0));
             ws.launches += 1 + (h_item_off[k + 1] > h_item_off[k]);
         }
         GM_CUDA(cudaEventRecord(ws.ev[2], s));
     } else {
         GM_CUDA(launch_order(imgs, d_pairs, P, qorder, s));
+        if (path == GM_PATH_TC) {
+            GM_CUDA(launch_stream(imgs, d_pairs, d_item_off, P, qorder, 0, n_items, static_cast<GroupDesc *>(ws.d_grec.p),
+                                  static_cast<int32_t *>(ws.d_grows.p), static_cast<int32_t *>(ws.d_stream.p),
+                                  ws.stream_cap, stream_used, ctr, s));
+            ++ws.launches;
+        }
         GM_CUDA(cudaEventRecord(ws.ev[1], s));
         GM_CUDA(launch_match(0, h_item_off[P], grid));
         GM_CUDA(cudaEventRecord(ws.ev[2], s));
@@ -315,7 +342,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     int64_t *h_off = static_cast<int64_t *>(ws.h_off.p);
     BatchCounters *h_ctr = reinterpret_cast<BatchCounters *>(h_off + P + 1);
     GM_CUDA(cudaMemcpyAsync(h_off, d_off, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToHost, s));
-    GM_CUDA(cudaMemcpyAsync(h_ctr, ctr, sizeof(BatchCounters) * 64, cudaMemcpyDeviceToHost, s));
+    GM_CUDA(cudaMemcpyAsync(h_ctr, ctr, sizeof(BatchCounters) * 64 + 16, cudaMemcpyDeviceToHost, s));
     ws.path_used = path;
     return GM_OK;
 }
@@ -335,6 +362,9 @@ void engine_stats(gm_ctx *ctx, Workspace &ws, gm_stats &S)
     }
     S.n_matches = h_off[P];
     for (int k = 0; k < 64; ++k) S.n_device_errors += (int64_t)h_ctr[k].errors;
+    ws.overflow = 0;
+    for (int k = 0; k < 64; ++k) ws.overflow += (int64_t)h_ctr[k].overflow;
+    ws.stream_used = (int64_t)reinterpret_cast<const unsigned long long *>(h_ctr + 64)[1];
     cudaEventElapsedTime(&S.ms_device, ws.ev[0], ws.ev[3]);
     cudaEventElapsedTime(&S.ms_match, ws.ev[1], ws.ev[2]);
     S.path_used = ws.path_used;
@@ -438,6 +468,11 @@ gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value)
         if (value != 16 && value != 32) return fail(GM_ERR_INVALID, "mma group must be 16 or 32 queries");
         ctx->mma_mt = (int32_t)(value / 16);
         return GM_OK;
+    case GM_OPT_STREAM_CAP:
+        if (value < 1 || value > (int64_t)1 << 34) return fail(GM_ERR_INVALID, "bad stream capacity");
+        ctx->ws.stream_cap = value;
+        free_dev(ctx, ctx->ws.d_stream);
+        return GM_OK;
     case GM_OPT_GRAPH:
         if (value < 0 || value > 1) return fail(GM_ERR_INVALID, "bad graph flag");
         ctx->graph = (int32_t)value;
@@ -462,11 +497,11 @@ gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t hei
     const int64_t m = (int64_t)gx * gy;
     if (m + 2 > INT32_MAX / 4) return fail(GM_ERR_INVALID, "gm_image_put: grid too large");
     const size_t N = (size_t)n;
-    // one block: xy, perm, inv_perm, desc, norm, col_off, xy_r, idx_r, row_off, desc_h, scale, norm256, rec, rec_r
-    size_t sz[14] = {8 * N, 4 * N, 4 * N, 128 * N, 4 * N, 4 * (size_t)(m + 2), 8 * N, 4 * N, 4 * (size_t)(m + 2),
-                     256 * N, 4 * N, 4 * N, 16 * (N + 1), 16 * (N + 1)};
-    size_t offs[14], tot = 0;
-    for (int k = 0; k < 14; ++k) {
+    // one block: xy, perm, inv_perm, desc, norm, col_off, xy_r, idx_r, row_off, desc_h, scale, norm256, rec
+    size_t sz[13] = {8 * N, 4 * N, 4 * N, 128 * N, 4 * N, 4 * (size_t)(m + 2), 8 * N, 4 * N, 4 * (size_t)(m + 2),
+                     256 * N, 4 * N, 4 * N, 16 * (N + 1)};
+    size_t offs[13], tot = 0;
+    for (int k = 0; k < 13; ++k) {
         offs[k] = tot;
         tot += align_up(std::max<size_t>(sz[k], 1), 256);
     }
@@ -489,7 +524,9 @@ gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t hei
         raw_xy = reinterpret_cast<const float2 *>(sp);
         raw_desc = reinterpret_cast<const uint8_t *>(sp + xy_al);
     }
-    if ((st = ensure_dev(ctx, ctx->d_work, sizeof(int32_t) * 2 * (size_t)(m + 3))) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_work, sizeof(int32_t) * (2 * (size_t)(m + 3) + 2 * (size_t)(m / 1024 + 3))))
+        != GM_OK)
+        return st;
     if ((st = ensure_dev(ctx, ctx->d_bad, 256)) != GM_OK) return st;
     unsigned long long *d_bad = static_cast<unsigned long long *>(ctx->d_bad.p);
     int32_t *work = static_cast<int32_t *>(ctx->d_work.p);
@@ -523,14 +560,12 @@ gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t hei
     float *d_scale = reinterpret_cast<float *>(bp + offs[10]);
     dev.norm256 = reinterpret_cast<int32_t *>(bp + offs[11]);
     dev.rec = reinterpret_cast<int4 *>(bp + offs[12]);
-    dev.rec_r = reinterpret_cast<int4 *>(bp + offs[13]);
     cudaError_t e = launch_bucket_build(raw_xy, raw_desc, n, width, height, sh, gx, gy, const_cast<float2 *>(dev.xy),
                                         const_cast<int32_t *>(dev.perm), const_cast<int32_t *>(dev.inv_perm),
                                         const_cast<int8_t *>(dev.desc), const_cast<int32_t *>(dev.norm),
                                         const_cast<int32_t *>(dev.norm256), const_cast<int32_t *>(dev.col_off), const_cast<float2 *>(dev.xy_r),
                                         const_cast<int32_t *>(dev.idx_r), const_cast<int32_t *>(dev.row_off),
-                                        const_cast<uint16_t *>(dev.desc_h), const_cast<int4 *>(dev.rec),
-                                        const_cast<int4 *>(dev.rec_r), work, s);
+                                        const_cast<uint16_t *>(dev.desc_h), const_cast<int4 *>(dev.rec), work, s);
     if (e == cudaSuccess && n > 0 && scale)
         e = cudaMemcpyAsync(d_scale, scale, 4 * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
@@ -655,9 +690,14 @@ gm_status gm_match_pairs(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int
     }
     gm_status st = engine_plan(ctx, ws, n_pairs, pairs);
     if (st != GM_OK) return st;
-    if ((st = engine_launch(ctx, ws, nullptr)) != GM_OK) return st;
-    GM_CUDA(cudaStreamSynchronize(ws.stream));
-    engine_stats(ctx, ws, ctx->stats);
+    for (int attempt = 0;; ++attempt) {
+        if ((st = engine_launch(ctx, ws, nullptr)) != GM_OK) return st;
+        GM_CUDA(cudaStreamSynchronize(ws.stream));
+        engine_stats(ctx, ws, ctx->stats);
+        if (!ws.overflow) break;
+        if (attempt >= 2) return fail(GM_ERR_NOMEM, "gm_match_pairs: candidate stream buffer kept overflowing");
+        ws.stream_cap = ws.stream_used + ws.stream_used / 4 + 1024;   // grow to what the batch needed, then rerun
+    }
     if (ctx->stats.n_device_errors)
         return fail(GM_ERR_TIMEOUT, "gm_match_pairs: %lld device-side waits ran out", (long long)ctx->stats.n_device_errors);
     const int64_t *h_off = static_cast<const int64_t *>(ws.h_off.p);

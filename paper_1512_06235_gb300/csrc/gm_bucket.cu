@@ -1,11 +1,12 @@
 // gm_bucket.cu -- grid bucketing of one image (App. A Step 1: cell index per feature, sort by cell, prefix scan
 // of the cell counts gives each cell's start).  Done once per image; the result stays resident.
 //
-// A stable counting sort: histogram (atomics) -> exclusive scan -> scatter.  The scatter is stable (original
-// index order inside every cell) because one warp walks the keypoints in index order, 32 at a time, and ranks
-// equal cells inside each chunk with __match_any_sync.  Two layouts are built: column-major (cells of a grid
-// column contiguous) and row-major.  Descriptors are then copied in column-major order, recentred to int8
-// (b - 128, the bit pattern b ^ 0x80), with their squared norms and an fp16 copy for the tensor-core path.
+// A counting sort: histogram (atomics) -> exclusive scan (block-parallel, two passes) -> scatter (one thread per
+// keypoint, atomic cursor per cell).  The order inside a cell is whatever the atomics give: no result depends on
+// it (every band decision is per keypoint, and an accepted match has a unique nearest neighbour because ties are
+// rejected).  Two layouts are built: column-major (cells of a grid column contiguous) and row-major.  Descriptors
+// are then copied in column-major order, recentred to int8 (b - 128, the bit pattern b ^ 0x80), with their
+// squared norms, an fp16 copy and the point records of the tensor-core path.
 #include <cuda_fp16.h>
 
 #include <cstdint>
@@ -43,84 +44,100 @@ __global__ void bucket_count_kernel(const float2 *__restrict__ xy, int32_t n, fl
     atomicAdd(&cnt_row[crow], 1);
 }
 
-// Exclusive scan of m counts into off[0..m] (off[m] = total); one block of 1024 threads.
-__global__ void exclusive_scan_kernel(const int32_t *__restrict__ cnt, int32_t m, int32_t *__restrict__ off)
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ int block_incl_scan(int v, int32_t *wsum, int &total)
 {
-    __shared__ int32_t warp_sums[32];
-    __shared__ int32_t carry;
-    if (threadIdx.x == 0) carry = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, s);
+        if (lane >= s) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int base = 0; base < m; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const int v = i < m ? cnt[i] : 0;
-        int incl = v;
+    if (wid == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, s);
-            if (lane >= s) incl += t;
+            const int t = __shfl_up_sync(0xffffffffu, w, s);
+            if (lane >= s) w += t;
         }
-        if (lane == 31) warp_sums[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            int w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
-#pragma unroll
-            for (int s = 1; s < 32; s <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, w, s);
-                if (lane >= s) w += t;
-            }
-            warp_sums[lane] = w;   // inclusive over warps
-        }
-        __syncthreads();
-        const int before = (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
-        if (i < m) off[i] = before + incl - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = before + incl;
-        __syncthreads();
+        wsum[lane] = w;
     }
-    if (threadIdx.x == 0) off[m] = carry;
+    __syncthreads();
+    total = wsum[nw - 1];
+    return (wid > 0 ? wsum[wid - 1] : 0) + incl;
 }
 
-// Stable scatter by one warp: column-major first (perm, xy, colpos), then row-major (xy_r, idx_r).
-// cur_col / cur_row: copies of the offsets, used as per-cell cursors.
-__global__ void bucket_scatter_kernel(const float2 *__restrict__ xy_raw, int32_t n, float W, float H, float inv_cs,
-                                      int gx, int gy,
-                                      int32_t *cur_col, int32_t *cur_row, float2 *xy, int32_t *perm,
-                                      int32_t *colpos, float2 *xy_r, int32_t *idx_r)  // colpos = inverse perm
+// Pass 1: per block of kScanBlock counts, the local exclusive scan into off[] and the block total.
+__global__ void __launch_bounds__(kScanBlock) scan_local_kernel(const int32_t *__restrict__ cnt, int32_t m,
+                                                                 int32_t *__restrict__ off, int32_t *__restrict__ bsum)
 {
-    const int lane = threadIdx.x & 31;
-    for (int pass = 0; pass < 2; ++pass) {
-        int32_t *cur = pass == 0 ? cur_col : cur_row;
-        for (int base = 0; base < n; base += 32) {
-            const int i = base + lane;
-            const bool valid = i < n;
-            const unsigned act = __ballot_sync(0xffffffffu, valid);
-            if (!valid) continue;
-            const float2 p = xy_raw[i];
-            int ccol, crow;
-            cell_of(p, W, H, inv_cs, gx, gy, ccol, crow);
-            const int cell = pass == 0 ? ccol : crow;
-            const unsigned peers = __match_any_sync(act, cell);
-            const int rank = __popc(peers & ((1u << lane) - 1u));
-            const int leader = __ffs(peers) - 1;
-            int basepos = 0;
-            if (lane == leader) basepos = cur[cell];
-            basepos = __shfl_sync(peers, basepos, leader);
-            const int pos = basepos + rank;
-            if (lane == leader) cur[cell] = basepos + __popc(peers);
-            if (pass == 0) {
-                perm[pos] = i;
-                xy[pos] = p;
-                colpos[i] = pos;
-            } else {
-                xy_r[pos] = p;
-                idx_r[pos] = colpos[i];
-            }
-            __syncwarp(act);
-        }
-        __syncwarp();
-        __threadfence_block();
-    }
+    __shared__ int32_t wsum[32];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    const int v = i < m ? cnt[i] : 0;
+    int total;
+    const int incl = block_incl_scan(v, wsum, total);
+    if (i < m) off[i] = incl - v;
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// Pass 2: add the totals of the earlier blocks; the last block also writes off[m] (the grand total).
+__global__ void __launch_bounds__(kScanBlock) scan_add_kernel(const int32_t *__restrict__ bsum, int32_t nblocks,
+                                                               int32_t m, int32_t *__restrict__ off)
+{
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t base;
+    int acc = 0;
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) acc += bsum[k];
+    int total;
+    block_incl_scan(acc, wsum, total);
+    if (threadIdx.x == 0) base = total;
+    __syncthreads();
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    if (i < m) off[i] += base;
+    if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) off[m] = base + bsum[blockIdx.x];
+}
+
+cudaError_t exclusive_scan(const int32_t *cnt, int32_t m, int32_t *off, int32_t *bsum, cudaStream_t st)
+{
+    const int nb = (m + kScanBlock - 1) / kScanBlock;
+    scan_local_kernel<<<nb, kScanBlock, 0, st>>>(cnt, m, off, bsum);
+    scan_add_kernel<<<nb, kScanBlock, 0, st>>>(bsum, nb, m, off);
+    return cudaGetLastError();
+}
+
+// Column-major scatter: one thread per keypoint (cur: per-cell cursors, initialised to the offsets).
+__global__ void scatter_col_kernel(const float2 *__restrict__ xy_raw, int32_t n, float W, float H, float inv_cs,
+                                   int gx, int gy, int32_t *__restrict__ cur, float2 *__restrict__ xy,
+                                   int32_t *__restrict__ perm, int32_t *__restrict__ inv_perm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 p = xy_raw[i];
+    int ccol, crow;
+    cell_of(p, W, H, inv_cs, gx, gy, ccol, crow);
+    const int pos = atomicAdd(&cur[ccol], 1);
+    perm[pos] = i;
+    xy[pos] = p;
+    inv_perm[i] = pos;
+}
+
+// Row-major scatter (after the column-major one: idx_r holds column-major positions).
+__global__ void scatter_row_kernel(const float2 *__restrict__ xy_raw, int32_t n, float W, float H, float inv_cs,
+                                   int gx, int gy, int32_t *__restrict__ cur, const int32_t *__restrict__ inv_perm,
+                                   float2 *__restrict__ xy_r, int32_t *__restrict__ idx_r)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 p = xy_raw[i];
+    int ccol, crow;
+    cell_of(p, W, H, inv_cs, gx, gy, ccol, crow);
+    const int pos = atomicAdd(&cur[crow], 1);
+    xy_r[pos] = p;
+    idx_r[pos] = inv_perm[i];
 }
 
 // One warp per sorted row: recentred int8 copy, squared norm and fp16 copy of the descriptor.
@@ -153,24 +170,20 @@ __global__ void desc_permute_kernel(const uint8_t *__restrict__ desc_raw, const 
     if (desc_h) reinterpret_cast<uint2 *>(desc_h + (int64_t)warp * kDim)[lane] = make_uint2(h01, h23);
 }
 
-// Point records for the tensor-core path: (x, y, |b'|^2 * 256, column-major position) in column-major and in
-// row-major order, each followed by a sentinel whose NaN coordinates fail every band test.
-__global__ void records_kernel(const float2 *__restrict__ xy, const float2 *__restrict__ xy_r,
-                               const int32_t *__restrict__ idx_r, const int32_t *__restrict__ norm256, int32_t n,
-                               int4 *__restrict__ rec, int4 *__restrict__ rec_r)
+// Point records for the tensor-core path: (x, y, |b'|^2 * 256, column-major position) in column-major order,
+// followed by a sentinel whose NaN coordinates fail every band test.
+__global__ void records_kernel(const float2 *__restrict__ xy, const int32_t *__restrict__ norm256, int32_t n,
+                               int4 *__restrict__ rec)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i > n) return;
     if (i == n) {
         const int nan = 0x7fc00000;
         rec[n] = make_int4(nan, nan, 0, 0);
-        rec_r[n] = make_int4(nan, nan, 0, 0);
         return;
     }
-    const float2 p = xy[i], q = xy_r[i];
-    const int j = idx_r[i];
+    const float2 p = xy[i];
     rec[i] = make_int4(__float_as_int(p.x), __float_as_int(p.y), norm256[i], i);
-    rec_r[i] = make_int4(__float_as_int(q.x), __float_as_int(q.y), norm256[j], j);
 }
 
 }  // namespace
@@ -194,26 +207,30 @@ cudaError_t launch_bucket_build(const float2 *xy_raw, const uint8_t *desc_raw, i
                                 int32_t height, int32_t cell_shift, int32_t gx, int32_t gy, float2 *xy, int32_t *perm,
                                 int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *norm256, int32_t *col_off,
                                 float2 *xy_r, int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int4 *rec,
-                                int4 *rec_r, int32_t *work, cudaStream_t st)
+                                int32_t *work, cudaStream_t st)
 {
     // col_off / row_off hold gx*gy + 2 entries: the cells, the out-of-image cell, the total
     const int m = gx * gy + 1;
     const float inv_cs = 1.0f / (float)(1 << cell_shift);
-    int32_t *cnt_col = work, *cnt_row = work + (m + 1);
+    int32_t *cnt_col = work, *cnt_row = work + (m + 1), *bsum = work + 2 * (m + 1);
     cudaError_t e;
-    exclusive_scan_kernel<<<1, 1024, 0, st>>>(cnt_col, m, col_off);
-    exclusive_scan_kernel<<<1, 1024, 0, st>>>(cnt_row, m, row_off);
+    if ((e = exclusive_scan(cnt_col, m, col_off, bsum, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan(cnt_row, m, row_off, bsum + (m + kScanBlock - 1) / kScanBlock, st)) != cudaSuccess)
+        return e;
     // cursors start at the offsets (reuse the count arrays)
     if ((e = cudaMemcpyAsync(cnt_col, col_off, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return e;
     if ((e = cudaMemcpyAsync(cnt_row, row_off, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return e;
     if (n > 0) {
-        bucket_scatter_kernel<<<1, 32, 0, st>>>(xy_raw, n, (float)width, (float)height, inv_cs, gx, gy, cnt_col,
-                                                cnt_row, xy, perm, inv_perm, xy_r, idx_r);
+        const int nb = (n + 255) / 256;
+        scatter_col_kernel<<<nb, 256, 0, st>>>(xy_raw, n, (float)width, (float)height, inv_cs, gx, gy, cnt_col, xy,
+                                               perm, inv_perm);
+        scatter_row_kernel<<<nb, 256, 0, st>>>(xy_raw, n, (float)width, (float)height, inv_cs, gx, gy, cnt_row,
+                                               inv_perm, xy_r, idx_r);
         desc_permute_kernel<<<(n + 7) / 8, 256, 0, st>>>(desc_raw, perm, n, desc, norm, norm256, desc_h);
     }
-    records_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(xy, xy_r, idx_r, norm256, n, rec, rec_r);
+    records_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(xy, norm256, n, rec);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,10 @@ struct Workspace {
     DevBuf d_rows;       // int32 [Q][2] match rows (device destination of the synchronous API)
     DevBuf d_ctr;        // BatchCounters [64]
     DevBuf d_next;       // int32 work-queue counter of the persistent kernel
+    DevBuf d_grec;       // GroupDesc [items] (tcgen05 path)
+    DevBuf d_grows;      // int32 [items][128] query rows of every group (tcgen05 path)
+    DevBuf d_stream;     // int32 [stream_cap] candidate streams of the groups (tcgen05 path)
+    int64_t stream_cap = 0, stream_used = 0, overflow = 0;
     HostBuf h_tab;       // pinned staging of d_tab
     HostBuf h_off;       // pinned: offsets [P+1] then counters [64]
     HostBuf h_rows;      // mapped pinned rows (serving destination)

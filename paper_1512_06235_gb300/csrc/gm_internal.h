@@ -34,15 +34,15 @@ struct ImageDev {
     const int32_t *row_off;         // [gx*gy + 2]; cell (cx, cy) -> cy*gx + cx
     const uint16_t *desc_h;         // [n][128] fp16 bits of (b - 128), column-major order (tensor-core path)
     const int4 *rec;                // [n + 1] (x, y, norm * 256, position) column-major; [n] = NaN sentinel
-    const int4 *rec_r;              // [n + 1] the same in row-major order (position = column-major position)
 };
 
-// TMA descriptors of one resident image (tcgen05 path): fp16 descriptor rows (box 64 x 1, 128-byte swizzle) and
-// the two record arrays (box 4 x 1 int32).  CUtensorMap carries the 64-byte alignment TMA requires.
+// TMA descriptors of one resident image (tcgen05 path): 64-row boxes of the fp16 descriptor rows (64 elements
+// wide, 128-byte swizzle) and of the records (read as FP32 so that rows past the end come back as NaN).
+// CUtensorMap carries the alignment TMA requires.
 struct TmaMaps {
-    CUtensorMap desc;
-    CUtensorMap rec;
-    CUtensorMap rec_r;
+    CUtensorMap desc_tile;   // fp16 descriptors, 64 x 64 box (contiguous chunks)
+    CUtensorMap desc_row;    // fp16 descriptors, 64 x 1 box (gather4 of scattered rows)
+    CUtensorMap rec_tile;    // records, 4 x 64 box, NaN past the end
 };
 
 struct PairDev {
@@ -61,20 +61,44 @@ struct BatchCounters {
     unsigned long long examined;    // points visited by the cell walk
     unsigned long long redecided;   // FP64 re-decisions
     unsigned long long errors;      // device-side argument / bound violations (must stay 0)
+    unsigned long long overflow;    // groups whose candidate stream did not fit the stream buffer
 };
+
+// Self-contained description of one query group of the tensor-core path (written by the stream kernel, so the
+// matching kernel needs no pair or image table lookups): stream[off .. off + total) holds column-major positions
+// in image B; flags bit 0: the group uses the whole image (positions 0 .. total-1, nothing stored), bit 1: the
+// stream did not fit the buffer (the batch must be run again with a larger buffer).  The group's query rows
+// (column-major positions in A, -1 past the end of the pair) are stored separately, kTcQueriesPerItem per group.
+struct alignas(16) GroupDesc {
+    int64_t off;                    // stream offset
+    const int4 *a_rec;              // A's point records (x, y, |a'|^2 * 256, position)
+    const int32_t *a_perm;          // A: column-major position -> original index
+    const uint16_t *a_desc;         // A's fp16 descriptor rows
+    const uint16_t *b_desc;         // B's fp16 descriptor rows
+    const int4 *b_rec;              // B's point records
+    const int32_t *b_perm;          // B: column-major position -> original index
+    int32_t a_slot, b_slot;         // image slots (TMA descriptor table)
+    int32_t a_n, b_n;
+    int32_t total, flags;
+    int32_t p, q;                   // ratio p/q
+    float F[9];
+    float d, W, H;                  // band half-width, size of image B
+    int64_t qoff;                   // the pair's offset in the per-query output
+};
+constexpr int kTcQueriesPerItem = 128;
 
 // ---- launchers (host functions defined in the .cu files) ---------------------------------------------------
 // Image registration (two phases, so that invalid input never touches the destination): the count phase
 // histograms the cells and counts keypoints outside [0,W) x [0,H) into *bad; the build phase (only after *bad
-// was read as 0) scans, scatters and copies the descriptors.  work: int32 scratch of 2*(gx*gy + 2) entries,
-// carried from the first phase to the second.  All pointers are device pointers.
+// was read as 0) scans, scatters and copies the descriptors.  work: int32 scratch of 2*(gx*gy + 2) + 2*(gx*gy/1024
+// + 2) entries, carried from the first phase to the second.  All pointers are device pointers.
 cudaError_t launch_bucket_count(const float2 *xy_raw, int32_t n, int32_t width, int32_t height, int32_t cell_shift,
                                 int32_t gx, int32_t gy, int32_t *work, unsigned long long *bad, cudaStream_t st);
 cudaError_t launch_bucket_build(const float2 *xy_raw, const uint8_t *desc_raw, int32_t n, int32_t width,
                                 int32_t height, int32_t cell_shift, int32_t gx, int32_t gy, float2 *xy, int32_t *perm,
                                 int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *norm256, int32_t *col_off,
                                 float2 *xy_r, int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int4 *rec,
-                                int4 *rec_r, int32_t *work, cudaStream_t st);
+                                int32_t *work, cudaStream_t st);
 
 // Query ordering (App. A Step 2 as an order only): per pair, sorts A's queries by the position of their
 // epipolar line in B.  qorder[qoff + k] = column-major position in A of the k-th query.
@@ -98,13 +122,19 @@ int match_mma_blocks_per_sm(int mt);
 
 // tcgen05 matching path (warp-specialised, TMA gather4 + tcgen05.mma): groups of kTcQueriesPerItem sorted
 // queries per work item, one persistent CTA per SM (grid CTAs take items item_begin + b, + grid, ...).
-// Every image of the batch must have max(gx, gy) <= match_tc_max_grid_lines().
-cudaError_t launch_match_tc(const ImageDev *imgs, const PairDev *pairs, const TmaMaps *maps, const int64_t *item_off,
-                            int32_t n_pairs, const int32_t *qorder, int64_t item_begin, int64_t item_end, int32_t grid,
-                            int32_t *match_j, BatchCounters *ctr, cudaStream_t st);
+// The group streams come from launch_stream; every image of the batch must have max(gx, gy) <=
+// match_tc_max_grid_lines().
+cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const int32_t *grows, const int32_t *stream,
+                            int64_t item_begin, int64_t item_end, int32_t grid, int32_t *match_j, BatchCounters *ctr,
+                            cudaStream_t st);
+// Candidate streams of the tcgen05 groups [item_begin, item_end) of a batch (grec is indexed by item); *used
+// accumulates the stream entries written (zeroed by the caller).
+cudaError_t launch_stream(const ImageDev *imgs, const PairDev *pairs, const int64_t *item_off, int32_t n_pairs,
+                          const int32_t *qorder, int64_t item_begin, int64_t item_end, GroupDesc *gdesc, int32_t *grows,
+                          int32_t *stream, int64_t capacity, unsigned long long *used, BatchCounters *ctr,
+                          cudaStream_t st);
 int match_tc_blocks_per_sm();
 int match_tc_max_grid_lines();
-constexpr int kTcQueriesPerItem = 128;
 
 // Output assembly: counts[p] = matches of pair p, pair_off = exclusive scan (pair_off[n_pairs] = total), then
 // rows (i, j) sorted by i into matches.

@@ -4,20 +4,27 @@
 // epipolar line, so a group's bands nearly coincide; every query keeps its own exact band).  One persistent CTA
 // per SM runs four roles that hand work to each other through mbarriers:
 //
-//   setup warps (2, alternate groups): the group's FP32 lines and exact-decision thresholds (gm_band.cuh), the
-//       chord envelope of the group's strips and one run of cells per grid column (see gm_match_mma.cu for the
-//       envelope argument), the run table, and the TMA gather4 of the 128 query descriptors (recentred, fp16:
-//       integers in [-128, 127] are exact) into the group's A tile (128-byte-swizzled K-major layout);
-//   loader warp: cuts the group's candidate stream into 64-row chunks and gathers, with TMA gather4, the fp16
-//       descriptor rows (two K halves) and a 16-byte record per candidate (x, y, |b'|^2 * 256, index) into a
-//       4-stage ring; slots past the end of the stream get the image's NaN sentinel record;
+//   setup warps (2, alternate groups): the gather (cp.async, two 256-byte rows per warp instruction) of the
+//       group's 128 query descriptors (recentred, fp16: integers in [-128, 127] are exact) into the group's A tile
+//       (128-byte-swizzled K-major layout), and the
+//       queries' coordinates, norms and output indices into shared memory.  Everything the CTA needs about a group
+//       comes from its descriptor (gm_stream.cu); the setup warp loads it before it waits for the slot;
+//   loader warp: cuts the group's candidate stream (computed beforehand by gm_stream.cu: the chord-bounded cell
+//       walk of the whole group) into 64-row chunks and brings the fp16 descriptor rows (two K halves) and a 16-byte
+//       record per candidate (x, y, |b'|^2 * 256, position) into a 4-stage ring: scattered rows of banded groups by
+//       cp.async (completion through cp.async.mbarrier.arrive), the contiguous rows of whole-image groups by TMA
+//       tile loads (64-row boxes, 128-byte swizzle; rows past the image read as NaN records); slots past the end of
+//       a stream get the image's NaN sentinel record.  It reads the descriptors itself and runs ahead of the setup
+//       warps;
 //   MMA warp (one elected thread): eight tcgen05.mma.kind::f16 per chunk (M = 128, N = 64, K = 16 each), f32
 //       accumulation into one of two tensor-memory buffers.  Products are integers of magnitude <= 2^14 and partial
 //       sums <= 2^21 < 2^24, so the accumulator holds the exact integer dot product a'.b';
-//   epilogue warps (8 = 4 lane quadrants x 2 column halves): tcgen05.ld of 32 accumulator columns, then per element
-//       the exact band test, D = |a'|^2 + |b'|^2 - 2 a'.b' packed with the column into one int32 key, a masked
-//       running top-2; at the end of the group the two column halves merge and the integer ratio test
-//       q^2 D1 < p^2 D2 decides (Sec. 2.3).
+//   epilogue warps (8 = 4 lane quadrants x 2 column halves): each thread derives its query's FP32 line and
+//       exact-decision thresholds (gm_band.cuh), then per chunk tcgen05.ld of 32 accumulator columns and per element
+//       the FP32 band test, D = |a'|^2 + |b'|^2 - 2 a'.b' packed with the column into one int32 key and a masked
+//       running top-2 (two interleaved accumulators, no branch in the loop); the rare elements inside the FP32 error
+//       margin are re-decided in FP64 afterwards; at the end of the group the two column halves merge and the
+//       integer ratio test q^2 D1 < p^2 D2 decides (Sec. 2.3).
 //
 // CTA b takes work items b, b + gridDim.x, ... (static order: every role derives the same group sequence).
 // Every mbarrier wait gives up after one second; the CTA then raises the batch error counter, every role leaves its
@@ -39,7 +46,7 @@ constexpr int kM = 128;             // queries per group (tensor-memory lanes)
 constexpr int kN = 64;              // candidates per chunk
 constexpr int kStages = 4;          // candidate chunks in flight
 constexpr int kSlots = 2;           // query groups in flight
-constexpr int kMaxRuns = 1024;      // grid lines per group walk
+constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
 constexpr int kEpiWarps = 8;
 constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;
 constexpr int kThreads = 12 * 32;
@@ -52,24 +59,17 @@ constexpr int kBHalf = kN * 128;                    // one K half of a candidate
 constexpr int kOffA = 0;                            // kSlots A tiles
 constexpr int kOffB = kOffA + kSlots * 2 * kAHalf;  // kStages candidate chunks
 constexpr int kOffRec = kOffB + kStages * 2 * kBHalf;
-constexpr int kRecStage = (kN / 4) * 128;         // records of a chunk: one 128-byte slot per quad of 4 records
+constexpr int kRecStage = kN * 16;                // records of a chunk (16 bytes each)
 constexpr int kOffCtl = kOffRec + kStages * kRecStage;
-constexpr uint32_t kChunkTx = kN * (256 + 16);      // bytes the loader's TMAs bring per chunk
-constexpr uint32_t kATx = kM * 256;
-
-struct Meta {
-    int32_t pair, nchunks, total, walk_full, colwise;
-};
+constexpr uint32_t kChunkTx = kN * (256 + 16);      // bytes the loader's TMA tile loads bring per chunk
 
 struct Ctl {
-    float ln[kSlots][kM][8];         // a, b, c, thr_lo, thr_hi, qx, qy, walk half-width (or -1 whole image, -2 none)
+    GroupDesc desc[kSlots];          // the group in each slot
+    float2 qxy[kSlots][kM];          // query coordinates
     int32_t rinfo[kSlots][kM][2];    // original A index (-1: no query), |a'|^2 * 256
     int32_t aidx[kSlots][kM];        // A rows to gather
-    int32_t run_start[kSlots][kMaxRuns];
-    int32_t run_excl[kSlots][kMaxRuns + 1];
     int32_t merge[kSlots][kM][4];
-    Meta meta[kSlots];
-    float F[kSlots][9];
+    alignas(16) int32_t lrows[kStages][kN];   // loader: source rows of the chunk in each stage
     uint64_t stage_full[kStages], stage_empty[kStages], acc_full[2], acc_empty[2];
     uint64_t grp_full[kSlots], grp_empty[kSlots], merge_ready[kSlots];
     uint32_t tmem_base;
@@ -127,21 +127,86 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// TMA gather of four rows (box: one row of the tensor map's box width) into consecutive shared rows.  The shared
+// TMA tile load of the map's box at (col, row) (2D).  The shared destination must be 128-byte aligned (1024 for
+// the 128-byte swizzle) and col a multiple of 16 bytes: a request that breaks either is counted in *bad and not
+// issued (its bytes never arrive, so the waiting role times out and the batch fails).
+__device__ __forceinline__ void tma_tile(uint32_t dst, const CUtensorMap *map, int col, int row, uint64_t *bar,
+                                         uint32_t align, unsigned long long *bad)
+{
+    if ((dst & (align - 1u)) != 0u || (col & 7) != 0 || row < 0) {
+        atomicAdd(bad, 1ull);
+        return;
+    }
+    asm volatile("cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                 "[%4];\n" ::"r"(dst),
+                 "l"(map), "r"(col), "r"(row), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// TMA gather of four rows (the box is one row of the map's box width) into consecutive shared rows.  The shared
 // destination must be 128-byte aligned and the rows inside the tensor [0, rows): a request that breaks either is
 // counted in *bad and not issued (its bytes never arrive, so the waiting role times out and the batch fails).
-__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map, int col, int r0, int r1, int r2, int r3,
-                                            uint64_t *bar, int rows, unsigned long long *bad)
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map, int col, int4 r, uint64_t *bar,
+                                            int rows, unsigned long long *bad)
 {
-    if ((dst & 127u) != 0u || (unsigned)r0 >= (unsigned)rows || (unsigned)r1 >= (unsigned)rows ||
-        (unsigned)r2 >= (unsigned)rows || (unsigned)r3 >= (unsigned)rows) {
+    if ((dst & 127u) != 0u || (col & 7) != 0 || (unsigned)r.x >= (unsigned)rows || (unsigned)r.y >= (unsigned)rows ||
+        (unsigned)r.z >= (unsigned)rows || (unsigned)r.w >= (unsigned)rows) {
         atomicAdd(bad, 1ull);
         return;
     }
     asm volatile("cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes "
                  "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
-                 "l"(map), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_u32(bar))
+                 "l"(map), "r"(col), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// Adds bytes to the transaction count of the current phase without arriving.
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+// The mbarrier receives one arrival once all cp.async operations issued so far by this thread have completed.
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 128-byte swizzle of a K-major tile: row r, 16-byte chunk c of one K half (rows are 128 bytes).
+__device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+// Gathers rows into a K-major, 128-byte-swizzled fp16 tile (two K halves of half_bytes each).  rows[k] (shared
+// memory) is the source row of tile row k.  One warp instruction copies two whole 256-byte rows (lanes 0-15: row
+// 2i, lanes 16-31: row 2i + 1), so every request reads whole 128-byte lines; the swizzle term of a lane repeats
+// every four instructions and is precomputed.
+__device__ __forceinline__ void gather_rows(uint32_t tile, int half_bytes, int nrows, const uint16_t *__restrict__ src,
+                                            const int32_t *rows)
+{
+    const int lane = threadIdx.x & 31;
+    const int sub = lane >> 4, c = lane & 15;   // c: 16-byte chunk of the 256-byte row
+    const int h = c >> 3, cc = c & 7;
+    const char *s0 = reinterpret_cast<const char *>(src) + c * 16;
+    uint32_t dst[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {   // tile row 2m + sub (+ 8 per four instructions): chunk cc ^ (row & 7)
+        const int r = 2 * m + sub;
+        dst[m] = tile + h * half_bytes + sw128(r, cc);
+    }
+    for (int i0 = 0; i0 < nrows / 2; i0 += 4) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r = 2 * (i0 + m) + sub;
+            cp_async16(dst[m] + i0 * 256, s0 + (int64_t)rows[r] * (kDim * 2));
+        }
+    }
 }
 
 // Shared-memory matrix descriptor: start >> 4, leading byte offset 16 (unused for swizzled K-major), stride byte
@@ -183,17 +248,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-__device__ __forceinline__ int pair_of_item(const int64_t *__restrict__ item_off, int n_pairs, int64_t t)
-{
-    int lo = 0, hi = n_pairs;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (item_off[mid] <= t) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ void raise_abort(Ctl &cl, BatchCounters *ctr)
 {
     if (!cl.abort_flag) {
@@ -203,187 +257,55 @@ __device__ __forceinline__ void raise_abort(Ctl &cl, BatchCounters *ctr)
 }
 
 // ------------------------------------------------------------------------------------------------ setup role
-// One warp prepares group gk into slot gk % 2: lines, thresholds, envelope, run table, A-tile gather.
-__device__ void setup_group(Ctl &cl, unsigned char *base, const ImageDev *__restrict__ imgs,
-                            const PairDev *__restrict__ pairs, const TmaMaps *__restrict__ maps,
-                            const int64_t *__restrict__ item_off, int32_t n_pairs, const int32_t *__restrict__ qorder,
-                            int64_t item, int g, unsigned long long &my_exam, unsigned long long *bad)
+// Query data of one group, loaded into registers before the slot is free (rows lane + 32 t).
+struct SetupData {
+    GroupDesc d;
+    int s4[4];
+    int4 r4[4];
+    int o4[4];
+};
+
+__device__ __forceinline__ void setup_load(SetupData &sd, const GroupDesc *__restrict__ gdesc,
+                                           const int32_t *__restrict__ grows, int64_t item)
 {
     const int lane = threadIdx.x & 31;
-    const int pi = pair_of_item(item_off, n_pairs, item);
-    const PairDev &P = pairs[pi];
-    const ImageDev &A = imgs[P.a];
-    const ImageDev &B = imgs[P.b];
-    const int q0 = (int)(item - item_off[pi]) * kM;
-    const float d = P.d;
-    const float W = (float)B.width, H = (float)B.height;
-    float F[9];
+    sd.d = gdesc[item];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) F[t] = P.F[t];
-    if (lane < 9) cl.F[g][lane] = F[lane];
+    for (int t = 0; t < 4; ++t) sd.s4[t] = __ldg(grows + item * kM + lane + 32 * t);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int sq = sd.s4[t];
+        sd.r4[t] = sq >= 0 ? __ldg(sd.d.a_rec + sq) : make_int4(0, 0, 0, 0);
+        sd.o4[t] = sq >= 0 ? __ldg(sd.d.a_perm + sq) : -1;
+    }
+}
 
-    // rows lane, lane + 32, lane + 64, lane + 96: issue the independent loads first
-    int s4[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const int k = q0 + lane + 32 * t;
-        s4[t] = k < P.n_a ? qorder[P.qoff + k] : -1;
-    }
-    float2 q4[4];
-    int n4[4], o4[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const int s = s4[t];
-        q4[t] = s >= 0 ? A.xy[s] : make_float2(0.0f, 0.0f);
-        n4[t] = s >= 0 ? A.norm256[s] : 0;
-        o4[t] = s >= 0 ? A.perm[s] : -1;
-    }
-    int votes = 0, nnorm = 0, full = 0;
+// Writes the group into slot g and gathers its A tile (the slot must be free).
+__device__ __forceinline__ void setup_store(Ctl &cl, unsigned char *base, const SetupData &sd, int g)
+{
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         const int r = lane + 32 * t;
-        float *L = cl.ln[g][r];
-        if (s4[t] >= 0) {
-            const BandLine bl = band_line(F, q4[t].x, q4[t].y, d, W, H);
-            float lo = bl.thr_lo, hi = bl.thr_hi, la = bl.a, lb = bl.b, lc = bl.c;
-            // whole-image rows accept every real keypoint; FP64-only rows send every real keypoint to the FP64
-            // decision; both use the zero line (s = 0 for real keypoints, NaN for the sentinel record)
-            if (bl.mode == kBandAll) { lo = INFINITY; hi = INFINITY; la = lb = lc = 0.0f; }
-            else if (bl.mode == kBandSlow) { lo = -1.0f; hi = INFINITY; la = lb = lc = 0.0f; }
-            L[0] = la; L[1] = lb; L[2] = lc; L[3] = lo; L[4] = hi; L[5] = q4[t].x; L[6] = q4[t].y;
-            L[7] = bl.mode == kBandNormal ? bl.t_walk : -1.0f;
-            if (bl.mode == kBandNormal) { ++nnorm; votes += fabsf(bl.b) >= fabsf(bl.a); }
-            else full = 1;
-        } else {
-            L[0] = L[1] = L[2] = 0.0f; L[3] = L[4] = -1.0f; L[5] = L[6] = 0.0f; L[7] = -2.0f;
-        }
-        cl.rinfo[g][r][0] = o4[t];
-        cl.rinfo[g][r][1] = n4[t];
-        cl.aidx[g][r] = s4[t] >= 0 ? s4[t] : 0;
+        cl.qxy[g][r] = make_float2(__int_as_float(sd.r4[t].x), __int_as_float(sd.r4[t].y));
+        cl.rinfo[g][r][0] = sd.o4[t];
+        cl.rinfo[g][r][1] = sd.r4[t].z;
+        cl.aidx[g][r] = sd.s4[t] >= 0 ? sd.s4[t] : 0;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        votes += __shfl_xor_sync(0xffffffffu, votes, o);
-        nnorm += __shfl_xor_sync(0xffffffffu, nnorm, o);
-        full |= __shfl_xor_sync(0xffffffffu, full, o);
-    }
+    if (lane == 0) cl.desc[g] = sd.d;
     __syncwarp();
-    // chord envelope of the group's strips in the walk frame (u: walked axis, v: the other)
-    const int colwise0 = 2 * votes >= nnorm;
-    const float ulim0 = colwise0 ? W : H;
-    float t0 = -INFINITY, t1 = -INFINITY, b0 = INFINITY, b1 = INFINITY, pad = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const float *L = cl.ln[g][lane + 32 * t];
-        if (!(L[7] >= 0.0f)) continue;
-        float pa = colwise0 ? L[0] : L[1], pb = colwise0 ? L[1] : L[0], c = L[2];
-        if (pb < 0.0f) { pa = -pa; pb = -pb; c = -c; }
-        const float T = L[7];
-        if (!(pb > 1e-30f)) { full = 1; continue; }
-        const float ib = 1.0f / pb;
-        const float e0 = -c * ib, e1 = -fmaf(pa, ulim0, c) * ib, h = T * ib;
-        t0 = fmaxf(t0, e0 + h); t1 = fmaxf(t1, e1 + h);
-        b0 = fminf(b0, e0 - h); b1 = fminf(b1, e1 - h);
-        pad = fmaxf(pad, 8.0f * kU * (fabsf(pa) * ulim0 + fabsf(c) + T) * ib);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        t0 = fmaxf(t0, __shfl_xor_sync(0xffffffffu, t0, o));
-        t1 = fmaxf(t1, __shfl_xor_sync(0xffffffffu, t1, o));
-        b0 = fminf(b0, __shfl_xor_sync(0xffffffffu, b0, o));
-        b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
-        pad = fmaxf(pad, __shfl_xor_sync(0xffffffffu, pad, o));
-        full |= __shfl_xor_sync(0xffffffffu, full, o);
-    }
-    pad += 1e-3f + 4.0f * kU * (fabsf(t0) + fabsf(t1) + fabsf(b0) + fabsf(b1));
-    const float et0 = t0 + pad, et1 = t1 + pad, eb0 = b0 - pad, eb1 = b1 - pad;
-    const bool fin = isfinite(et0) && isfinite(et1) && isfinite(eb0) && isfinite(eb1);
-    const int walk_full = full || (nnorm > 0 && !fin);
-    const bool none = nnorm == 0 && !full;
-    const int colwise = walk_full ? 1 : colwise0;
-    // one run of cells per grid line
-    const float cs = (float)(1 << B.cell_shift), inv_cs = 1.0f / cs;
-    const int nlines = none ? 0 : walk_full ? 1 : (colwise ? B.gx : B.gy);
-    const int ng = colwise ? B.gy : B.gx;
-    const float ulim = colwise ? W : H, vlim = colwise ? H : W;
-    const int32_t *offs = colwise ? B.col_off : B.row_off;
-    int carry = 0;
-    for (int base_line = 0; base_line < kMaxRuns; base_line += 32 * 8) {
-        int st[8], en[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int kk = base_line + 32 * t + lane;
-            st[t] = -1;
-            en[t] = 0;
-            if (kk < nlines) {
-                if (walk_full) {
-                    st[t] = -2;
-                } else {
-                    const float u0 = (float)kk * cs, u1 = fminf(u0 + cs, ulim);
-                    const float f0 = u0 / ulim, f1 = u1 / ulim;
-                    const float top0 = fmaf(et1 - et0, f0, et0), top1 = fmaf(et1 - et0, f1, et0);
-                    const float bot0 = fmaf(eb1 - eb0, f0, eb0), bot1 = fmaf(eb1 - eb0, f1, eb0);
-                    const float lo = fminf(bot0, bot1), hi = fmaxf(top0, top1);
-                    if (hi >= 0.0f && lo < vlim) {
-                        const int c0 = max(0, (int)floorf(fmaxf(lo, 0.0f) * inv_cs));
-                        const int c1 = min(ng - 1, (int)floorf(fminf(hi, vlim) * inv_cs));
-                        if (c0 <= c1) { st[t] = kk * ng + c0; en[t] = kk * ng + c1 + 1; }
-                    }
-                }
-            }
-        }
-        // run bounds (independent loads), then start / length
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            int s0 = 0, s1 = 0;
-            if (st[t] >= 0) { s0 = offs[st[t]]; s1 = offs[en[t]]; }
-            else if (st[t] == -2) { s0 = 0; s1 = B.n; }
-            st[t] = s0;
-            en[t] = s1 - s0;
-        }
-        // exclusive scan of the lengths, in grid-line order
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int kk = base_line + 32 * t + lane;
-            int incl = en[t];
-#pragma unroll
-            for (int s = 1; s < 32; s <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, incl, s);
-                if (lane >= s) incl += u;
-            }
-            cl.run_start[g][kk] = st[t];
-            cl.run_excl[g][kk] = carry + incl - en[t];
-            carry += __shfl_sync(0xffffffffu, incl, 31);
-        }
-    }
-    if (lane == 0) {
-        cl.run_excl[g][kMaxRuns] = carry;
-        Meta &m = cl.meta[g];
-        m.pair = pi;
-        m.total = carry;
-        m.nchunks = (carry + kN - 1) / kN;
-        m.walk_full = walk_full;
-        m.colwise = colwise;
-        my_exam += (unsigned long long)carry * kM;
-    }
-    __syncwarp();
-    // A tile: 32 quads of rows, two K halves each; lane 0 announces the bytes (and releases the slot data) first
-    if (lane == 0) mbar_expect_tx(&cl.grp_full[g], kATx);
-    __syncwarp();
-    const CUtensorMap *dmap = &maps[P.a].desc;
-    const uint32_t abase = smem_u32(base + kOffA + g * 2 * kAHalf);
-    const int *ai = cl.aidx[g] + 4 * lane;
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-        tma_gather4(abase + h * kAHalf + 4 * lane * 128, dmap, 64 * h, ai[0], ai[1], ai[2], ai[3], &cl.grp_full[g], A.n,
-                    bad);
+    // A tile: 128 rows, two per warp instruction; every lane's copies complete into grp_full (noinc arrivals),
+    // plus one ordinary arrival that releases the slot data written above
+    gather_rows(smem_u32(base + kOffA + g * 2 * kAHalf), kAHalf, kM, sd.d.a_desc, cl.aidx[g]);
+    cp_async_arrive(&cl.grp_full[g]);
+    if (lane == 0) mbar_arrive(&cl.grp_full[g]);
 }
 
 // ------------------------------------------------------------------------------------------------ kernel
 __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
-    const ImageDev *__restrict__ imgs, const PairDev *__restrict__ pairs, const TmaMaps *__restrict__ maps,
-    const int64_t *__restrict__ item_off, int32_t n_pairs, const int32_t *__restrict__ qorder, int64_t item_begin,
-    int64_t item_end, int32_t *__restrict__ match_j, BatchCounters *__restrict__ ctr)
+    const TmaMaps *__restrict__ maps, const GroupDesc *__restrict__ gdesc, const int32_t *__restrict__ grows,
+    const int32_t *__restrict__ stream, int64_t item_begin, int64_t item_end, int32_t *__restrict__ match_j,
+    BatchCounters *__restrict__ ctr)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -393,13 +315,13 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     const int64_t stride = gridDim.x;
     const int64_t first = item_begin + blockIdx.x;
     const int n_groups = first < item_end ? (int)((item_end - first + stride - 1) / stride) : 0;
-    unsigned long long my_cand = 0, my_exam = 0, my_redec = 0;
+    unsigned long long my_cand = 0, my_redec = 0;
 
     if (tid == 0) {
         cl.abort_flag = 0;
         cl.stat[0] = cl.stat[1] = cl.stat[2] = 0ull;
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&cl.stage_full[s], 1);
+            mbar_init(&cl.stage_full[s], 32);   // the 32 loader lanes
             mbar_init(&cl.stage_empty[s], 1 + kEpiWarps);
         }
         for (int b = 0; b < 2; ++b) {
@@ -407,8 +329,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             mbar_init(&cl.acc_empty[b], kEpiWarps);
         }
         for (int g = 0; g < kSlots; ++g) {
-            mbar_init(&cl.grp_full[g], 1);
-            mbar_init(&cl.grp_empty[g], 1 + 1 + kEpiWarps);   // MMA commit, loader, epilogue warps
+            mbar_init(&cl.grp_full[g], 33);   // 32 cp.async arrivals + the setup warp's release
+            mbar_init(&cl.grp_empty[g], 1 + kEpiWarps);   // MMA commit, epilogue warps
             mbar_init(&cl.merge_ready[g], kEpiWarps / 2);
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -428,65 +350,82 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         const int j = warp - kSetupWarp0;
         for (int gk = j; gk < n_groups && !cl.abort_flag; gk += kSlots) {
             const int g = gk % kSlots;
+            SetupData sd;
+            setup_load(sd, gdesc, grows, first + (int64_t)gk * stride);   // in flight while the slot drains
             if (!mbar_wait_warp(&cl.grp_empty[g], ((gk / kSlots) & 1) ^ 1)) { raise_abort(cl, ctr); break; }
-            setup_group(cl, base, imgs, pairs, maps, item_off, n_pairs, qorder, first + (int64_t)gk * stride, g,
-                        my_exam, &ctr->errors);
+            setup_store(cl, base, sd, g);
         }
     } else if (warp == kLoaderWarp) {
-        // ---------------------------------------------------------------- loader warp
+        // ---------------------------------------------------------------- loader warp (runs ahead of the setup)
         int ck = 0;
-        for (int gk = 0; gk < n_groups && !cl.abort_flag; ++gk) {
-            const int g = gk % kSlots;
-            if (!mbar_wait_warp(&cl.grp_full[g], (gk / kSlots) & 1)) { raise_abort(cl, ctr); break; }
-            const Meta m = cl.meta[g];
-            const PairDev &P = pairs[m.pair];
-            const ImageDev &B = imgs[P.b];
-            const CUtensorMap *dmap = &maps[P.b].desc;
-            const CUtensorMap *rmap = m.colwise ? &maps[P.b].rec : &maps[P.b].rec_r;
-            const int32_t *excl = cl.run_excl[g];
-            bool ok = true;
-            for (int c = 0; c < m.nchunks; ++c, ++ck) {
-                const int s = ck % kStages;
-                if (!mbar_wait_warp(&cl.stage_empty[s], ((ck / kStages) & 1) ^ 1)) { ok = false; break; }
-                // two consecutive slots per lane: record row (walk layout) and descriptor row (column-major)
-                int rrow[2], drow[2];
+        bool ok = true;
+        GroupDesc dnext;
+        if (n_groups > 0) dnext = gdesc[first];
+        for (int gk = 0; gk < n_groups && ok && !cl.abort_flag; ++gk) {
+            const GroupDesc dcur = dnext;
+            if (gk + 1 < n_groups) dnext = gdesc[first + (int64_t)(gk + 1) * stride];
+            const int total = dcur.total, nchunks = (total + kN - 1) / kN, full = dcur.flags & 1;
+            const CUtensorMap *dmap = &maps[dcur.b_slot].desc_tile;
+            const CUtensorMap *rmap = &maps[dcur.b_slot].rec_tile;
+            const CUtensorMap *gmap = &maps[dcur.b_slot].desc_row;
+            const int4 *brec = dcur.b_rec;
+            const int32_t *gs = stream + dcur.off;
+            // positions of chunk c are loaded two chunks ahead, so their latency overlaps earlier chunks
+            auto fetch = [&](int c, int (&pp)[2]) {
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int p = c * kN + 2 * lane + e;
-                    rrow[e] = B.n;   // sentinel record (NaN coordinates)
-                    drow[e] = 0;
-                    if (p < m.total) {
-                        int pos = p;
-                        if (!m.walk_full) {
-                            int lo = 0, hi = kMaxRuns;
-                            while (hi - lo > 1) {
-                                const int mid = (lo + hi) >> 1;
-                                if (excl[mid] <= p) lo = mid;
-                                else hi = mid;
-                            }
-                            pos = cl.run_start[g][lo] + (p - excl[lo]);
-                        }
-                        rrow[e] = pos;
-                        drow[e] = m.colwise ? pos : B.idx_r[pos];
-                    }
+                    pp[e] = p < total ? (full ? p : __ldg(gs + p)) : -1;
                 }
-                const int r2 = __shfl_down_sync(0xffffffffu, rrow[0], 1), r3 = __shfl_down_sync(0xffffffffu, rrow[1], 1);
-                const int d2 = __shfl_down_sync(0xffffffffu, drow[0], 1), d3 = __shfl_down_sync(0xffffffffu, drow[1], 1);
-                if (lane == 0) mbar_expect_tx(&cl.stage_full[s], kChunkTx);
-                __syncwarp();
-                if ((lane & 1) == 0) {
-                    const int quad = lane >> 1;   // slots 4 quad .. 4 quad + 3
-                    const uint32_t bbase = smem_u32(base + kOffB + s * 2 * kBHalf) + 4 * quad * 128;
-                    tma_gather4(bbase, dmap, 0, drow[0], drow[1], d2, d3, &cl.stage_full[s], B.n, &ctr->errors);
-                    tma_gather4(bbase + kBHalf, dmap, 64, drow[0], drow[1], d2, d3, &cl.stage_full[s], B.n,
+            };
+            int pn1[2] = {-1, -1}, pn2[2] = {-1, -1};
+            if (!full) {
+                fetch(0, pn1);
+                fetch(1, pn2);
+            }
+            for (int c = 0; c < nchunks; ++c, ++ck) {
+                const int s = ck % kStages;
+                int pcur[2] = {pn1[0], pn1[1]};
+                if (!full) {
+                    pn1[0] = pn2[0];
+                    pn1[1] = pn2[1];
+                    fetch(c + 2, pn2);
+                }
+                if (!mbar_wait_warp(&cl.stage_empty[s], ((ck / kStages) & 1) ^ 1)) { ok = false; break; }
+                const uint32_t bstage = smem_u32(base + kOffB + s * 2 * kBHalf);
+                const uint32_t rstage = smem_u32(base + kOffRec + s * kRecStage);
+                if (full) {
+                    // contiguous rows: TMA tile loads (rows past the image come back as NaN records)
+                    if (lane == 0) {
+                        mbar_expect_tx(&cl.stage_full[s], kChunkTx);
+                        tma_tile(bstage, dmap, 0, c * kN, &cl.stage_full[s], 1024u, &ctr->errors);
+                        tma_tile(bstage + kBHalf, dmap, 64, c * kN, &cl.stage_full[s], 1024u, &ctr->errors);
+                        tma_tile(rstage, rmap, 0, c * kN, &cl.stage_full[s], 128u, &ctr->errors);
+                    } else {
+                        mbar_arrive(&cl.stage_full[s]);
+                    }
+                } else {
+                    // scattered rows: TMA gather4 of the descriptors (lane: four rows of one K half), cp.async of
+                    // the records; past the end of the stream: descriptor row 0, the NaN sentinel record
+                    int32_t *lrows = cl.lrows[s];
+                    lrows[2 * lane] = pcur[0] >= 0 ? pcur[0] : 0;
+                    lrows[2 * lane + 1] = pcur[1] >= 0 ? pcur[1] : 0;
+                    if (lane == 0) mbar_expect_tx_only(&cl.stage_full[s], (uint32_t)kN * 256u);
+                    __syncwarp();
+                    const int quad = lane & 15, h = lane >> 4;
+                    const int4 r4 = *reinterpret_cast<const int4 *>(lrows + 4 * quad);
+                    tma_gather4(bstage + h * kBHalf + quad * 512, gmap, 64 * h, r4, &cl.stage_full[s], dcur.b_n,
                                 &ctr->errors);
-                    tma_gather4(smem_u32(base + kOffRec + s * kRecStage + quad * 128), rmap, 0, rrow[0], rrow[1], r2, r3,
-                                &cl.stage_full[s], B.n + 1, &ctr->errors);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int slot = 2 * lane + e;
+                        cp_async16(rstage + slot * 16, brec + (pcur[e] >= 0 ? pcur[e] : dcur.b_n));
+                    }
+                    cp_async_arrive(&cl.stage_full[s]);
                 }
             }
-            if (!ok) { raise_abort(cl, ctr); break; }
-            if (lane == 0) mbar_arrive(&cl.grp_empty[g]);   // the loader is done with the run table
         }
+        if (!ok) raise_abort(cl, ctr);
     } else if (warp == kMmaWarp) {
         // ---------------------------------------------------------------- MMA warp (one thread issues)
         if (lane == 0) {
@@ -494,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             for (int gk = 0; gk < n_groups && !cl.abort_flag; ++gk) {
                 const int g = gk % kSlots;
                 if (!mbar_wait(&cl.grp_full[g], (gk / kSlots) & 1)) { raise_abort(cl, ctr); break; }
-                const int nchunks = cl.meta[g].nchunks;
+                const int nchunks = (cl.desc[g].total + kN - 1) / kN;
                 const uint32_t abase = smem_u32(base + kOffA + g * 2 * kAHalf);
                 bool ok = true;
                 for (int c = 0; c < nchunks; ++c, ++ck) {
@@ -502,6 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                     if (!mbar_wait(&cl.stage_full[s], (ck / kStages) & 1) ||
                         !mbar_wait(&cl.acc_empty[b], ((ck >> 1) & 1) ^ 1)) { ok = false; break; }
                     tc_fence_after();
+                    fence_proxy_async();   // cp.async writes (generic proxy) -> tensor-core reads (async proxy)
                     const uint32_t bbase = smem_u32(base + kOffB + s * 2 * kBHalf);
 #pragma unroll
                     for (int ks = 0; ks < 8; ++ks) {
@@ -526,18 +466,26 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         for (int gk = 0; gk < n_groups && !cl.abort_flag; ++gk) {
             const int g = gk % kSlots;
             if (!mbar_wait_warp(&cl.grp_full[g], (gk / kSlots) & 1)) { raise_abort(cl, ctr); break; }
-            const Meta m = cl.meta[g];
-            const PairDev &P = pairs[m.pair];
-            const float la = cl.ln[g][row][0], lb = cl.ln[g][row][1], lc = cl.ln[g][row][2];
-            const float llo = cl.ln[g][row][3], lhi = cl.ln[g][row][4], qx = cl.ln[g][row][5], qy = cl.ln[g][row][6];
+            const GroupDesc &gd = cl.desc[g];
+            const int total = gd.total, nchunks = (total + kN - 1) / kN;
+            const float d = gd.d;
             const int out_i = cl.rinfo[g][row][0];
+            const float qx = cl.qxy[g][row].x, qy = cl.qxy[g][row].y;
+            float la = 0.0f, lb = 0.0f, lc = 0.0f, llo = -1.0f, lhi = -1.0f;   // no query: never inside
+            if (out_i >= 0) {
+                const BandLine bl = band_line(gd.F, qx, qy, d, gd.W, gd.H);
+                la = bl.a; lb = bl.b; lc = bl.c; llo = bl.thr_lo; lhi = bl.thr_hi;
+                // whole-image rows accept every real keypoint; FP64-only rows send every real keypoint to the FP64
+                // decision; both use the zero line (s = 0 for real keypoints, NaN for the sentinel record)
+                if (bl.mode == kBandAll) { llo = INFINITY; lhi = INFINITY; la = lb = lc = 0.0f; }
+                else if (bl.mode == kBandSlow) { llo = -1.0f; lhi = INFINITY; la = lb = lc = 0.0f; }
+            }
             // key = (|a'|^2 + |b'|^2 - 2 dot) * 256 + column with dot taken from the f32 accumulator through
             // bits = float_bits(dot + 1.5 * 2^23) = 0x4B400000 + dot, and 512 * 0x4B400000 = 2^31 (mod 2^32)
             const uint32_t Rc = (uint32_t)cl.rinfo[g][row][1] + 0x80000000u + (uint32_t)(32 * h);
-            const float d = P.d;
             int k1 = INT_MAX, k2 = INT_MAX, j1 = 0, cnt = 0;
             bool ok = true;
-            for (int c = 0; c < m.nchunks; ++c, ++ck) {
+            for (int c = 0; c < nchunks; ++c, ++ck) {
                 const int s = ck % kStages, b = ck & 1;
                 if (!mbar_wait_warp(&cl.acc_full[b], (ck >> 1) & 1)) { ok = false; break; }
                 tc_fence_after();
@@ -547,33 +495,45 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&cl.acc_empty[b]);
                 if (!mbar_wait_warp(&cl.stage_full[s], (ck / kStages) & 1)) { ok = false; break; }   // records visible
-                // record of column t: quad slot t / 4 (128 bytes each), entry t % 4
-                const int4 *rs = rec + (s * kRecStage + 1024 * h) / 16;
+                const int4 *rs = rec + (s * kRecStage) / 16 + 32 * h;
                 const int k1_before = k1;
-                if (32 * h < m.total - c * kN) {
+                if (32 * h < total - c * kN) {
+                    // two interleaved top-2 accumulators (even / odd columns) shorten the dependency chain; elements
+                    // within the FP32 error margin are counted as outside here and re-decided below
+                    int ka1 = k1, ka2 = k2, kb1 = INT_MAX, kb2 = INT_MAX;
+                    uint32_t und = 0u;
 #pragma unroll
                     for (int jj = 0; jj < 32; ++jj) {
-                        const int4 r = rs[(jj >> 2) * 8 + (jj & 3)];
-                        const float x = __int_as_float(r.x), y = __int_as_float(r.y);
-                        const float sv = fmaf(la, x, fmaf(lb, y, lc));
+                        const int4 r = rs[jj];
+                        const float sv = fmaf(la, __int_as_float(r.x), fmaf(lb, __int_as_float(r.y), lc));
                         const float as = fabsf(sv);
-                        bool inb = as <= llo;
-                        if (!inb && as <= lhi) {
-                            inb = band_exact_call(cl.F[g], qx, qy, d, x, y);
-                            ++my_redec;
-                        }
+                        const bool inb = as <= llo;
+                        und |= (as <= lhi && !inb) ? (1u << jj) : 0u;
                         const uint32_t bits = (uint32_t)__float_as_int(__int_as_float(v[jj]) + 12582912.0f);
                         const int key = (int)(Rc + (uint32_t)r.z + (uint32_t)jj - 512u * bits);
                         const int km = inb ? key : INT_MAX;
-                        k2 = min(k2, max(k1, km));
-                        k1 = min(k1, km);
+                        if (jj & 1) { kb2 = min(kb2, max(kb1, km)); kb1 = min(kb1, km); }
+                        else { ka2 = min(ka2, max(ka1, km)); ka1 = min(ka1, km); }
                         cnt += inb;
                     }
+                    k2 = min(min(ka2, kb2), max(ka1, kb1));
+                    k1 = min(ka1, kb1);
+                    if (und) {   // rare: FP64 re-decision, operation by operation as the reference definition
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            if (!((und >> jj) & 1u)) continue;
+                            const int4 r = rs[jj];
+                            ++my_redec;
+                            if (!band_exact_call(gd.F, qx, qy, d, __int_as_float(r.x), __int_as_float(r.y))) continue;
+                            const uint32_t bits = (uint32_t)__float_as_int(__int_as_float(v[jj]) + 12582912.0f);
+                            const int key = (int)(Rc + (uint32_t)r.z + (uint32_t)jj - 512u * bits);
+                            k2 = min(k2, max(k1, key));
+                            k1 = min(k1, key);
+                            ++cnt;
+                        }
+                    }
                 }
-                if (k1 < k1_before) {
-                    const int t = (k1 & 255) - 32 * h;
-                    j1 = rs[(t >> 2) * 8 + (t & 3)].w;
-                }
+                if (k1 < k1_before) j1 = rs[(k1 & 255) - 32 * h].w;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&cl.stage_empty[s]);
             }
@@ -594,9 +554,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 cnt += mg[3];
                 if (out_i >= 0) {
                     const int64_t D1 = k1 >> 8, D2 = k2 >> 8;
+                    const int64_t pp = gd.p, qq = gd.q;
                     int outj = -1;
-                    if (cnt >= 2 && (int64_t)P.q * P.q * D1 < (int64_t)P.p * P.p * D2) outj = imgs[P.b].perm[j1];
-                    match_j[P.qoff + out_i] = outj;
+                    if (cnt >= 2 && qq * qq * D1 < pp * pp * D2) outj = __ldg(gd.b_perm + j1);
+                    match_j[gd.qoff + out_i] = outj;
                     my_cand += (unsigned long long)cnt;
                 }
             }
@@ -609,12 +570,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         my_cand += __shfl_xor_sync(0xffffffffu, my_cand, o);
-        my_exam += __shfl_xor_sync(0xffffffffu, my_exam, o);
         my_redec += __shfl_xor_sync(0xffffffffu, my_redec, o);
     }
     if (lane == 0) {
         atomicAdd(&cl.stat[0], my_cand);
-        atomicAdd(&cl.stat[1], my_exam);
         atomicAdd(&cl.stat[2], my_redec);
     }
     tc_fence_before();
@@ -626,7 +585,6 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     if (tid == 0) {
         BatchCounters *cc = ctr + (blockIdx.x % kCounterShards);
         atomicAdd(&cc->candidates, cl.stat[0]);
-        atomicAdd(&cc->examined, cl.stat[1]);
         atomicAdd(&cc->redecided, cl.stat[2]);
     }
 }
@@ -647,19 +605,19 @@ cudaError_t prepare()
 
 int match_tc_blocks_per_sm() { return 1; }
 
-int match_tc_max_grid_lines() { return kMaxRuns; }
+int match_tc_max_grid_lines() { return kMaxGridLines; }
 
-cudaError_t launch_match_tc(const ImageDev *imgs, const PairDev *pairs, const TmaMaps *maps, const int64_t *item_off,
-                            int32_t n_pairs, const int32_t *qorder, int64_t item_begin, int64_t item_end, int32_t grid,
-                            int32_t *match_j, BatchCounters *ctr, cudaStream_t st)
+cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const int32_t *grows, const int32_t *stream,
+                            int64_t item_begin, int64_t item_end, int32_t grid, int32_t *match_j, BatchCounters *ctr,
+                            cudaStream_t st)
 {
     const int64_t n = item_end - item_begin;
     if (n <= 0) return cudaSuccess;
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
     const int64_t g = std::max<int64_t>(1, grid > 0 ? std::min<int64_t>(grid, n) : n);
-    match_tc_kernel<<<(unsigned)g, kThreads, kSmemBytes, st>>>(imgs, pairs, maps, item_off, n_pairs, qorder, item_begin,
-                                                             item_end, match_j, ctr);
+    match_tc_kernel<<<(unsigned)g, kThreads, kSmemBytes, st>>>(maps, gdesc, grows, stream, item_begin, item_end, match_j,
+                                                             ctr);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,22 @@ struct GpuEngine {
     void collect(int s, std::vector<SchedRequest *> &batch)
     {
         SlotState &S = slots[s];
+        if (!S.failed) {
+            // a candidate-stream overflow invalidates the batch: grow the buffer and run it again (rare)
+            gm_stats tmp;
+            engine_stats(ctx, S.ws, tmp);
+            for (int attempt = 0; S.ws.overflow && attempt < 2; ++attempt) {
+                std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+                S.ws.stream_cap = S.ws.stream_used + S.ws.stream_used / 4 + 1024;
+                if (engine_launch(ctx, S.ws, static_cast<int32_t *>(S.ws.h_rows.p)) != GM_OK ||
+                    cudaStreamSynchronize(S.ws.stream) != cudaSuccess) {
+                    S.failed = true;
+                    break;
+                }
+                engine_stats(ctx, S.ws, tmp);
+            }
+            if (S.ws.overflow || tmp.n_device_errors) S.failed = true;
+        }
         if (S.failed) {
             for (int k : S.idx)
                 if (batch[k]->status == GM_OK) batch[k]->status = GM_ERR_CUDA;

@@ -212,6 +212,23 @@ def test_facade_full_batch_sampled(gm, facade_scene):
             np.testing.assert_array_equal(rows2[k], rows[k], err_msg=f"{name} pair {k}")
 
 
+def test_stream_buffer_overflow_reruns(gm, facade_scene):
+    """A candidate-stream buffer far too small for the batch forces the grow-and-rerun path; results unchanged."""
+    sc = facade_scene
+    pairs = sc.pairs[:40]
+    rows, st = _gpu_rows(gm, sc, pairs=pairs)
+    with gm.Context(device=0) as ctx:
+        ctx.set_option(gm.GM_OPT_STREAM_CAP, 1000)
+        for k in sorted({p.a for p in pairs} | {p.b for p in pairs}):
+            ctx.put_image(k, sc.images[k])
+        off, m = ctx.match_pairs(pairs)
+        st2 = ctx.stats()
+    got = gm.split_matches(off, m)
+    for k in range(len(pairs)):
+        np.testing.assert_array_equal(got[k], rows[k])
+    assert st2["n_candidates"] == st["n_candidates"]
+
+
 def test_serving_alone_equals_mix(gm, facade_scene):
     sc = facade_scene
     pairs = sc.pairs[:60]
