@@ -236,7 +236,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     const int32_t P = ws.n_pairs;
     const int64_t Q = ws.Q;
     const size_t pair_bytes = align_up(sizeof(PairDev) * std::max(P, 1), 256);
-    const size_t tab_bytes = pair_bytes + sizeof(int64_t) * (P + 1);
+    const size_t tab_bytes = 2 * pair_bytes + sizeof(int64_t) * (P + 1);
     gm_status st;
     if ((st = ensure_dev(ctx, ws.d_tab, tab_bytes)) != GM_OK) return st;
     if ((st = ensure_dev(ctx, ws.d_qorder, sizeof(int32_t) * std::max<int64_t>(Q, 1))) != GM_OK) return st;
@@ -262,13 +262,24 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
 
     char *hs = static_cast<char *>(ws.h_tab.p);
     std::memcpy(hs, ws.pd.data(), sizeof(PairDev) * P);
-    int64_t *h_item_off = reinterpret_cast<int64_t *>(hs + pair_bytes);
+    // processing order: pairs grouped by image B (then A), so that the groups in flight at the same time read the
+    // same B descriptors and these stay in L2; results stay indexed by the caller's pair order
+    ws.proc.resize(P);
+    for (int32_t k = 0; k < P; ++k) ws.proc[k] = k;
+    std::stable_sort(ws.proc.begin(), ws.proc.end(), [&](int32_t x, int32_t y) {
+        const PairDev &u = ws.pd[x], &v = ws.pd[y];
+        return u.b != v.b ? u.b < v.b : u.a < v.a;
+    });
+    PairDev *h_proc = reinterpret_cast<PairDev *>(hs + pair_bytes);
+    for (int32_t k = 0; k < P; ++k) h_proc[k] = ws.pd[ws.proc[k]];
+    int64_t *h_item_off = reinterpret_cast<int64_t *>(hs + 2 * pair_bytes);
     h_item_off[0] = 0;
-    for (int32_t k = 0; k < P; ++k) h_item_off[k + 1] = h_item_off[k] + (ws.pd[k].n_a + qpi - 1) / qpi;
+    for (int32_t k = 0; k < P; ++k) h_item_off[k + 1] = h_item_off[k] + (h_proc[k].n_a + qpi - 1) / qpi;
 
     char *ds = static_cast<char *>(ws.d_tab.p);
-    const PairDev *d_pairs = reinterpret_cast<const PairDev *>(ds);
-    const int64_t *d_item_off = reinterpret_cast<const int64_t *>(ds + pair_bytes);
+    const PairDev *d_pairs = reinterpret_cast<const PairDev *>(ds);                  // caller's order
+    const PairDev *d_proc = reinterpret_cast<const PairDev *>(ds + pair_bytes);      // processing order
+    const int64_t *d_item_off = reinterpret_cast<const int64_t *>(ds + 2 * pair_bytes);
     int32_t *qorder = static_cast<int32_t *>(ws.d_qorder.p);
     int32_t *match_j = static_cast<int32_t *>(ws.d_matchj.p);
     BatchCounters *ctr = static_cast<BatchCounters *>(ws.d_ctr.p);
@@ -294,13 +305,13 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     const int32_t grid = ctx->num_sms * bps;
     auto launch_match = [&](int64_t i0, int64_t i1, int32_t gsz) -> cudaError_t {
         if (path == GM_PATH_SIMT)
-            return launch_match_simt(imgs, d_pairs, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
+            return launch_match_simt(imgs, d_proc, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
         if (path == GM_PATH_TC)
             return launch_match_tc(static_cast<const TmaMaps *>(ctx->d_maps.p),
                                    static_cast<const GroupDesc *>(ws.d_grec.p),
                                    static_cast<const int32_t *>(ws.d_grows.p), static_cast<const int32_t *>(ws.d_stream.p),
                                    i0, i1, gsz > 0 ? gsz : ctx->num_sms, match_j, ctr, s);
-        return launch_match_mma(mt, imgs, d_pairs, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
+        return launch_match_mma(mt, imgs, d_proc, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
     };
 
     ws.launches = 0;
@@ -311,9 +322,9 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
         // plain form: every pair gets its own launches (one block per work item)
         GM_CUDA(cudaEventRecord(ws.ev[1], s));
         for (int32_t k = 0; k < P; ++k) {
-            GM_CUDA(launch_order(imgs, d_pairs + k, 1, qorder, s));
+            GM_CUDA(launch_order(imgs, d_proc + k, 1, qorder, s));
             if (path == GM_PATH_TC) {
-                GM_CUDA(launch_stream(imgs, d_pairs, d_item_off, P, qorder, h_item_off[k], h_item_off[k + 1],
+                GM_CUDA(launch_stream(imgs, d_proc, d_item_off, P, qorder, h_item_off[k], h_item_off[k + 1],
                                       static_cast<GroupDesc *>(ws.d_grec.p), static_cast<int32_t *>(ws.d_grows.p),
                                       static_cast<int32_t *>(ws.d_stream.p), ws.stream_cap, stream_used, ctr, s));
                 ++ws.launches;
@@ -325,7 +336,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     } else {
         GM_CUDA(launch_order(imgs, d_pairs, P, qorder, s));
         if (path == GM_PATH_TC) {
-            GM_CUDA(launch_stream(imgs, d_pairs, d_item_off, P, qorder, 0, n_items, static_cast<GroupDesc *>(ws.d_grec.p),
+            GM_CUDA(launch_stream(imgs, d_proc, d_item_off, P, qorder, 0, n_items, static_cast<GroupDesc *>(ws.d_grec.p),
                                   static_cast<int32_t *>(ws.d_grows.p), static_cast<int32_t *>(ws.d_stream.p),
                                   ws.stream_cap, stream_used, ctr, s));
             ++ws.launches;
@@ -382,7 +393,7 @@ gm_status gm_create(const gm_config *cfg, gm_ctx **out)
     if (!cfg || !out) return fail(GM_ERR_INVALID, "gm_create: null argument");
     *out = nullptr;
     if (cfg->path < GM_PATH_AUTO || cfg->path > GM_PATH_SIMT) return fail(GM_ERR_INVALID, "gm_create: bad path");
-    int cell_shift = 4;
+    int cell_shift = 3;   // 8 px cells unless configured
     if (cfg->cell_px) {
         int c = cfg->cell_px, sh = 0;
         while ((1 << sh) < c) ++sh;

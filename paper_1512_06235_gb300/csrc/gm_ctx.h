@@ -38,7 +38,7 @@ struct ImageSlot {
 // Everything one batch needs on the device and in pinned host memory.  The synchronous API owns one; every
 // serving slot owns its own, so batches on different slots can be in flight at the same time.
 struct Workspace {
-    DevBuf d_tab;        // pair table, then the work-item table (pair, first query) of the match kernel
+    DevBuf d_tab;        // pair table (caller's order), pair table (processing order), work-item offsets
     DevBuf d_qorder;     // int32 [Q] query order per pair
     DevBuf d_matchj;     // int32 [Q] per-query decision (original B index or -1), indexed by original A index
     DevBuf d_counts;     // int32 [P]
@@ -58,6 +58,7 @@ struct Workspace {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // plan of the batch being run
     std::vector<PairDev> pd;
+    std::vector<int32_t> proc;   // processing order of the pairs (grouped by image B)
     int64_t Q = 0, nitems = 0;
     int32_t n_pairs = 0;
     int32_t launches = 0;
@@ -78,7 +79,7 @@ struct gm_ctx {
     uint64_t budget = 0;
     int32_t path = GM_PATH_AUTO;
     int32_t schedule = 0;
-    int32_t cell_shift = 4;
+    int32_t cell_shift = 3;
     int32_t graph = 0;
     int32_t max_inflight = 2;
     int32_t num_sms = 0;

@@ -6,16 +6,16 @@
 //
 //   setup warps (2, alternate groups): the gather (cp.async, two 256-byte rows per warp instruction) of the
 //       group's 128 query descriptors (recentred, fp16: integers in [-128, 127] are exact) into the group's A tile
-//       (128-byte-swizzled K-major layout), and the
-//       queries' coordinates, norms and output indices into shared memory.  Everything the CTA needs about a group
-//       comes from its descriptor (gm_stream.cu); the setup warp loads it before it waits for the slot;
-//   loader warp: cuts the group's candidate stream (computed beforehand by gm_stream.cu: the chord-bounded cell
-//       walk of the whole group) into 64-row chunks and brings the fp16 descriptor rows (two K halves) and a 16-byte
-//       record per candidate (x, y, |b'|^2 * 256, position) into a 4-stage ring: scattered rows of banded groups by
-//       cp.async (completion through cp.async.mbarrier.arrive), the contiguous rows of whole-image groups by TMA
-//       tile loads (64-row boxes, 128-byte swizzle; rows past the image read as NaN records); slots past the end of
-//       a stream get the image's NaN sentinel record.  It reads the descriptors itself and runs ahead of the setup
-//       warps;
+//       (128-byte-swizzled K-major layout), the queries' coordinates, norms and output indices, and the group's
+//       candidate stream (positions computed beforehand by gm_stream.cu: the chord-bounded cell walk of the whole
+//       group), all into the group's slot in shared memory.  Everything the CTA needs about a group comes from its
+//       descriptor; the setup warp loads it before it waits for the slot;
+//   loader warp: cuts the staged stream into 64-row chunks and brings the fp16 descriptor rows (two K halves) and
+//       a 16-byte record per candidate (x, y, |b'|^2 * 256, position) into a 4-stage ring: scattered rows of banded
+//       groups by TMA gather4 (records by cp.async; completion through cp.async.mbarrier.arrive), the contiguous
+//       rows of whole-image groups by TMA tile loads (64-row boxes, 128-byte swizzle; rows past the image read as
+//       NaN records); slots past the end of a stream get the image's NaN sentinel record.  Positions come from
+//       shared memory, so global-memory latency stays off the loader's issue path;
 //   MMA warp (one elected thread): eight tcgen05.mma.kind::f16 per chunk (M = 128, N = 64, K = 16 each), f32
 //       accumulation into one of two tensor-memory buffers.  Products are integers of magnitude <= 2^14 and partial
 //       sums <= 2^21 < 2^24, so the accumulator holds the exact integer dot product a'.b';
@@ -46,6 +46,7 @@ constexpr int kM = 128;             // queries per group (tensor-memory lanes)
 constexpr int kN = 64;              // candidates per chunk
 constexpr int kStages = 4;          // candidate chunks in flight
 constexpr int kSlots = 2;           // query groups in flight
+constexpr int kPosCap = 8192;       // candidate positions a slot stages in shared memory (multiple of kN)
 constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
 constexpr int kEpiWarps = 8;
 constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;
@@ -69,7 +70,7 @@ struct Ctl {
     int32_t rinfo[kSlots][kM][2];    // original A index (-1: no query), |a'|^2 * 256
     int32_t aidx[kSlots][kM];        // A rows to gather
     int32_t merge[kSlots][kM][4];
-    alignas(16) int32_t lrows[kStages][kN];   // loader: source rows of the chunk in each stage
+    alignas(16) int32_t pos[kSlots][kPosCap];   // the group's candidate positions (staged by the setup warp)
     uint64_t stage_full[kStages], stage_empty[kStages], acc_full[2], acc_empty[2];
     uint64_t grp_full[kSlots], grp_empty[kSlots], merge_ready[kSlots];
     uint32_t tmem_base;
@@ -183,12 +184,13 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 // 128-byte swizzle of a K-major tile: row r, 16-byte chunk c of one K half (rows are 128 bytes).
 __device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
-// Gathers rows into a K-major, 128-byte-swizzled fp16 tile (two K halves of half_bytes each).  rows[k] (shared
-// memory) is the source row of tile row k.  One warp instruction copies two whole 256-byte rows (lanes 0-15: row
-// 2i, lanes 16-31: row 2i + 1), so every request reads whole 128-byte lines; the swizzle term of a lane repeats
-// every four instructions and is precomputed.
+// Gathers rows into a K-major, 128-byte-swizzled fp16 tile (two K halves of half_bytes each): tile row r is source
+// row rows[r] for r < lim and row 0 past it (rows may point to shared or global memory; entries past lim are not
+// read).  One warp instruction copies two whole 256-byte rows (lanes 0-15: row 2i, lanes 16-31: row 2i + 1), so
+// every request reads whole 128-byte lines; a lane's swizzled destination repeats every four instructions (plus
+// 1024 bytes) and is computed once.
 __device__ __forceinline__ void gather_rows(uint32_t tile, int half_bytes, int nrows, const uint16_t *__restrict__ src,
-                                            const int32_t *rows)
+                                            const int32_t *rows, int lim)
 {
     const int lane = threadIdx.x & 31;
     const int sub = lane >> 4, c = lane & 15;   // c: 16-byte chunk of the 256-byte row
@@ -196,15 +198,13 @@ __device__ __forceinline__ void gather_rows(uint32_t tile, int half_bytes, int n
     const char *s0 = reinterpret_cast<const char *>(src) + c * 16;
     uint32_t dst[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {   // tile row 2m + sub (+ 8 per four instructions): chunk cc ^ (row & 7)
-        const int r = 2 * m + sub;
-        dst[m] = tile + h * half_bytes + sw128(r, cc);
-    }
+    for (int m = 0; m < 4; ++m) dst[m] = tile + h * half_bytes + sw128(2 * m + sub, cc);
     for (int i0 = 0; i0 < nrows / 2; i0 += 4) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int r = 2 * (i0 + m) + sub;
-            cp_async16(dst[m] + i0 * 256, s0 + (int64_t)rows[r] * (kDim * 2));
+            const int row = r < lim ? rows[r] : 0;
+            cp_async16(dst[m] + i0 * 256, s0 + (int64_t)row * (kDim * 2));
         }
     }
 }
@@ -256,6 +256,13 @@ __device__ __forceinline__ void raise_abort(Ctl &cl, BatchCounters *ctr)
     }
 }
 
+// A banded group whose candidate stream fits the slot (and starts on a 16-byte boundary, as gm_stream.cu lays
+// them out) has its positions staged in shared memory; otherwise the loader reads them from global memory.
+__device__ __forceinline__ bool positions_staged(const GroupDesc &d)
+{
+    return (d.flags & 3) == 0 && d.total > 0 && d.total <= kPosCap && (d.off & 3) == 0;
+}
+
 // ------------------------------------------------------------------------------------------------ setup role
 // Query data of one group, loaded into registers before the slot is free (rows lane + 32 t).
 struct SetupData {
@@ -281,7 +288,8 @@ __device__ __forceinline__ void setup_load(SetupData &sd, const GroupDesc *__res
 }
 
 // Writes the group into slot g and gathers its A tile (the slot must be free).
-__device__ __forceinline__ void setup_store(Ctl &cl, unsigned char *base, const SetupData &sd, int g)
+__device__ __forceinline__ void setup_store(Ctl &cl, unsigned char *base, const SetupData &sd, int g,
+                                            const int32_t *__restrict__ stream)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -296,7 +304,13 @@ __device__ __forceinline__ void setup_store(Ctl &cl, unsigned char *base, const 
     __syncwarp();
     // A tile: 128 rows, two per warp instruction; every lane's copies complete into grp_full (noinc arrivals),
     // plus one ordinary arrival that releases the slot data written above
-    gather_rows(smem_u32(base + kOffA + g * 2 * kAHalf), kAHalf, kM, sd.d.a_desc, cl.aidx[g]);
+    gather_rows(smem_u32(base + kOffA + g * 2 * kAHalf), kAHalf, kM, sd.d.a_desc, cl.aidx[g], kM);
+    if (positions_staged(sd.d)) {   // the candidate stream, 16 bytes per copy (the tail of the last copy is unused)
+        const int4 *src = reinterpret_cast<const int4 *>(stream + sd.d.off);
+        const uint32_t dst = smem_u32(cl.pos[g]);
+        const int n16 = (sd.d.total + 3) >> 2;
+        for (int k = lane; k < n16; k += 32) cp_async16(dst + 16 * k, src + k);
+    }
     cp_async_arrive(&cl.grp_full[g]);
     if (lane == 0) mbar_arrive(&cl.grp_full[g]);
 }
@@ -353,44 +367,27 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             SetupData sd;
             setup_load(sd, gdesc, grows, first + (int64_t)gk * stride);   // in flight while the slot drains
             if (!mbar_wait_warp(&cl.grp_empty[g], ((gk / kSlots) & 1) ^ 1)) { raise_abort(cl, ctr); break; }
-            setup_store(cl, base, sd, g);
+            setup_store(cl, base, sd, g, stream);
         }
     } else if (warp == kLoaderWarp) {
-        // ---------------------------------------------------------------- loader warp (runs ahead of the setup)
+        // ---------------------------------------------------------------- loader warp
         int ck = 0;
         bool ok = true;
-        GroupDesc dnext;
-        if (n_groups > 0) dnext = gdesc[first];
         for (int gk = 0; gk < n_groups && ok && !cl.abort_flag; ++gk) {
-            const GroupDesc dcur = dnext;
-            if (gk + 1 < n_groups) dnext = gdesc[first + (int64_t)(gk + 1) * stride];
-            const int total = dcur.total, nchunks = (total + kN - 1) / kN, full = dcur.flags & 1;
-            const CUtensorMap *dmap = &maps[dcur.b_slot].desc_tile;
-            const CUtensorMap *rmap = &maps[dcur.b_slot].rec_tile;
-            const CUtensorMap *gmap = &maps[dcur.b_slot].desc_row;
-            const int4 *brec = dcur.b_rec;
-            const int32_t *gs = stream + dcur.off;
-            // positions of chunk c are loaded two chunks ahead, so their latency overlaps earlier chunks
-            auto fetch = [&](int c, int (&pp)[2]) {
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int p = c * kN + 2 * lane + e;
-                    pp[e] = p < total ? (full ? p : __ldg(gs + p)) : -1;
-                }
-            };
-            int pn1[2] = {-1, -1}, pn2[2] = {-1, -1};
-            if (!full) {
-                fetch(0, pn1);
-                fetch(1, pn2);
-            }
+            const int g = gk % kSlots;
+            // the group's descriptor and staged positions are in the slot once the setup warp has filled it
+            if (!mbar_wait_warp(&cl.grp_full[g], (gk / kSlots) & 1)) { ok = false; break; }
+            const GroupDesc &dg = cl.desc[g];
+            const int total = dg.total, nchunks = (total + kN - 1) / kN, full = dg.flags & 1, b_n = dg.b_n;
+            const CUtensorMap *dmap = &maps[dg.b_slot].desc_tile;
+            const CUtensorMap *rmap = &maps[dg.b_slot].rec_tile;
+            const CUtensorMap *gmap = &maps[dg.b_slot].desc_row;
+            const int4 *brec = dg.b_rec;
+            const bool staged = positions_staged(dg);
+            const int32_t *gs = stream + dg.off;
+            const int32_t *ps = cl.pos[g];
             for (int c = 0; c < nchunks; ++c, ++ck) {
                 const int s = ck % kStages;
-                int pcur[2] = {pn1[0], pn1[1]};
-                if (!full) {
-                    pn1[0] = pn2[0];
-                    pn1[1] = pn2[1];
-                    fetch(c + 2, pn2);
-                }
                 if (!mbar_wait_warp(&cl.stage_empty[s], ((ck / kStages) & 1) ^ 1)) { ok = false; break; }
                 const uint32_t bstage = smem_u32(base + kOffB + s * 2 * kBHalf);
                 const uint32_t rstage = smem_u32(base + kOffRec + s * kRecStage);
@@ -405,22 +402,25 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                         mbar_arrive(&cl.stage_full[s]);
                     }
                 } else {
-                    // scattered rows: TMA gather4 of the descriptors (lane: four rows of one K half), cp.async of
-                    // the records; past the end of the stream: descriptor row 0, the NaN sentinel record
-                    int32_t *lrows = cl.lrows[s];
-                    lrows[2 * lane] = pcur[0] >= 0 ? pcur[0] : 0;
-                    lrows[2 * lane + 1] = pcur[1] >= 0 ? pcur[1] : 0;
+                    // scattered rows: TMA gather4 of the descriptor rows (lane: four rows of one K half) and
+                    // cp.async of the records (lane: slots 2 lane, 2 lane + 1); past the end of the stream:
+                    // descriptor row 0 and the NaN sentinel record
+                    const int lim = total - c * kN;
+                    const int32_t *rows = (staged ? ps : gs) + c * kN;
+                    const int quad = lane & 15, h = lane >> 4;
+                    int4 r4;
+                    r4.x = 4 * quad < lim ? rows[4 * quad] : 0;
+                    r4.y = 4 * quad + 1 < lim ? rows[4 * quad + 1] : 0;
+                    r4.z = 4 * quad + 2 < lim ? rows[4 * quad + 2] : 0;
+                    r4.w = 4 * quad + 3 < lim ? rows[4 * quad + 3] : 0;
+                    const int e0 = 2 * lane < lim ? rows[2 * lane] : b_n;
+                    const int e1 = 2 * lane + 1 < lim ? rows[2 * lane + 1] : b_n;
                     if (lane == 0) mbar_expect_tx_only(&cl.stage_full[s], (uint32_t)kN * 256u);
                     __syncwarp();
-                    const int quad = lane & 15, h = lane >> 4;
-                    const int4 r4 = *reinterpret_cast<const int4 *>(lrows + 4 * quad);
-                    tma_gather4(bstage + h * kBHalf + quad * 512, gmap, 64 * h, r4, &cl.stage_full[s], dcur.b_n,
+                    tma_gather4(bstage + h * kBHalf + quad * 512, gmap, 64 * h, r4, &cl.stage_full[s], b_n,
                                 &ctr->errors);
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int slot = 2 * lane + e;
-                        cp_async16(rstage + slot * 16, brec + (pcur[e] >= 0 ? pcur[e] : dcur.b_n));
-                    }
+                    cp_async16(rstage + (2 * lane) * 16, brec + e0);
+                    cp_async16(rstage + (2 * lane + 1) * 16, brec + e1);
                     cp_async_arrive(&cl.stage_full[s]);
                 }
             }

@@ -173,8 +173,9 @@ __global__ void __launch_bounds__(kWarps * 32) stream_kernel(
             total = carry;
         }
     }
-    // reserve the block's space with one atomic
-    if (lane == 0) wtotal[warp] = (active && !full) ? total : 0;
+    // reserve the block's space with one atomic; every stream starts on a 16-byte boundary (reservations are
+    // rounded up to four positions) so that the matcher can stage it with 16-byte copies
+    if (lane == 0) wtotal[warp] = (active && !full) ? (total + 3) & ~3 : 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long sum = 0;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kWarps * 32) stream_kernel(
     __syncthreads();
     if (!active) return;
     const unsigned long long off = wbase[warp];
-    const bool overflow = !full && off + (unsigned long long)total > (unsigned long long)capacity;
+    const bool overflow = !full && off + (unsigned long long)((total + 3) & ~3) > (unsigned long long)capacity;
     if (lane == 0) {
         const PairDev &P = *Pp;
         const ImageDev &A = *Ap, &B = *Bp;
