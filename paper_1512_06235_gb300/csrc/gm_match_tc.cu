@@ -4,18 +4,17 @@
 // epipolar line, so a group's bands nearly coincide; every query keeps its own exact band).  One persistent CTA
 // per SM runs four roles that hand work to each other through mbarriers:
 //
-//   setup warps (2, alternate groups): the gather (cp.async, two 256-byte rows per warp instruction) of the
-//       group's 128 query descriptors (recentred, fp16: integers in [-128, 127] are exact) into the group's A tile
-//       (128-byte-swizzled K-major layout), the queries' coordinates, norms and output indices, and the group's
-//       candidate stream (positions computed beforehand by gm_stream.cu: the chord-bounded cell walk of the whole
-//       group), all into the group's slot in shared memory.  Everything the CTA needs about a group comes from its
-//       descriptor; the setup warp loads it before it waits for the slot;
-//   loader warp: cuts the staged stream into 64-row chunks and brings the fp16 descriptor rows (two K halves) and
-//       a 16-byte record per candidate (x, y, |b'|^2 * 256, position) into a 4-stage ring: scattered rows of banded
-//       groups by TMA gather4 (records by cp.async; completion through cp.async.mbarrier.arrive), the contiguous
-//       rows of whole-image groups by TMA tile loads (64-row boxes, 128-byte swizzle; rows past the image read as
-//       NaN records); slots past the end of a stream get the image's NaN sentinel record.  Positions come from
-//       shared memory, so global-memory latency stays off the loader's issue path;
+//   worker warps (3): group set-up and chunk loads, round robin (a TMA or cp.async issue stream of one warp
+//       moves only about 6 bytes per cycle, so one warp cannot keep the pipeline fed).  Set-up of a group: its
+//       coordinates, norms and output indices, the TMA gather4 of its 128 query descriptors (recentred, fp16:
+//       integers in [-128, 127] are exact) into the slot's A tile (128-byte-swizzled K-major layout), and a copy of
+//       its candidate stream (positions computed beforehand by gm_stream.cu: the chord-bounded cell walk of the
+//       whole group) into shared memory; everything comes from the group's descriptor, loaded well before the slot
+//       frees.  Chunk loads: 64 stream positions at a time, the fp16 descriptor rows (two K halves) and a 16-byte
+//       record per candidate (x, y, |b'|^2 * 256, position) into a 4-stage ring: scattered rows by TMA gather4
+//       (records by cp.async, completion through cp.async.mbarrier.arrive), the contiguous rows of whole-image
+//       groups by TMA tile loads (64-row boxes, 128-byte swizzle; rows past the image read as NaN records); slots
+//       past the end of a stream get the image's NaN sentinel record;
 //   MMA warp (one elected thread): eight tcgen05.mma.kind::f16 per chunk (M = 128, N = 64, K = 16 each), f32
 //       accumulation into one of two tensor-memory buffers.  Products are integers of magnitude <= 2^14 and partial
 //       sums <= 2^21 < 2^24, so the accumulator holds the exact integer dot product a'.b';
@@ -45,13 +44,15 @@ namespace {
 constexpr int kM = 128;             // queries per group (tensor-memory lanes)
 constexpr int kN = 64;              // candidates per chunk
 constexpr int kStages = 4;          // candidate chunks in flight
-constexpr int kSlots = 2;           // query groups in flight
-constexpr int kPosCap = 8192;       // candidate positions a slot stages in shared memory (multiple of kN)
+constexpr int kAcc = 2;             // accumulator buffers in tensor memory
+constexpr int kSlots = 3;           // query groups in flight
+constexpr int kPosCap = 3840;       // candidate positions a slot stages in shared memory (multiple of kN)
 constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
 constexpr int kEpiWarps = 8;
-constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;
+constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;   // worker warps: 8, 10, 11
+constexpr int kWorkers = 3;
 constexpr int kThreads = 12 * 32;
-constexpr int kTmemCols = 2 * kN;   // two accumulator buffers
+constexpr int kTmemCols = kAcc * kN;
 constexpr int kCounterShards = 64;
 constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
 
@@ -62,22 +63,22 @@ constexpr int kOffB = kOffA + kSlots * 2 * kAHalf;  // kStages candidate chunks
 constexpr int kOffRec = kOffB + kStages * 2 * kBHalf;
 constexpr int kRecStage = kN * 16;                // records of a chunk (16 bytes each)
 constexpr int kOffCtl = kOffRec + kStages * kRecStage;
-constexpr uint32_t kChunkTx = kN * (256 + 16);      // bytes the loader's TMA tile loads bring per chunk
 
 struct Ctl {
     GroupDesc desc[kSlots];          // the group in each slot
     float2 qxy[kSlots][kM];          // query coordinates
     int32_t rinfo[kSlots][kM][2];    // original A index (-1: no query), |a'|^2 * 256
-    int32_t aidx[kSlots][kM];        // A rows to gather
+    alignas(16) int32_t aidx[kSlots][kM];   // A rows to gather
     int32_t merge[kSlots][kM][4];
     alignas(16) int32_t pos[kSlots][kPosCap];   // the group's candidate positions (staged by the setup warp)
-    uint64_t stage_full[kStages], stage_empty[kStages], acc_full[2], acc_empty[2];
-    uint64_t grp_full[kSlots], grp_empty[kSlots], merge_ready[kSlots];
+    uint64_t stage_full[kStages], stage_empty[kStages], acc_full[kAcc], acc_empty[kAcc];
+    uint64_t grp_full[kSlots], grp_empty[kSlots], merge_ready[kSlots], pos_full[kSlots];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
     unsigned long long stat[3];
 };
 constexpr int kSmemBytes = kOffCtl + (int)sizeof(Ctl) + 1024;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -95,9 +96,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     uint64_t t0 = 0;
     for (uint32_t it = 0;; ++it) {
         uint32_t done;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        // the suspend-time hint lets the thread sleep until the phase completes (or 20 us pass) instead of
+        // spinning on issue slots that the epilogue warps need
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done)
-                     : "r"(a), "r"(parity)
+                     : "r"(a), "r"(parity), "r"(20000u)
                      : "memory");
         if (done) return true;
         if ((it & 255) == 0) {
@@ -179,35 +182,7 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *bar)
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// 128-byte swizzle of a K-major tile: row r, 16-byte chunk c of one K half (rows are 128 bytes).
-__device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
-
-// Gathers rows into a K-major, 128-byte-swizzled fp16 tile (two K halves of half_bytes each): tile row r is source
-// row rows[r] for r < lim and row 0 past it (rows may point to shared or global memory; entries past lim are not
-// read).  One warp instruction copies two whole 256-byte rows (lanes 0-15: row 2i, lanes 16-31: row 2i + 1), so
-// every request reads whole 128-byte lines; a lane's swizzled destination repeats every four instructions (plus
-// 1024 bytes) and is computed once.
-__device__ __forceinline__ void gather_rows(uint32_t tile, int half_bytes, int nrows, const uint16_t *__restrict__ src,
-                                            const int32_t *rows, int lim)
-{
-    const int lane = threadIdx.x & 31;
-    const int sub = lane >> 4, c = lane & 15;   // c: 16-byte chunk of the 256-byte row
-    const int h = c >> 3, cc = c & 7;
-    const char *s0 = reinterpret_cast<const char *>(src) + c * 16;
-    uint32_t dst[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) dst[m] = tile + h * half_bytes + sw128(2 * m + sub, cc);
-    for (int i0 = 0; i0 < nrows / 2; i0 += 4) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int r = 2 * (i0 + m) + sub;
-            const int row = r < lim ? rows[r] : 0;
-            cp_async16(dst[m] + i0 * 256, s0 + (int64_t)row * (kDim * 2));
-        }
-    }
-}
 
 // Shared-memory matrix descriptor: start >> 4, leading byte offset 16 (unused for swizzled K-major), stride byte
 // offset 1024 (8-row groups of 128-byte rows), version bits 46-48 = 0b001, 128-byte swizzle (mode 2, bits 61-63).
@@ -287,9 +262,9 @@ __device__ __forceinline__ void setup_load(SetupData &sd, const GroupDesc *__res
     }
 }
 
-// Writes the group into slot g and gathers its A tile (the slot must be free).
-__device__ __forceinline__ void setup_store(Ctl &cl, unsigned char *base, const SetupData &sd, int g,
-                                            const int32_t *__restrict__ stream)
+// Writes the group into slot g (the slot must be free): query data, descriptor and the staged candidate positions
+// (cp.async); pos_full completes with the 32 lanes' cp.async arrivals and lane 0's release.
+__device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g, const int32_t *__restrict__ stream)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -301,18 +276,15 @@ __device__ __forceinline__ void setup_store(Ctl &cl, unsigned char *base, const 
         cl.aidx[g][r] = sd.s4[t] >= 0 ? sd.s4[t] : 0;
     }
     if (lane == 0) cl.desc[g] = sd.d;
-    __syncwarp();
-    // A tile: 128 rows, two per warp instruction; every lane's copies complete into grp_full (noinc arrivals),
-    // plus one ordinary arrival that releases the slot data written above
-    gather_rows(smem_u32(base + kOffA + g * 2 * kAHalf), kAHalf, kM, sd.d.a_desc, cl.aidx[g], kM);
     if (positions_staged(sd.d)) {   // the candidate stream, 16 bytes per copy (the tail of the last copy is unused)
         const int4 *src = reinterpret_cast<const int4 *>(stream + sd.d.off);
         const uint32_t dst = smem_u32(cl.pos[g]);
         const int n16 = (sd.d.total + 3) >> 2;
         for (int k = lane; k < n16; k += 32) cp_async16(dst + 16 * k, src + k);
     }
-    cp_async_arrive(&cl.grp_full[g]);
-    if (lane == 0) mbar_arrive(&cl.grp_full[g]);
+    cp_async_arrive(&cl.pos_full[g]);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&cl.pos_full[g]);
 }
 
 // ------------------------------------------------------------------------------------------------ kernel
@@ -335,16 +307,17 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         cl.abort_flag = 0;
         cl.stat[0] = cl.stat[1] = cl.stat[2] = 0ull;
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&cl.stage_full[s], 32);   // the 32 loader lanes
-            mbar_init(&cl.stage_empty[s], 1 + kEpiWarps);
+            mbar_init(&cl.stage_full[s], 32 * kWorkers);   // every lane of the three workers (+ tile bytes)
+            mbar_init(&cl.stage_empty[s], 1 + kEpiWarps);  // the MMA commit, the epilogue warps (records read)
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kAcc; ++b) {
             mbar_init(&cl.acc_full[b], 1);
             mbar_init(&cl.acc_empty[b], kEpiWarps);
         }
         for (int g = 0; g < kSlots; ++g) {
-            mbar_init(&cl.grp_full[g], 33);   // 32 cp.async arrivals + the setup warp's release
-            mbar_init(&cl.grp_empty[g], 1 + kEpiWarps);   // MMA commit, epilogue warps
+            mbar_init(&cl.pos_full[g], 33);   // the setup warp's 32 cp.async arrivals + its release
+            mbar_init(&cl.grp_full[g], kWorkers);   // each worker's arrival with its share of the A tile's bytes
+            mbar_init(&cl.grp_empty[g], 1 + kEpiWarps + kWorkers);   // MMA commit, epilogue warps, workers
             mbar_init(&cl.merge_ready[g], kEpiWarps / 2);
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -359,26 +332,42 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     tc_fence_after();
     const uint32_t tmem = cl.tmem_base;
 
-    if (warp >= kSetupWarp0) {
-        // ---------------------------------------------------------------- setup warps: groups gk = j, j + 2, ...
-        const int j = warp - kSetupWarp0;
-        for (int gk = j; gk < n_groups && !cl.abort_flag; gk += kSlots) {
-            const int g = gk % kSlots;
-            SetupData sd;
-            setup_load(sd, gdesc, grows, first + (int64_t)gk * stride);   // in flight while the slot drains
-            if (!mbar_wait_warp(&cl.grp_empty[g], ((gk / kSlots) & 1) ^ 1)) { raise_abort(cl, ctr); break; }
-            setup_store(cl, base, sd, g, stream);
-        }
-    } else if (warp == kLoaderWarp) {
-        // ---------------------------------------------------------------- loader warp
+    if (warp == kLoaderWarp || warp >= kSetupWarp0) {
+        // ---------------------------------------------------------------- worker warps
+        // A TMA or cp.async issue stream of one warp moves only about 6 bytes per cycle, so the three workers share
+        // every copy: worker wk issues the gather4 operations o = wk (mod 3) of each tile and the records e = wk
+        // (mod 3) of each chunk.  The set-up of group gk (query data, descriptor, positions) is worker gk mod 3's.
+        // Every worker walks every group and chunk in order and arrives on grp_empty when it is done with a group,
+        // so a slot is never refilled before every worker has seen its previous contents.
+        const int wk = warp == kLoaderWarp ? 0 : 1 + warp - kSetupWarp0;
         int ck = 0;
         bool ok = true;
+        SetupData nxt;
+        if (wk < n_groups) setup_load(nxt, gdesc, grows, first + (int64_t)wk * stride);   // in flight early
         for (int gk = 0; gk < n_groups && ok && !cl.abort_flag; ++gk) {
             const int g = gk % kSlots;
-            // the group's descriptor and staged positions are in the slot once the setup warp has filled it
-            if (!mbar_wait_warp(&cl.grp_full[g], (gk / kSlots) & 1)) { ok = false; break; }
+            if (gk % kWorkers == wk) {
+                if (!mbar_wait_warp(&cl.grp_empty[g], ((gk / kSlots) & 1) ^ 1)) { ok = false; break; }
+                setup_store(cl, nxt, g, stream);
+                if (gk + kWorkers < n_groups) setup_load(nxt, gdesc, grows, first + (int64_t)(gk + kWorkers) * stride);
+            }
+            // the group's descriptor, query rows and staged positions are in the slot once pos_full completes
+            if (!mbar_wait_warp(&cl.pos_full[g], (gk / kSlots) & 1)) { ok = false; break; }
             const GroupDesc &dg = cl.desc[g];
             const int total = dg.total, nchunks = (total + kN - 1) / kN, full = dg.flags & 1, b_n = dg.b_n;
+            {   // this worker's share of the A tile: operation o = wk + 3 lane < 64 gathers rows 4 (o & 31) + 0..3 of
+                // K half o >> 5; grp_full completes with the three workers' arrivals and all the tile's bytes
+                const int nops = (2 * kM / 4 - wk + kWorkers - 1) / kWorkers;
+                if (lane == 0) mbar_expect_tx(&cl.grp_full[g], (uint32_t)nops * 512u);
+                __syncwarp();
+                const int o = wk + kWorkers * lane;
+                if (o < 2 * kM / 4) {
+                    const int q = o & 31, hh = o >> 5;
+                    const int4 r4 = *reinterpret_cast<const int4 *>(cl.aidx[g] + 4 * q);
+                    tma_gather4(smem_u32(base + kOffA + g * 2 * kAHalf + hh * kAHalf + q * 512),
+                                &maps[dg.a_slot].desc_row, 64 * hh, r4, &cl.grp_full[g], dg.a_n, &ctr->errors);
+                }
+            }
             const CUtensorMap *dmap = &maps[dg.b_slot].desc_tile;
             const CUtensorMap *rmap = &maps[dg.b_slot].rec_tile;
             const CUtensorMap *gmap = &maps[dg.b_slot].desc_row;
@@ -387,43 +376,47 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             const int32_t *gs = stream + dg.off;
             const int32_t *ps = cl.pos[g];
             for (int c = 0; c < nchunks; ++c, ++ck) {
-                const int s = ck % kStages;
-                if (!mbar_wait_warp(&cl.stage_empty[s], ((ck / kStages) & 1) ^ 1)) { ok = false; break; }
-                const uint32_t bstage = smem_u32(base + kOffB + s * 2 * kBHalf);
-                const uint32_t rstage = smem_u32(base + kOffRec + s * kRecStage);
+                const int sb = ck % kStages;
+                if (!mbar_wait_warp(&cl.stage_empty[sb], ((ck / kStages) & 1) ^ 1)) { ok = false; break; }
+                const uint32_t bstage = smem_u32(base + kOffB + sb * 2 * kBHalf);
+                const uint32_t rstage = smem_u32(base + kOffRec + sb * kRecStage);
                 if (full) {
-                    // contiguous rows: TMA tile loads (rows past the image come back as NaN records)
-                    if (lane == 0) {
-                        mbar_expect_tx(&cl.stage_full[s], kChunkTx);
-                        tma_tile(bstage, dmap, 0, c * kN, &cl.stage_full[s], 1024u, &ctr->errors);
-                        tma_tile(bstage + kBHalf, dmap, 64, c * kN, &cl.stage_full[s], 1024u, &ctr->errors);
-                        tma_tile(rstage, rmap, 0, c * kN, &cl.stage_full[s], 128u, &ctr->errors);
+                    // contiguous rows: TMA tile loads by worker 0 (rows past the image come back as NaN records)
+                    if (wk == 0 && lane == 0) {
+                        mbar_expect_tx(&cl.stage_full[sb], 2u * kBHalf + (uint32_t)kRecStage);
+                        tma_tile(bstage, dmap, 0, c * kN, &cl.stage_full[sb], 1024u, &ctr->errors);
+                        tma_tile(bstage + kBHalf, dmap, 64, c * kN, &cl.stage_full[sb], 1024u, &ctr->errors);
+                        tma_tile(rstage, rmap, 0, c * kN, &cl.stage_full[sb], 128u, &ctr->errors);
                     } else {
-                        mbar_arrive(&cl.stage_full[s]);
+                        mbar_arrive(&cl.stage_full[sb]);
                     }
                 } else {
-                    // scattered rows: TMA gather4 of the descriptor rows (lane: four rows of one K half) and
-                    // cp.async of the records (lane: slots 2 lane, 2 lane + 1); past the end of the stream:
-                    // descriptor row 0 and the NaN sentinel record
+                    // scattered rows: gather4 operation o = wk + 3 lane < 32 brings rows 4 (o & 15) + 0..3 of K half
+                    // o >> 4; record slot e = wk + 3 lane < 64 by cp.async.  Past the end of the stream: descriptor
+                    // row 0 and the NaN sentinel record
                     const int lim = total - c * kN;
                     const int32_t *rows = (staged ? ps : gs) + c * kN;
-                    const int quad = lane & 15, h = lane >> 4;
-                    int4 r4;
-                    r4.x = 4 * quad < lim ? rows[4 * quad] : 0;
-                    r4.y = 4 * quad + 1 < lim ? rows[4 * quad + 1] : 0;
-                    r4.z = 4 * quad + 2 < lim ? rows[4 * quad + 2] : 0;
-                    r4.w = 4 * quad + 3 < lim ? rows[4 * quad + 3] : 0;
-                    const int e0 = 2 * lane < lim ? rows[2 * lane] : b_n;
-                    const int e1 = 2 * lane + 1 < lim ? rows[2 * lane + 1] : b_n;
-                    if (lane == 0) mbar_expect_tx_only(&cl.stage_full[s], (uint32_t)kN * 256u);
+                    const int nops = (kN / 2 - wk + kWorkers - 1) / kWorkers;
+                    if (lane == 0) mbar_expect_tx_only(&cl.stage_full[sb], (uint32_t)nops * 512u);
                     __syncwarp();
-                    tma_gather4(bstage + h * kBHalf + quad * 512, gmap, 64 * h, r4, &cl.stage_full[s], b_n,
-                                &ctr->errors);
-                    cp_async16(rstage + (2 * lane) * 16, brec + e0);
-                    cp_async16(rstage + (2 * lane + 1) * 16, brec + e1);
-                    cp_async_arrive(&cl.stage_full[s]);
+                    const int o = wk + kWorkers * lane;
+                    if (o < kN / 2) {
+                        const int q = o & 15, hh = o >> 4;
+                        int4 r4;
+                        r4.x = 4 * q < lim ? rows[4 * q] : 0;
+                        r4.y = 4 * q + 1 < lim ? rows[4 * q + 1] : 0;
+                        r4.z = 4 * q + 2 < lim ? rows[4 * q + 2] : 0;
+                        r4.w = 4 * q + 3 < lim ? rows[4 * q + 3] : 0;
+                        tma_gather4(bstage + hh * kBHalf + q * 512, gmap, 64 * hh, r4, &cl.stage_full[sb], b_n,
+                                    &ctr->errors);
+                    }
+                    const int e = wk + kWorkers * lane;
+                    if (e < kN) cp_async16(rstage + e * 16, brec + (e < lim ? rows[e] : b_n));
+                    cp_async_arrive(&cl.stage_full[sb]);
                 }
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cl.grp_empty[g]);
         }
         if (!ok) raise_abort(cl, ctr);
     } else if (warp == kMmaWarp) {
@@ -437,11 +430,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 const uint32_t abase = smem_u32(base + kOffA + g * 2 * kAHalf);
                 bool ok = true;
                 for (int c = 0; c < nchunks; ++c, ++ck) {
-                    const int s = ck % kStages, b = ck & 1;
+                    const int s = ck % kStages, b = ck % kAcc;
                     if (!mbar_wait(&cl.stage_full[s], (ck / kStages) & 1) ||
-                        !mbar_wait(&cl.acc_empty[b], ((ck >> 1) & 1) ^ 1)) { ok = false; break; }
+                        !mbar_wait(&cl.acc_empty[b], ((ck / kAcc) & 1) ^ 1)) { ok = false; break; }
                     tc_fence_after();
-                    fence_proxy_async();   // cp.async writes (generic proxy) -> tensor-core reads (async proxy)
                     const uint32_t bbase = smem_u32(base + kOffB + s * 2 * kBHalf);
 #pragma unroll
                     for (int ks = 0; ks < 8; ++ks) {
@@ -486,15 +478,15 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             int k1 = INT_MAX, k2 = INT_MAX, j1 = 0, cnt = 0;
             bool ok = true;
             for (int c = 0; c < nchunks; ++c, ++ck) {
-                const int s = ck % kStages, b = ck & 1;
-                if (!mbar_wait_warp(&cl.acc_full[b], (ck >> 1) & 1)) { ok = false; break; }
+                const int s = ck % kStages, b = ck % kAcc;
+                if (!mbar_wait_warp(&cl.acc_full[b], (ck / kAcc) & 1)) { ok = false; break; }
                 tc_fence_after();
                 uint32_t v[32];
                 tmem_ld32(tmem_lane + b * kN, v);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&cl.acc_empty[b]);
-                if (!mbar_wait_warp(&cl.stage_full[s], (ck / kStages) & 1)) { ok = false; break; }   // records visible
+                if (!mbar_wait_warp(&cl.stage_full[s], (ck / kStages) & 1)) { ok = false; break; }   // records
                 const int4 *rs = rec + (s * kRecStage) / 16 + 32 * h;
                 const int k1_before = k1;
                 if (32 * h < total - c * kN) {
@@ -515,6 +507,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                         if (jj & 1) { kb2 = min(kb2, max(kb1, km)); kb1 = min(kb1, km); }
                         else { ka2 = min(ka2, max(ka1, km)); ka1 = min(ka1, km); }
                         cnt += inb;
+                        // keep the records' shared-memory loads in blocks of eight: hoisting all 32 (128 registers)
+                        // ahead of the arithmetic spills registers
+                        if ((jj & 7) == 7) asm volatile("" ::: "memory");
                     }
                     k2 = min(min(ka2, kb2), max(ka1, kb1));
                     k1 = min(ka1, kb1);
