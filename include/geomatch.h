@@ -153,6 +153,19 @@ GM_API gm_status gm_match_pairs(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pai
 GM_API gm_status gm_band_candidates(gm_ctx *ctx, const gm_pair *pair, int32_t query_begin, int32_t query_count,
                              int64_t *cand_off, int32_t *cand, int64_t cap, int64_t *n_written);
 
+/* gm_band_candidates without any allocation (the paper has no counterpart: this is an interface for callers that
+ * must not allocate, e.g. with device memory fully committed or in latency-critical loops where cudaMalloc,
+ * cudaFree or cudaHostAlloc would stall).  Same sets, same layout, same errors as gm_band_candidates, except:
+ *   cand_off, cand: DEVICE memory of the context's device (GM_ERR_INVALID otherwise), caller-owned;
+ *   scratch: one fixed 4 MiB device array per device, so query_count * ceil(|B| / 32) * 4 + 4 * query_count + 768
+ *            bytes must fit in 4 MiB (GM_ERR_INVALID with the sizes otherwise; split the query range);
+ *   the first call on a device sets up the scratch address and should come before any stream capture;
+ *   calls that overlap in time on one device (any thread or context) race on the scratch: serialise them.
+ * The call returns when the outputs are complete. */
+GM_API gm_status gm_band_candidates_static(gm_ctx *ctx, const gm_pair *pair, int32_t query_begin,
+                                           int32_t query_count, int64_t *cand_off, int32_t *cand, int64_t cap,
+                                           int64_t *n_written);
+
 /* Counters and device timings of the last gm_match_pairs call on this context. */
 GM_API gm_status gm_get_stats(const gm_ctx *ctx, gm_stats *out);
 

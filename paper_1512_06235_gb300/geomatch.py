@@ -76,6 +76,8 @@ _SIGNATURES = {
     "gm_match_pairs": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_p, c_p, c_i64, ctypes.POINTER(c_i64)]),
     "gm_band_candidates": (c_i32, [c_p, ctypes.POINTER(GmPair), c_i32, c_i32, c_p, c_p, c_i64,
                                    ctypes.POINTER(c_i64)]),
+    "gm_band_candidates_static": (c_i32, [c_p, ctypes.POINTER(GmPair), c_i32, c_i32, c_p, c_p, c_i64,
+                                          ctypes.POINTER(c_i64)]),
     "gm_get_stats": (c_i32, [c_p, ctypes.POINTER(GmStats)]),
     "gm_submit": (c_i32, [c_p, ctypes.POINTER(GmPair), ctypes.POINTER(c_u64)]),
     "gm_poll": (c_i32, [c_p, c_u64, c_p, c_i64, ctypes.POINTER(c_i64), c_i32, ctypes.POINTER(ctypes.c_double)]),
@@ -200,6 +202,22 @@ def gm_band_candidates(ctx, pair, query_begin: int, query_count: int, cand_off, 
     pc, _, k2 = _ptr(cand)
     n = c_i64(0)
     st = load_library().gm_band_candidates(ctx, arr, query_begin, query_count, po, pc, cap, ctypes.byref(n))
+    if st == GM_ERR_NOMEM:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = n.value
+        raise err
+    _check(st, ctx)
+    del k1, k2
+    return n.value
+
+
+def gm_band_candidates_static(ctx, pair, query_begin: int, query_count: int, cand_off, cand, cap: int) -> int:
+    """gm_band_candidates with caller-owned device outputs and no allocation inside the call."""
+    arr = _pairs_array([pair])
+    po, _, k1 = _ptr(cand_off)
+    pc, _, k2 = _ptr(cand)
+    n = c_i64(0)
+    st = load_library().gm_band_candidates_static(ctx, arr, query_begin, query_count, po, pc, cap, ctypes.byref(n))
     if st == GM_ERR_NOMEM:
         err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
         err.required = n.value
