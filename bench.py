@@ -346,7 +346,7 @@ def main():
     kname, ksrc, kdtype = MATCH_KERNELS[st["path_used"]]
     alg_bytes = _algorithmic_bytes(sc, pairs, st["n_matches"])
     achieved = alg_bytes / (ms_match / 1e3) / 1e9
-    traffic = _profiled_traffic(kname, ksrc, WORKLOAD) if not args.pairs and args.cell in (0, 8) else None
+    traffic = _profiled_traffic(kname, ksrc, WORKLOAD) if not args.pairs and args.cell in (0, 4) else None
     tensor_ops = 256.0 * st["n_candidates"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
@@ -367,7 +367,7 @@ def main():
             "vs_baseline": None, "dtype": kdtype, "data": "synthetic (seeded facade scene; stands in for the paper's "
                                                          "Rome16K-style components)",
             "config": {"workload": WORKLOAD if not args.pairs else f"{WORKLOAD}_first{args.pairs}", "pairs": len(pairs), "images": len(sc.images), "keypoints_per_image": 8000,
-                       "band_px": 4.0, "ratio": 0.8, "cell_px": args.cell or 8, "group": args.group, "l2": "flushed between steps (512 MB write)",
+                       "band_px": 4.0, "ratio": 0.8, "cell_px": args.cell or "auto (4)", "group": args.group, "l2": "flushed between steps (512 MB write)",
                        "path": st["path_used"], "schedule": "persistent batch" if not args.schedule else "one pair per launch"},
             "comparisons_per_s": comps_per_s, "candidates_per_step": st["n_candidates"],
             "examined_per_step": st["n_examined"], "redecided_per_step": st["n_redecided"], "matches_per_step": st["n_matches"],

@@ -67,7 +67,8 @@ enum {
 enum {
     GM_OPT_PATH = 1,        /* GM_PATH_* */
     GM_OPT_SCHEDULE = 2,    /* 0 = whole batch per launch (default), 1 = one pair per launch (plain form) */
-    GM_OPT_CELL_PX = 3,     /* grid cell size of images put afterwards: 4, 8, 16, 32, 64 or 128 px (default 8) */
+    GM_OPT_CELL_PX = 3,     /* grid cell size of images put afterwards: 4, 8, 16, 32, 64 or 128 px, or 0 =
+                               automatic (the default: 4 px, coarser only for images wider than 4096 px) */
     GM_OPT_GRAPH = 4,       /* 1 = replay batches through a captured CUDA graph when the shape repeats */
     GM_OPT_MMA_GROUP = 5,   /* queries per group of the mma path: 16 (default) or 32 */
     GM_OPT_STREAM_CAP = 6   /* entries of the tcgen05 path's candidate-stream buffer (grown automatically) */
@@ -79,7 +80,7 @@ typedef struct {
     int32_t max_inflight;        /* serving: batches that may be on the device at once (>= 1; 0 = 2) */
     void *cuda_stream;           /* cudaStream_t for synchronous calls, or NULL for the context's own stream */
     int32_t path;                /* GM_PATH_* */
-    int32_t cell_px;             /* grid cell size in px (power of two, 4..128); 0 = 8 */
+    int32_t cell_px;             /* grid cell size in px (power of two, 4..128); 0 = automatic */
     const char *tuner_cache;     /* reserved (may be NULL) */
 } gm_config;
 

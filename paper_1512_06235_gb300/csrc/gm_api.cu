@@ -393,7 +393,7 @@ gm_status gm_create(const gm_config *cfg, gm_ctx **out)
     if (!cfg || !out) return fail(GM_ERR_INVALID, "gm_create: null argument");
     *out = nullptr;
     if (cfg->path < GM_PATH_AUTO || cfg->path > GM_PATH_SIMT) return fail(GM_ERR_INVALID, "gm_create: bad path");
-    int cell_shift = 3;   // 8 px cells unless configured
+    int cell_shift = 0;   // automatic unless configured
     if (cfg->cell_px) {
         int c = cfg->cell_px, sh = 0;
         while ((1 << sh) < c) ++sh;
@@ -468,6 +468,10 @@ gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value)
         ctx->schedule = (int32_t)value;
         return GM_OK;
     case GM_OPT_CELL_PX: {
+        if (value == 0) {   // automatic
+            ctx->cell_shift = 0;
+            return GM_OK;
+        }
         int sh = 0;
         while ((1ll << sh) < value) ++sh;
         if ((1ll << sh) != value || sh < kMinCellShift || sh > kMaxCellShift)
@@ -502,7 +506,13 @@ gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t hei
         return fail(GM_ERR_INVALID, "gm_image_put: bad arguments (id %d, %dx%d, n %d)", image_id, width, height, n);
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     GM_CUDA(cudaSetDevice(ctx->device));
-    const int sh = ctx->cell_shift;
+    // grid cell: the configured size, or automatically 4 px unless the image is so large that the grid would cross
+    // more lines than the tcgen05 kernel's run table holds
+    int sh = ctx->cell_shift;
+    if (sh == 0) {
+        sh = kMinCellShift;
+        while (sh < kMaxCellShift && ((std::max(width, height) + (1 << sh) - 1) >> sh) > match_tc_max_grid_lines()) ++sh;
+    }
     const int cs = 1 << sh;
     const int gx = (width + cs - 1) / cs, gy = (height + cs - 1) / cs;
     const int64_t m = (int64_t)gx * gy;

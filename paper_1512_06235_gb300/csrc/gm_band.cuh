@@ -80,6 +80,31 @@ __device__ __forceinline__ bool band_exact(const float F[9], float x, float y, f
     return fabs(s) <= thr;
 }
 
+// The same decision split in two: the FP64 line and threshold of a query (once), then the test of a point.  Every
+// operation is the one band_exact performs, in the same order, so the outcome is identical; a == b == 0 gives the
+// threshold -1 (no point is inside, as band_exact returns false).
+struct BandLine64 {
+    double a, b, c, thr;
+};
+
+__device__ __forceinline__ BandLine64 band_line64(const float F[9], float x, float y, float d)
+{
+    const double X = (double)x, Y = (double)y;
+    BandLine64 L;
+    L.a = __dadd_rn(__dadd_rn(__dmul_rn((double)F[0], X), __dmul_rn((double)F[1], Y)), (double)F[2]);
+    L.b = __dadd_rn(__dadd_rn(__dmul_rn((double)F[3], X), __dmul_rn((double)F[4], Y)), (double)F[5]);
+    L.c = __dadd_rn(__dadd_rn(__dmul_rn((double)F[6], X), __dmul_rn((double)F[7], Y)), (double)F[8]);
+    const double n = __dsqrt_rn(__dadd_rn(__dmul_rn(L.a, L.a), __dmul_rn(L.b, L.b)));
+    L.thr = n == 0.0 ? -1.0 : __dmul_rn((double)d, n);
+    return L;
+}
+
+static __device__ __noinline__ bool band_test64_call(double a, double b, double c, double thr, float xp, float yp)
+{
+    const double s = __dadd_rn(__dadd_rn(__dmul_rn(a, (double)xp), __dmul_rn(b, (double)yp)), c);
+    return fabs(s) <= thr;
+}
+
 // Out-of-line copy of band_exact for unrolled epilogues: the rare FP64 re-decision stays one call instead of
 // being inlined at every element (which would flood the instruction cache).
 static __device__ __noinline__ bool band_exact_call(const float *F, float x, float y, float d, float xp, float yp)

@@ -79,7 +79,7 @@ struct gm_ctx {
     uint64_t budget = 0;
     int32_t path = GM_PATH_AUTO;
     int32_t schedule = 0;
-    int32_t cell_shift = 3;
+    int32_t cell_shift = 0;          // 0: automatic per image
     int32_t graph = 0;
     int32_t max_inflight = 2;
     int32_t num_sms = 0;

@@ -464,8 +464,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             const int out_i = cl.rinfo[g][row][0];
             const float qx = cl.qxy[g][row].x, qy = cl.qxy[g][row].y;
             float la = 0.0f, lb = 0.0f, lc = 0.0f, llo = -1.0f, lhi = -1.0f;   // no query: never inside
+            BandLine64 l64{0.0, 0.0, 0.0, -1.0};
             if (out_i >= 0) {
                 const BandLine bl = band_line(gd.F, qx, qy, d, gd.W, gd.H);
+                if (bl.mode == kBandNormal || bl.mode == kBandSlow) l64 = band_line64(gd.F, qx, qy, d);
                 la = bl.a; lb = bl.b; lc = bl.c; llo = bl.thr_lo; lhi = bl.thr_hi;
                 // whole-image rows accept every real keypoint; FP64-only rows send every real keypoint to the FP64
                 // decision; both use the zero line (s = 0 for real keypoints, NaN for the sentinel record)
@@ -490,42 +492,49 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 const int4 *rs = rec + (s * kRecStage) / 16 + 32 * h;
                 const int k1_before = k1;
                 if (32 * h < total - c * kN) {
-                    // two interleaved top-2 accumulators (even / odd columns) shorten the dependency chain; elements
-                    // within the FP32 error margin are counted as outside here and re-decided below
+                    // two interleaved top-2 accumulators (even / odd columns) shorten the dependency chain; bit jj
+                    // of mlo marks an element inside by the FP32 test, of mhi one not outside (mhi & ~mlo: within
+                    // the error margin, re-decided in FP64 below)
                     int ka1 = k1, ka2 = k2, kb1 = INT_MAX, kb2 = INT_MAX;
-                    uint32_t und = 0u;
+                    uint32_t mlo = 0u, mhi = 0u;
 #pragma unroll
                     for (int jj = 0; jj < 32; ++jj) {
                         const int4 r = rs[jj];
                         const float sv = fmaf(la, __int_as_float(r.x), fmaf(lb, __int_as_float(r.y), lc));
                         const float as = fabsf(sv);
                         const bool inb = as <= llo;
-                        und |= (as <= lhi && !inb) ? (1u << jj) : 0u;
+                        if (inb) mlo |= 1u << jj;
+                        if (as <= lhi) mhi |= 1u << jj;
                         const uint32_t bits = (uint32_t)__float_as_int(__int_as_float(v[jj]) + 12582912.0f);
                         const int key = (int)(Rc + (uint32_t)r.z + (uint32_t)jj - 512u * bits);
-                        const int km = inb ? key : INT_MAX;
-                        if (jj & 1) { kb2 = min(kb2, max(kb1, km)); kb1 = min(kb1, km); }
-                        else { ka2 = min(ka2, max(ka1, km)); ka1 = min(ka1, km); }
-                        cnt += inb;
+                        if (inb) {
+                            if (jj & 1) { kb2 = min(kb2, max(kb1, key)); kb1 = min(kb1, key); }
+                            else { ka2 = min(ka2, max(ka1, key)); ka1 = min(ka1, key); }
+                        }
                         // keep the records' shared-memory loads in blocks of eight: hoisting all 32 (128 registers)
                         // ahead of the arithmetic spills registers
                         if ((jj & 7) == 7) asm volatile("" ::: "memory");
                     }
                     k2 = min(min(ka2, kb2), max(ka1, kb1));
                     k1 = min(ka1, kb1);
-                    if (und) {   // rare: FP64 re-decision, operation by operation as the reference definition
+                    cnt += __popc(mlo);
+                    uint32_t und = mhi & ~mlo;
+                    while (und) {   // rare: FP64 re-decision with the row's FP64 line (operation order as the reference)
+                        const int jj = __ffs(und) - 1;
+                        und &= und - 1u;
+                        const int4 r = rs[jj];
+                        ++my_redec;
+                        if (!band_test64_call(l64.a, l64.b, l64.c, l64.thr, __int_as_float(r.x), __int_as_float(r.y)))
+                            continue;
+                        // the dot product of element jj: v cannot be indexed at run time, so select it
+                        uint32_t vj = 0u;
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            if (!((und >> jj) & 1u)) continue;
-                            const int4 r = rs[jj];
-                            ++my_redec;
-                            if (!band_exact_call(gd.F, qx, qy, d, __int_as_float(r.x), __int_as_float(r.y))) continue;
-                            const uint32_t bits = (uint32_t)__float_as_int(__int_as_float(v[jj]) + 12582912.0f);
-                            const int key = (int)(Rc + (uint32_t)r.z + (uint32_t)jj - 512u * bits);
-                            k2 = min(k2, max(k1, key));
-                            k1 = min(k1, key);
-                            ++cnt;
-                        }
+                        for (int t = 0; t < 32; ++t) vj = t == jj ? v[t] : vj;
+                        const uint32_t bits = (uint32_t)__float_as_int(__int_as_float(vj) + 12582912.0f);
+                        const int key = (int)(Rc + (uint32_t)r.z + (uint32_t)jj - 512u * bits);
+                        k2 = min(k2, max(k1, key));
+                        k1 = min(k1, key);
+                        ++cnt;
                     }
                 }
                 if (k1 < k1_before) j1 = rs[(k1 & 255) - 32 * h].w;
