@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         cl.abort_flag = 0;
         cl.stat[0] = cl.stat[1] = cl.stat[2] = 0ull;
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&cl.stage_full[s], 32 * kWorkers);   // every lane of the three workers (+ tile bytes)
+            mbar_init(&cl.stage_full[s], 32 * kWorkers);   // every lane of every worker (+ tile bytes)
             mbar_init(&cl.stage_empty[s], 1 + kEpiWarps);  // the MMA commit, the epilogue warps (records read)
         }
         for (int b = 0; b < kAcc; ++b) {
@@ -464,10 +464,12 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             const int out_i = cl.rinfo[g][row][0];
             const float qx = cl.qxy[g][row].x, qy = cl.qxy[g][row].y;
             float la = 0.0f, lb = 0.0f, lc = 0.0f, llo = -1.0f, lhi = -1.0f;   // no query: never inside
+            // the row's FP64 line, computed on its first re-decision in the group (FP64 is slow on this GPU and
+            // only a few rows need it)
             BandLine64 l64{0.0, 0.0, 0.0, -1.0};
+            bool have64 = false;
             if (out_i >= 0) {
                 const BandLine bl = band_line(gd.F, qx, qy, d, gd.W, gd.H);
-                if (bl.mode == kBandNormal || bl.mode == kBandSlow) l64 = band_line64(gd.F, qx, qy, d);
                 la = bl.a; lb = bl.b; lc = bl.c; llo = bl.thr_lo; lhi = bl.thr_hi;
                 // whole-image rows accept every real keypoint; FP64-only rows send every real keypoint to the FP64
                 // decision; both use the zero line (s = 0 for real keypoints, NaN for the sentinel record)
@@ -524,6 +526,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                         und &= und - 1u;
                         const int4 r = rs[jj];
                         ++my_redec;
+                        if (!have64) {
+                            l64 = band_line64(gd.F, qx, qy, d);
+                            have64 = true;
+                        }
                         if (!band_test64_call(l64.a, l64.b, l64.c, l64.thr, __int_as_float(r.x), __int_as_float(r.y)))
                             continue;
                         // the dot product of element jj: v cannot be indexed at run time, so select it
