@@ -230,6 +230,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--pairs", type=int, default=0, help="use only the first N pairs (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch every step directly (no CUDA graph replay)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving leg: Poisson arrivals, req/s")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving leg duration (0: skip)")
     args = ap.parse_args()
@@ -263,6 +264,8 @@ def main():
         ctx.set_option(gm.GM_OPT_SCHEDULE, args.schedule)
     if args.group != 16:
         ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
+    if not args.no_graph:
+        ctx.set_option(gm.GM_OPT_GRAPH, 1)
     # ---- device-resident measurement: images registered before the timed region
     for k, im in enumerate(sc.images):
         ctx.put_image(k, im)
@@ -319,6 +322,8 @@ def main():
     e2e_ctx = gm.Context(device=local, stream=stream, path=args.path, cell_px=args.cell)
     if args.group != 16:
         e2e_ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
+    if not args.no_graph:
+        e2e_ctx.set_option(gm.GM_OPT_GRAPH, 1)
 
     def e2e_step():
         for k, (w, h, xy, scl, ds) in enumerate(pinned):
@@ -368,7 +373,8 @@ def main():
                                                          "Rome16K-style components)",
             "config": {"workload": WORKLOAD if not args.pairs else f"{WORKLOAD}_first{args.pairs}", "pairs": len(pairs), "images": len(sc.images), "keypoints_per_image": 8000,
                        "band_px": 4.0, "ratio": 0.8, "cell_px": args.cell or "auto (4)", "group": args.group, "l2": "flushed between steps (512 MB write)",
-                       "path": st["path_used"], "schedule": "persistent batch" if not args.schedule else "one pair per launch"},
+                       "path": st["path_used"], "schedule": "persistent batch" if not args.schedule else "one pair per launch",
+                       "graph": not args.no_graph and not args.schedule},
             "comparisons_per_s": comps_per_s, "candidates_per_step": st["n_candidates"],
             "examined_per_step": st["n_examined"], "redecided_per_step": st["n_redecided"], "matches_per_step": st["n_matches"],
             "ms_match_kernel": ms_match,

@@ -314,47 +314,91 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
         return launch_match_mma(mt, imgs, d_proc, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
     };
 
-    ws.launches = 0;
-    GM_CUDA(cudaEventRecord(ws.ev[0], s));
-    GM_CUDA(cudaMemcpyAsync(ds, hs, tab_bytes, cudaMemcpyHostToDevice, s));
-    GM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(BatchCounters) * 64 + 16, s));
-    if (ctx->schedule == 1) {
-        // plain form: every pair gets its own launches (one block per work item)
-        GM_CUDA(cudaEventRecord(ws.ev[1], s));
-        for (int32_t k = 0; k < P; ++k) {
-            GM_CUDA(launch_order(imgs, d_proc + k, 1, qorder, s));
+    // everything below is stream work only; with GM_OPT_GRAPH it is captured once per batch shape (sizes, launch
+    // geometry and every buffer address) and replayed when the shape repeats: the pinned tables it copies from are
+    // rewritten above before every replay
+    auto enqueue = [&](bool capturing) -> gm_status {
+        auto record = [&](cudaEvent_t e) {
+            return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+        };
+        ws.launches = 0;
+        GM_CUDA(record(ws.ev[0]));
+        GM_CUDA(cudaMemcpyAsync(ds, hs, tab_bytes, cudaMemcpyHostToDevice, s));
+        GM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(BatchCounters) * 64 + 16, s));
+        if (ctx->schedule == 1) {
+            // plain form: every pair gets its own launches (one block per work item)
+            GM_CUDA(record(ws.ev[1]));
+            for (int32_t k = 0; k < P; ++k) {
+                GM_CUDA(launch_order(imgs, d_proc + k, 1, qorder, s));
+                if (path == GM_PATH_TC) {
+                    GM_CUDA(launch_stream(imgs, d_proc, d_item_off, P, qorder, h_item_off[k], h_item_off[k + 1],
+                                          static_cast<GroupDesc *>(ws.d_grec.p), static_cast<int32_t *>(ws.d_grows.p),
+                                          static_cast<int32_t *>(ws.d_stream.p), ws.stream_cap, stream_used, ctr, s));
+                    ++ws.launches;
+                }
+                GM_CUDA(launch_match(h_item_off[k], h_item_off[k + 1], 0));
+                ws.launches += 1 + (h_item_off[k + 1] > h_item_off[k]);
+            }
+            GM_CUDA(record(ws.ev[2]));
+        } else {
+            GM_CUDA(launch_order(imgs, d_proc, P, qorder, s));
             if (path == GM_PATH_TC) {
-                GM_CUDA(launch_stream(imgs, d_proc, d_item_off, P, qorder, h_item_off[k], h_item_off[k + 1],
+                GM_CUDA(launch_stream(imgs, d_proc, d_item_off, P, qorder, 0, n_items,
                                       static_cast<GroupDesc *>(ws.d_grec.p), static_cast<int32_t *>(ws.d_grows.p),
                                       static_cast<int32_t *>(ws.d_stream.p), ws.stream_cap, stream_used, ctr, s));
                 ++ws.launches;
             }
-            GM_CUDA(launch_match(h_item_off[k], h_item_off[k + 1], 0));
-            ws.launches += 1 + (h_item_off[k + 1] > h_item_off[k]);
+            GM_CUDA(record(ws.ev[1]));
+            GM_CUDA(launch_match(0, h_item_off[P], grid));
+            GM_CUDA(record(ws.ev[2]));
+            ws.launches += 2;
         }
-        GM_CUDA(cudaEventRecord(ws.ev[2], s));
-    } else {
-        GM_CUDA(launch_order(imgs, d_pairs, P, qorder, s));
-        if (path == GM_PATH_TC) {
-            GM_CUDA(launch_stream(imgs, d_proc, d_item_off, P, qorder, 0, n_items, static_cast<GroupDesc *>(ws.d_grec.p),
-                                  static_cast<int32_t *>(ws.d_grows.p), static_cast<int32_t *>(ws.d_stream.p),
-                                  ws.stream_cap, stream_used, ctr, s));
-            ++ws.launches;
-        }
-        GM_CUDA(cudaEventRecord(ws.ev[1], s));
-        GM_CUDA(launch_match(0, h_item_off[P], grid));
-        GM_CUDA(cudaEventRecord(ws.ev[2], s));
-        ws.launches += 2;
-    }
-    GM_CUDA(launch_count_matches(d_pairs, P, match_j, static_cast<int32_t *>(ws.d_counts.p), d_off, s));
-    GM_CUDA(launch_write_matches(d_pairs, P, match_j, d_off, rows, s));
-    ws.launches += 3;
-    GM_CUDA(cudaEventRecord(ws.ev[3], s));
-    int64_t *h_off = static_cast<int64_t *>(ws.h_off.p);
-    BatchCounters *h_ctr = reinterpret_cast<BatchCounters *>(h_off + P + 1);
-    GM_CUDA(cudaMemcpyAsync(h_off, d_off, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToHost, s));
-    GM_CUDA(cudaMemcpyAsync(h_ctr, ctr, sizeof(BatchCounters) * 64 + 16, cudaMemcpyDeviceToHost, s));
+        GM_CUDA(launch_count_matches(d_pairs, P, match_j, static_cast<int32_t *>(ws.d_counts.p), d_off, s));
+        GM_CUDA(launch_write_matches(d_pairs, P, match_j, d_off, rows, s));
+        ws.launches += 3;
+        GM_CUDA(record(ws.ev[3]));
+        int64_t *h_off = static_cast<int64_t *>(ws.h_off.p);
+        BatchCounters *h_ctr = reinterpret_cast<BatchCounters *>(h_off + P + 1);
+        GM_CUDA(cudaMemcpyAsync(h_off, d_off, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToHost, s));
+        GM_CUDA(cudaMemcpyAsync(h_ctr, ctr, sizeof(BatchCounters) * 64 + 16, cudaMemcpyDeviceToHost, s));
+        return GM_OK;
+    };
     ws.path_used = path;
+    if (!ctx->graph || ctx->schedule == 1) return enqueue(false);
+    const GraphKey key{P, Q, n_items, path, mt, grid, ws.stream_cap, tab_bytes, ws.d_tab.p, ws.d_qorder.p,
+                       ws.d_matchj.p, ws.d_counts.p, ws.d_off.p, rows, ws.d_ctr.p, ws.d_grec.p, ws.d_grows.p,
+                       ws.d_stream.p, ctx->d_imgs.p, ctx->d_maps.p, ws.h_tab.p, ws.h_off.p, s};
+    if (ws.gexec && std::memcmp(&key, &ws.gkey, sizeof(key)) == 0) {
+        GM_CUDA(cudaGraphLaunch(ws.gexec, s));
+        ws.launches = ws.glaunches;
+        return GM_OK;
+    }
+    if (std::memcmp(&key, &ws.gseen, sizeof(key)) != 0) {   // a new shape runs directly once; captured when seen again
+        ws.gseen = key;
+        return enqueue(false);
+    }
+    if (ws.gexec) {
+        cudaGraphExecDestroy(ws.gexec);
+        ws.gexec = nullptr;
+    }
+    GM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const gm_status est = enqueue(true);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (est != GM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return est;
+    }
+    if (ce != cudaSuccess) return fail(GM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&ws.gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        ws.gexec = nullptr;
+        return fail(GM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+    }
+    ws.gkey = key;
+    ws.glaunches = ws.launches;
+    GM_CUDA(cudaGraphLaunch(ws.gexec, s));
     return GM_OK;
 }
 

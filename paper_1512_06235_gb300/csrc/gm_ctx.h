@@ -37,6 +37,17 @@ struct ImageSlot {
 
 // Everything one batch needs on the device and in pinned host memory.  The synchronous API owns one; every
 // serving slot owns its own, so batches on different slots can be in flight at the same time.
+// Everything a captured batch depends on besides the contents of its pinned tables and device buffers.
+struct GraphKey {
+    int64_t P, Q, n_items;
+    int32_t path, mt;
+    int64_t grid, stream_cap;
+    size_t tab_bytes;
+    const void *d_tab, *d_qorder, *d_matchj, *d_counts, *d_off, *rows, *d_ctr, *d_grec, *d_grows, *d_stream, *d_imgs,
+        *d_maps, *h_tab, *h_off;
+    cudaStream_t stream;
+};
+
 struct Workspace {
     DevBuf d_tab;        // pair table (caller's order), pair table (processing order), work-item offsets
     DevBuf d_qorder;     // int32 [Q] query order per pair
@@ -63,9 +74,10 @@ struct Workspace {
     int32_t n_pairs = 0;
     int32_t launches = 0;
     int32_t path_used = 0;
-    // CUDA graph of the last plan shape
+    // CUDA graph of the last batch shape (GM_OPT_GRAPH): captured the second time a shape is seen
     cudaGraphExec_t gexec = nullptr;
-    uint64_t gkey = 0;
+    GraphKey gkey{}, gseen{};
+    int32_t glaunches = 0;
 };
 
 struct Server;

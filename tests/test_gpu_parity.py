@@ -212,6 +212,30 @@ def test_facade_full_batch_sampled(gm, facade_scene):
             np.testing.assert_array_equal(rows2[k], rows[k], err_msg=f"{name} pair {k}")
 
 
+def test_graph_replay_equal(gm, facade_scene):
+    """GM_OPT_GRAPH: a batch shape seen twice is captured, then replayed; every call gives the direct run's lists,
+    also when the pinned pair table changes between replays (same shape, different pairs)."""
+    sc = facade_scene
+    pairs_a, pairs_b = sc.pairs[:60], sc.pairs[60:120]
+    ref_a, st_a = _gpu_rows(gm, sc, pairs=pairs_a)
+    ref_b, _ = _gpu_rows(gm, sc, pairs=pairs_b)
+    with gm.Context(device=0) as ctx:
+        ctx.set_option(gm.GM_OPT_GRAPH, 1)
+        for k in sorted({p.a for p in sc.pairs[:120]} | {p.b for p in sc.pairs[:120]}):
+            ctx.put_image(k, sc.images[k])
+        for it in range(4):
+            off, m = ctx.match_pairs(pairs_a)
+            got = gm.split_matches(off, m)
+            for k in range(len(pairs_a)):
+                np.testing.assert_array_equal(got[k], ref_a[k], err_msg=f"call {it} pair {k}")
+            assert ctx.stats()["n_candidates"] == st_a["n_candidates"]
+        same_shape = sum(sc.images[p.a].n for p in pairs_b) == sum(sc.images[p.a].n for p in pairs_a)
+        off, m = ctx.match_pairs(pairs_b)
+        got = gm.split_matches(off, m)
+        for k in range(len(pairs_b)):
+            np.testing.assert_array_equal(got[k], ref_b[k], err_msg=f"second batch pair {k} (same shape {same_shape})")
+
+
 def test_stream_buffer_overflow_reruns(gm, facade_scene):
     """A candidate-stream buffer far too small for the batch forces the grow-and-rerun path; results unchanged."""
     sc = facade_scene
