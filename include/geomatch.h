@@ -81,7 +81,7 @@ typedef struct {
     void *cuda_stream;           /* cudaStream_t for synchronous calls, or NULL for the context's own stream */
     int32_t path;                /* GM_PATH_* */
     int32_t cell_px;             /* grid cell size in px (power of two, 4..128); 0 = automatic */
-    const char *tuner_cache;     /* reserved (may be NULL) */
+    const char *tuner_cache;     /* gm_autotune's settings file (text, appended), or NULL */
 } gm_config;
 
 typedef struct {
@@ -108,6 +108,15 @@ typedef struct {
     int64_t n_device_errors;     /* device-side bounded waits that ran out (the call then fails with TIMEOUT) */
 } gm_stats;
 
+/* Result of gm_autotune. */
+typedef struct {
+    int32_t path;                /* GM_PATH_* chosen */
+    int32_t mma_group;           /* queries per group of the mma path: 16 or 32 */
+    int32_t cell_px;             /* grid cell size chosen: 4, 8 or 16 px */
+    float ms;                    /* device time of the batch with these settings (best of the timed runs) */
+    int32_t from_cache;          /* 1 if the settings came from the tuner_cache file without timing */
+} gm_tune_result;
+
 /* Creates a context on cfg->device.  *out receives the handle.  Errors: GM_ERR_INVALID (null pointer, bad
  * option value), GM_ERR_CUDA (device unavailable). */
 GM_API gm_status gm_create(const gm_config *cfg, gm_ctx **out);
@@ -133,6 +142,17 @@ GM_API gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int3
 
 /* Drops image `image_id` from the context.  GM_ERR_NOT_FOUND if unknown. */
 GM_API gm_status gm_image_evict(gm_ctx *ctx, int32_t image_id);
+
+/* Autotuner (a tuning aid; the paper has no counterpart).  Times gm_match_pairs on this batch for every distance
+ * path (tc; mma with 16- and 32-query groups; simt) and grid cell size (4, 8, 16 px), `repeats` timed runs each
+ * after one warm-up, and leaves the fastest setting in the context: GM_OPT_PATH, GM_OPT_MMA_GROUP and
+ * GM_OPT_CELL_PX, with the batch's images re-binned from their resident copies to the chosen cell size.  Every
+ * setting gives identical match lists.  With cfg->tuner_cache set, the choice is appended to that text file under
+ * the batch's signature (pair count, query and target totals, band sum, image size) and a later call with the same
+ * signature applies it without timing (*out->from_cache = 1).  Errors: GM_ERR_INVALID (null pointer, n_pairs < 1,
+ * repeats outside [1, 100]), GM_ERR_NOT_FOUND (an image not put), and those of gm_match_pairs / gm_image_put. */
+GM_API gm_status gm_autotune(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int32_t repeats,
+                             gm_tune_result *out);
 
 /* Matches n_pairs pairs in one batch (Sec. 6.2; App. A Steps 2-4 for all pairs at once) and writes, in the pairs'
  * order, the match list of every pair sorted by the query index i:

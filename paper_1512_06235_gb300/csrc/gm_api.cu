@@ -457,6 +457,7 @@ gm_status gm_create(const gm_config *cfg, gm_ctx **out)
     ctx->path = cfg->path;
     ctx->cell_shift = cell_shift;
     ctx->max_inflight = cfg->max_inflight > 0 ? cfg->max_inflight : 2;
+    if (cfg->tuner_cache) ctx->tuner_cache = cfg->tuner_cache;
     if (cfg->cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     } else {
@@ -491,7 +492,7 @@ gm_status gm_destroy(gm_ctx *ctx)
     }
     ctx->images.clear();
     workspace_free(ctx, ctx->ws);
-    for (DevBuf *b : {&ctx->d_imgs, &ctx->d_maps, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap})
+    for (DevBuf *b : {&ctx->d_imgs, &ctx->d_maps, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap, &ctx->d_tune})
         free_dev(ctx, *b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -666,6 +667,8 @@ gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t hei
         ctx->bytes_images += tot;
     }
     img->dev = dev;
+    img->scale = d_scale;
+    img->has_scale = n > 0 && scale != nullptr;
     // device image table (grow keeps old entries)
     const size_t need = sizeof(ImageDev) * ctx->slots.size();
     if (ctx->d_imgs.bytes < need) {

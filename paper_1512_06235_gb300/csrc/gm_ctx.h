@@ -33,6 +33,8 @@ struct ImageSlot {
     TmaMaps maps{};
     void *block = nullptr;
     size_t bytes = 0;
+    const float *scale = nullptr;   // keypoint scales in the caller's order (inside block)
+    bool has_scale = false;
 };
 
 // Everything one batch needs on the device and in pinned host memory.  The synchronous API owns one; every
@@ -105,7 +107,8 @@ struct gm_ctx {
     size_t bytes_work = 0;          // every DevBuf of the context and of the server slots
 
     gm::Workspace ws;               // synchronous calls
-    gm::DevBuf d_stage, d_work, d_bad, d_bitmap;
+    gm::DevBuf d_stage, d_work, d_bad, d_bitmap, d_tune;
+    std::string tuner_cache;        // gm_autotune's settings file ("" = none)
     gm_stats stats{};
     std::recursive_mutex mu;        // guards images, slots, budget counters and ws
 

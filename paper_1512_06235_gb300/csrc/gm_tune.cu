@@ -1,0 +1,211 @@
+// gm_tune.cu -- gm_autotune: picks the distance path, the query-group size of the mma path and the grid cell size
+// for a batch by timing them on the device.
+//
+// Every setting computes the same match lists (each one is exact), so the tuner only looks at time.  Candidates:
+// path tc, mma with 16- and 32-query groups, simt; cell sizes 4, 8 and 16 px.  A cell size other than the one an
+// image was binned with needs the image re-binned: its resident copy is put back into the caller's order (keypoint
+// i at index i, descriptors b = b' + 128) by one kernel and registered again through gm_image_put.  The winner is
+// left in the context (options, and the batch's images binned with the winning cell size) and, with a tuner_cache
+// file configured, stored there under the batch's signature; a later call with the same signature applies it
+// without timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cinttypes>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "gm_ctx.h"
+
+namespace gm {
+
+gm_status prepare_pair(gm_ctx *ctx, const gm_pair &pr, int64_t k, PairDev &pd);
+
+namespace {
+
+// caller's order from the cell order: xy[perm[p]] = xy_cell[p], desc[perm[p]] = desc_cell[p] ^ 0x80 (b' + 128)
+__global__ void unpermute_kernel(const float2 *__restrict__ xy_c, const int8_t *__restrict__ desc_c,
+                                 const int32_t *__restrict__ perm, int n, float2 *__restrict__ xy,
+                                 uint8_t *__restrict__ desc)
+{
+    const int p = blockIdx.x;
+    if (p >= n) return;
+    const int o = perm[p];
+    if (threadIdx.x == 0) xy[o] = xy_c[p];
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(desc_c + (int64_t)p * kDim);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(desc + (int64_t)o * kDim);
+    dst[threadIdx.x] = src[threadIdx.x] ^ 0x80808080u;
+}
+
+#define GM_CUDA_T(call)                                                                                \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return gm::fail(GM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Re-bins a resident image with cell shift `sh` (no-op when it already has it).
+gm_status rebin(gm_ctx *ctx, ImageSlot *img, int sh)
+{
+    if (img->dev.cell_shift == sh) return GM_OK;
+    const int n = img->dev.n;
+    const size_t N = (size_t)std::max(n, 1);
+    const size_t xy_b = align_up(8 * N, 256), desc_b = align_up(128 * N, 256), sc_b = align_up(4 * N, 256);
+    gm_status st = ensure_dev(ctx, ctx->d_tune, xy_b + desc_b + sc_b);
+    if (st != GM_OK) return st;
+    char *t = static_cast<char *>(ctx->d_tune.p);
+    float2 *xy = reinterpret_cast<float2 *>(t);
+    uint8_t *desc = reinterpret_cast<uint8_t *>(t + xy_b);
+    float *scale = reinterpret_cast<float *>(t + xy_b + desc_b);
+    cudaStream_t s = ctx->ws.stream;
+    if (n > 0) {
+        unpermute_kernel<<<n, kDim / 4, 0, s>>>(img->dev.xy, img->dev.desc, img->dev.perm, n, xy, desc);
+        GM_CUDA_T(cudaGetLastError());
+        if (img->has_scale) GM_CUDA_T(cudaMemcpyAsync(scale, img->scale, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    }
+    const int32_t saved = ctx->cell_shift;
+    ctx->cell_shift = sh;
+    st = gm_image_put(ctx, img->id, img->dev.width, img->dev.height, n, reinterpret_cast<const float *>(xy),
+                      img->has_scale ? scale : nullptr, desc, 1);
+    ctx->cell_shift = saved;
+    return st;
+}
+
+std::string signature(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs)
+{
+    int64_t qa = 0, nb = 0;
+    double dsum = 0.0;
+    int32_t wmax = 0, hmax = 0, ninf = 0;
+    for (int32_t k = 0; k < n_pairs; ++k) {
+        const ImageSlot *a = ctx->images.at(pairs[k].img_a), *b = ctx->images.at(pairs[k].img_b);
+        qa += a->dev.n;
+        nb += b->dev.n;
+        if (std::isinf(pairs[k].band_px)) ++ninf;
+        else dsum += pairs[k].band_px;
+        wmax = std::max(wmax, b->dev.width);
+        hmax = std::max(hmax, b->dev.height);
+    }
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "pairs=%d queries=%" PRId64 " targets=%" PRId64 " band_sum=%.0f whole_image=%d w=%d h=%d",
+                  n_pairs, qa, nb, dsum, ninf, wmax, hmax);
+    return buf;
+}
+
+bool cache_lookup(const std::string &file, const std::string &sig, gm_tune_result &r)
+{
+    FILE *f = std::fopen(file.c_str(), "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        const char *bar = std::strchr(line, '|');
+        if (!bar || std::string(line, bar - line) != sig) continue;
+        gm_tune_result t{};
+        if (std::sscanf(bar + 1, " path=%d group=%d cell=%d ms=%f", &t.path, &t.mma_group, &t.cell_px, &t.ms) == 4) {
+            r = t;
+            found = true;   // the last entry for a signature wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &file, const std::string &sig, const gm_tune_result &r)
+{
+    FILE *f = std::fopen(file.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "%s| path=%d group=%d cell=%d ms=%.4f\n", sig.c_str(), r.path, r.mma_group, r.cell_px, r.ms);
+    std::fclose(f);
+}
+
+}  // namespace
+}  // namespace gm
+
+extern "C" {
+
+gm_status gm_autotune(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int32_t repeats, gm_tune_result *out)
+{
+    using namespace gm;
+    if (!ctx || n_pairs <= 0 || !pairs || !out || repeats < 1 || repeats > 100)
+        return fail(GM_ERR_INVALID, "gm_autotune: bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    GM_CUDA_T(cudaSetDevice(ctx->device));
+    for (int32_t k = 0; k < n_pairs; ++k) {
+        PairDev pd;
+        const gm_status st = prepare_pair(ctx, pairs[k], k, pd);
+        if (st != GM_OK) return st;
+    }
+    std::set<int32_t> ids;
+    for (int32_t k = 0; k < n_pairs; ++k) {
+        ids.insert(pairs[k].img_a);
+        ids.insert(pairs[k].img_b);
+    }
+    auto apply = [&](const gm_tune_result &r) -> gm_status {
+        int sh = 0;
+        while ((1 << sh) < r.cell_px) ++sh;
+        for (int32_t id : ids) {
+            const gm_status st = rebin(ctx, ctx->images.at(id), sh);
+            if (st != GM_OK) return st;
+        }
+        ctx->cell_shift = sh;
+        ctx->path = r.path;
+        ctx->mma_mt = r.mma_group / 16;
+        return GM_OK;
+    };
+    const std::string sig = signature(ctx, n_pairs, pairs);
+    gm_tune_result best{};
+    if (!ctx->tuner_cache.empty() && cache_lookup(ctx->tuner_cache, sig, best)) {
+        best.from_cache = 1;
+        const gm_status st = apply(best);
+        if (st != GM_OK) return st;
+        *out = best;
+        return GM_OK;
+    }
+    int64_t cap = 0;
+    for (int32_t k = 0; k < n_pairs; ++k) cap += ctx->images.at(pairs[k].img_a)->dev.n;
+    std::vector<int64_t> off(n_pairs + 1);
+    const size_t rows_b = align_up(sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(cap, 1), 256);
+    // the match rows of the trial runs go to the tuner's own device buffer (re-binning reuses it later)
+    const int32_t saved_path = ctx->path, saved_mt = ctx->mma_mt, saved_graph = ctx->graph;
+    ctx->graph = 0;
+    best.ms = INFINITY;
+    const int cells[3] = {4, 8, 16};
+    const int cand[4][2] = {{GM_PATH_TC, 16}, {GM_PATH_MMA, 16}, {GM_PATH_MMA, 32}, {GM_PATH_SIMT, 16}};
+    gm_status st = GM_OK;
+    for (int ci = 0; ci < 3 && st == GM_OK; ++ci) {
+        for (int32_t id : ids)
+            if ((st = rebin(ctx, ctx->images.at(id), ci + 2)) != GM_OK) break;
+        if (st != GM_OK) break;
+        for (int pi = 0; pi < 4 && st == GM_OK; ++pi) {
+            ctx->path = cand[pi][0];
+            ctx->mma_mt = cand[pi][1] / 16;
+            if ((st = ensure_dev(ctx, ctx->d_tune, rows_b)) != GM_OK) break;
+            float ms = INFINITY;
+            for (int r = 0; r <= repeats && st == GM_OK; ++r) {   // one untimed warm-up run
+                int64_t nw = 0;
+                st = gm_match_pairs(ctx, n_pairs, pairs, off.data(), static_cast<int32_t *>(ctx->d_tune.p), cap, &nw);
+                if (st == GM_OK && r > 0) ms = std::min(ms, ctx->stats.ms_device);
+            }
+            if (st == GM_OK && ms < best.ms) {
+                best.path = cand[pi][0];
+                best.mma_group = cand[pi][1];
+                best.cell_px = cells[ci];
+                best.ms = ms;
+            }
+        }
+    }
+    ctx->path = saved_path;
+    ctx->mma_mt = saved_mt;
+    ctx->graph = saved_graph;
+    if (st != GM_OK) return st;
+    best.from_cache = 0;
+    if ((st = apply(best)) != GM_OK) return st;
+    if (!ctx->tuner_cache.empty()) cache_store(ctx->tuner_cache, sig, best);
+    *out = best;
+    return GM_OK;
+}
+
+}  // extern "C"

@@ -58,6 +58,14 @@ class GmServingStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GmTuneResult(ctypes.Structure):
+    _fields_ = [("path", c_i32), ("mma_group", c_i32), ("cell_px", c_i32), ("ms", ctypes.c_float),
+                ("from_cache", c_i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GeomatchError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
@@ -78,6 +86,7 @@ _SIGNATURES = {
                                    ctypes.POINTER(c_i64)]),
     "gm_band_candidates_static": (c_i32, [c_p, ctypes.POINTER(GmPair), c_i32, c_i32, c_p, c_p, c_i64,
                                           ctypes.POINTER(c_i64)]),
+    "gm_autotune": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_i32, ctypes.POINTER(GmTuneResult)]),
     "gm_get_stats": (c_i32, [c_p, ctypes.POINTER(GmStats)]),
     "gm_submit": (c_i32, [c_p, ctypes.POINTER(GmPair), ctypes.POINTER(c_u64)]),
     "gm_poll": (c_i32, [c_p, c_u64, c_p, c_i64, ctypes.POINTER(c_i64), c_i32, ctypes.POINTER(ctypes.c_double)]),
@@ -147,9 +156,10 @@ def _pairs_array(pairs):
 # ---------------------------------------------------------------------------------------------- C mirrors
 
 def gm_create(device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 2, cuda_stream: int = 0,
-              path: int = GM_PATH_AUTO, cell_px: int = 0):
+              path: int = GM_PATH_AUTO, cell_px: int = 0, tuner_cache: str = None):
     lib = load_library()
-    cfg = GmConfig(device, mem_budget_bytes, max_inflight, c_p(cuda_stream or None), path, cell_px, None)
+    cfg = GmConfig(device, mem_budget_bytes, max_inflight, c_p(cuda_stream or None), path, cell_px,
+                   tuner_cache.encode() if tuner_cache else None)
     h = c_p()
     _check(lib.gm_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h
@@ -227,6 +237,13 @@ def gm_band_candidates_static(ctx, pair, query_begin: int, query_count: int, can
     return n.value
 
 
+def gm_autotune(ctx, pairs, repeats: int = 3) -> dict:
+    arr = _pairs_array(pairs)
+    r = GmTuneResult()
+    _check(load_library().gm_autotune(ctx, len(pairs), arr, repeats, ctypes.byref(r)), ctx)
+    return r.as_dict()
+
+
 def gm_get_stats(ctx) -> dict:
     s = GmStats()
     _check(load_library().gm_get_stats(ctx, ctypes.byref(s)), ctx)
@@ -279,11 +296,11 @@ class Context:
     """A matcher context on one GPU: resident images, batch matching, candidate sets and serving."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 2, stream=None,
-                 path: int = GM_PATH_AUTO, cell_px: int = 0):
+                 path: int = GM_PATH_AUTO, cell_px: int = 0, tuner_cache: str = None):
         handle = 0
         if stream is not None:
             handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        self.h = gm_create(device, mem_budget_bytes, max_inflight, handle, path, cell_px)
+        self.h = gm_create(device, mem_budget_bytes, max_inflight, handle, path, cell_px, tuner_cache)
         self.n = {}
         self.device = device
 
@@ -350,6 +367,9 @@ class Context:
 
     def stats(self) -> dict:
         return gm_get_stats(self.h)
+
+    def autotune(self, pairs, repeats: int = 3) -> dict:
+        return gm_autotune(self.h, pairs, repeats)
 
     def submit(self, pair) -> int:
         return gm_submit(self.h, pair)

@@ -236,6 +236,36 @@ def test_graph_replay_equal(gm, facade_scene):
             np.testing.assert_array_equal(got[k], ref_b[k], err_msg=f"second batch pair {k} (same shape {same_shape})")
 
 
+def test_autotune_and_cache(gm, facade_scene, tmp_path):
+    """gm_autotune leaves a valid setting whose lists equal the default run's; the cache file gives the same
+    setting back without timing."""
+    sc = facade_scene
+    pairs = sc.pairs[:24]
+    ref, _ = _gpu_rows(gm, sc, pairs=pairs)
+    cache = str(tmp_path / "tune.txt")
+    used = sorted({p.a for p in pairs} | {p.b for p in pairs})
+    with gm.Context(device=0, tuner_cache=cache) as ctx:
+        for k in used:
+            ctx.put_image(k, sc.images[k])
+        r = ctx.autotune(pairs, repeats=1)
+        assert r["from_cache"] == 0 and r["cell_px"] in (4, 8, 16) and r["mma_group"] in (16, 32)
+        assert r["path"] in (gm.GM_PATH_TC, gm.GM_PATH_MMA, gm.GM_PATH_SIMT) and r["ms"] > 0
+        off, m = ctx.match_pairs(pairs)
+        got = gm.split_matches(off, m)
+        for k in range(len(pairs)):
+            np.testing.assert_array_equal(got[k], ref[k])
+    with gm.Context(device=0, tuner_cache=cache) as ctx:
+        for k in used:
+            ctx.put_image(k, sc.images[k])
+        r2 = ctx.autotune(pairs, repeats=1)
+        assert r2["from_cache"] == 1
+        assert (r2["path"], r2["mma_group"], r2["cell_px"]) == (r["path"], r["mma_group"], r["cell_px"])
+        off, m = ctx.match_pairs(pairs)
+        got = gm.split_matches(off, m)
+        for k in range(len(pairs)):
+            np.testing.assert_array_equal(got[k], ref[k])
+
+
 def test_stream_buffer_overflow_reruns(gm, facade_scene):
     """A candidate-stream buffer far too small for the batch forces the grow-and-rerun path; results unchanged."""
     sc = facade_scene
