@@ -518,9 +518,10 @@ def main():
     if not args.no_graph:
         e2e_ctx.set_option(gm.GM_OPT_GRAPH, 1)
 
-    def e2e_step():
-        for k, (w, h, xy, scl, ds) in enumerate(pinned):
-            gm.gm_image_put(e2e_ctx.h, k, w, h, xy, scl, ds)
+    batch = [(k, w, h, xy, scl, ds) for k, (w, h, xy, scl, ds) in enumerate(pinned)]
+
+    def e2e_step():   # all images of the step in one gm_images_put call, then the batch
+        gm.gm_images_put(e2e_ctx.h, batch)
         return gm.gm_match_pairs(e2e_ctx.h, gp, off_h, rows_h, cap)
 
     e2e_step()

@@ -140,6 +140,22 @@ GM_API gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value);
 GM_API gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t height, int32_t n,
                        const float *xy, const float *scale, const uint8_t *desc, int32_t on_device);
 
+/* One image of gm_images_put: the arguments of gm_image_put. */
+typedef struct {
+    int32_t image_id;
+    int32_t width, height;
+    int32_t n;
+    const float *xy;             /* float32 [n][2] */
+    const float *scale;          /* float32 [n] or NULL */
+    const uint8_t *desc;         /* uint8 [n][128] */
+} gm_image;
+
+/* Registers `count` images at once (App. A Step 1 for each; same arguments, layout and errors as gm_image_put,
+ * all pointers host memory (on_device = 0) or all device memory (1)).  Every keypoint of every image is checked
+ * before anything registered changes; the device work of all images is enqueued back to back, so a batch of
+ * images costs two stream synchronisations instead of two per image.  An id given twice is GM_ERR_INVALID. */
+GM_API gm_status gm_images_put(gm_ctx *ctx, int32_t count, const gm_image *images, int32_t on_device);
+
 /* Drops image `image_id` from the context.  GM_ERR_NOT_FOUND if unknown. */
 GM_API gm_status gm_image_evict(gm_ctx *ctx, int32_t image_id);
 

@@ -542,185 +542,272 @@ gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value)
     }
 }
 
-gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t height, int32_t n, const float *xy,
-                       const float *scale, const uint8_t *desc, int32_t on_device)
+}  // extern "C"
+
+namespace gm {
+namespace {
+
+// Layout of one resident image block: xy, perm, inv_perm, desc, norm, col_off, xy_r, idx_r, row_off, desc_h, scale,
+// norm256, rec (256-byte aligned arrays).
+struct ImageLayout {
+    int sh = 0, gx = 0, gy = 0;
+    int64_t m = 0;
+    size_t offs[13] = {};
+    size_t tot = 0;
+};
+
+ImageLayout image_layout(const gm_ctx *ctx, int32_t width, int32_t height, int32_t n)
 {
-    if (!ctx) return fail(GM_ERR_INVALID, "gm_image_put: null context");
-    if (image_id < 0 || width <= 0 || height <= 0 || width > (1 << 20) || height > (1 << 20) || n < 0 ||
-        (n > 0 && (!xy || !desc)) || (on_device != 0 && on_device != 1))
-        return fail(GM_ERR_INVALID, "gm_image_put: bad arguments (id %d, %dx%d, n %d)", image_id, width, height, n);
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    GM_CUDA(cudaSetDevice(ctx->device));
+    ImageLayout L;
     // grid cell: the configured size, or automatically 4 px unless the image is so large that the grid would cross
     // more lines than the tcgen05 kernel's run table holds
-    int sh = ctx->cell_shift;
-    if (sh == 0) {
-        sh = kMinCellShift;
-        while (sh < kMaxCellShift && ((std::max(width, height) + (1 << sh) - 1) >> sh) > match_tc_max_grid_lines()) ++sh;
+    L.sh = ctx->cell_shift;
+    if (L.sh == 0) {
+        L.sh = kMinCellShift;
+        while (L.sh < kMaxCellShift && ((std::max(width, height) + (1 << L.sh) - 1) >> L.sh) > match_tc_max_grid_lines())
+            ++L.sh;
     }
-    const int cs = 1 << sh;
-    const int gx = (width + cs - 1) / cs, gy = (height + cs - 1) / cs;
-    const int64_t m = (int64_t)gx * gy;
-    if (m + 2 > INT32_MAX / 4) return fail(GM_ERR_INVALID, "gm_image_put: grid too large");
+    const int cs = 1 << L.sh;
+    L.gx = (width + cs - 1) / cs;
+    L.gy = (height + cs - 1) / cs;
+    L.m = (int64_t)L.gx * L.gy;
     const size_t N = (size_t)n;
-    // one block: xy, perm, inv_perm, desc, norm, col_off, xy_r, idx_r, row_off, desc_h, scale, norm256, rec
-    size_t sz[13] = {8 * N, 4 * N, 4 * N, 128 * N, 4 * N, 4 * (size_t)(m + 2), 8 * N, 4 * N, 4 * (size_t)(m + 2),
-                     256 * N, 4 * N, 4 * N, 16 * (N + 1)};
-    size_t offs[13], tot = 0;
+    const size_t sz[13] = {8 * N, 4 * N, 4 * N, 128 * N, 4 * N, 4 * (size_t)(L.m + 2), 8 * N, 4 * N,
+                           4 * (size_t)(L.m + 2), 256 * N, 4 * N, 4 * N, 16 * (N + 1)};
     for (int k = 0; k < 13; ++k) {
-        offs[k] = tot;
-        tot += align_up(std::max<size_t>(sz[k], 1), 256);
+        L.offs[k] = L.tot;
+        L.tot += align_up(std::max<size_t>(sz[k], 1), 256);
     }
-    auto it = ctx->images.find(image_id);
-    const bool reuse = it != ctx->images.end() && it->second->bytes >= tot;
-    const size_t replaced = it != ctx->images.end() ? it->second->bytes : 0;
-    if (!reuse && ctx->budget && ctx->bytes_images - replaced + tot + ctx->bytes_work > ctx->budget)
-        return fail(GM_ERR_BUDGET, "gm_image_put: image %d (%zu bytes) exceeds the device-memory budget", image_id, tot);
-    cudaStream_t s = ctx->ws.stream;
-    const float2 *raw_xy = reinterpret_cast<const float2 *>(xy);
-    const uint8_t *raw_desc = desc;
-    gm_status st;
-    // 1. stage host inputs and validate the keypoints (nothing registered is touched yet)
-    const size_t xy_al = align_up(8 * N + 1, 256);
-    if (!on_device && n > 0) {
-        if ((st = ensure_dev(ctx, ctx->d_stage, xy_al + align_up(128 * N + 1, 256))) != GM_OK) return st;
-        char *sp = static_cast<char *>(ctx->d_stage.p);
-        GM_CUDA(cudaMemcpyAsync(sp, xy, 8 * N, cudaMemcpyHostToDevice, s));
-        GM_CUDA(cudaMemcpyAsync(sp + xy_al, desc, 128 * N, cudaMemcpyHostToDevice, s));
-        raw_xy = reinterpret_cast<const float2 *>(sp);
-        raw_desc = reinterpret_cast<const uint8_t *>(sp + xy_al);
-    }
-    if ((st = ensure_dev(ctx, ctx->d_work, sizeof(int32_t) * (2 * (size_t)(m + 3) + 2 * (size_t)(m / 1024 + 3))))
-        != GM_OK)
-        return st;
-    if ((st = ensure_dev(ctx, ctx->d_bad, 256)) != GM_OK) return st;
-    unsigned long long *d_bad = static_cast<unsigned long long *>(ctx->d_bad.p);
-    int32_t *work = static_cast<int32_t *>(ctx->d_work.p);
-    GM_CUDA(launch_bucket_count(raw_xy, n, width, height, sh, gx, gy, work, d_bad, s));
-    unsigned long long bad = 0;
-    GM_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
-    GM_CUDA(cudaStreamSynchronize(s));
-    if (bad) return fail(GM_ERR_INVALID, "gm_image_put: %llu keypoints outside [0,%d)x[0,%d)", bad, width, height);
-    // 2. destination block: the replaced image's block when it is large enough (no serving batch may still read it)
-    if (ctx->server) server_drain(ctx->server);
-    void *block = nullptr;
-    if (reuse) {
-        block = it->second->block;
-    } else if (cudaMalloc(&block, tot) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(GM_ERR_NOMEM, "gm_image_put: cudaMalloc of %zu bytes failed", tot);
-    }
+    return L;
+}
+
+ImageDev image_dev(const ImageLayout &L, void *block, int32_t width, int32_t height, int32_t n)
+{
     char *bp = static_cast<char *>(block);
     ImageDev dev{};
-    dev.n = n; dev.width = width; dev.height = height; dev.cell_shift = sh; dev.gx = gx; dev.gy = gy;
-    dev.xy = reinterpret_cast<float2 *>(bp + offs[0]);
-    dev.perm = reinterpret_cast<int32_t *>(bp + offs[1]);
-    dev.inv_perm = reinterpret_cast<int32_t *>(bp + offs[2]);
-    dev.desc = reinterpret_cast<int8_t *>(bp + offs[3]);
-    dev.norm = reinterpret_cast<int32_t *>(bp + offs[4]);
-    dev.col_off = reinterpret_cast<int32_t *>(bp + offs[5]);
-    dev.xy_r = reinterpret_cast<float2 *>(bp + offs[6]);
-    dev.idx_r = reinterpret_cast<int32_t *>(bp + offs[7]);
-    dev.row_off = reinterpret_cast<int32_t *>(bp + offs[8]);
-    dev.desc_h = reinterpret_cast<uint16_t *>(bp + offs[9]);
-    float *d_scale = reinterpret_cast<float *>(bp + offs[10]);
-    dev.norm256 = reinterpret_cast<int32_t *>(bp + offs[11]);
-    dev.rec = reinterpret_cast<int4 *>(bp + offs[12]);
-    cudaError_t e = launch_bucket_build(raw_xy, raw_desc, n, width, height, sh, gx, gy, const_cast<float2 *>(dev.xy),
-                                        const_cast<int32_t *>(dev.perm), const_cast<int32_t *>(dev.inv_perm),
-                                        const_cast<int8_t *>(dev.desc), const_cast<int32_t *>(dev.norm),
-                                        const_cast<int32_t *>(dev.norm256), const_cast<int32_t *>(dev.col_off), const_cast<float2 *>(dev.xy_r),
-                                        const_cast<int32_t *>(dev.idx_r), const_cast<int32_t *>(dev.row_off),
-                                        const_cast<uint16_t *>(dev.desc_h), const_cast<int4 *>(dev.rec), work, s);
-    if (e == cudaSuccess && n > 0 && scale)
-        e = cudaMemcpyAsync(d_scale, scale, 4 * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) {
-        if (!reuse) cudaFree(block);
-        return fail(GM_ERR_CUDA, "gm_image_put: %s", cudaGetErrorString(e));
+    dev.n = n; dev.width = width; dev.height = height; dev.cell_shift = L.sh; dev.gx = L.gx; dev.gy = L.gy;
+    dev.xy = reinterpret_cast<float2 *>(bp + L.offs[0]);
+    dev.perm = reinterpret_cast<int32_t *>(bp + L.offs[1]);
+    dev.inv_perm = reinterpret_cast<int32_t *>(bp + L.offs[2]);
+    dev.desc = reinterpret_cast<int8_t *>(bp + L.offs[3]);
+    dev.norm = reinterpret_cast<int32_t *>(bp + L.offs[4]);
+    dev.col_off = reinterpret_cast<int32_t *>(bp + L.offs[5]);
+    dev.xy_r = reinterpret_cast<float2 *>(bp + L.offs[6]);
+    dev.idx_r = reinterpret_cast<int32_t *>(bp + L.offs[7]);
+    dev.row_off = reinterpret_cast<int32_t *>(bp + L.offs[8]);
+    dev.desc_h = reinterpret_cast<uint16_t *>(bp + L.offs[9]);
+    dev.norm256 = reinterpret_cast<int32_t *>(bp + L.offs[11]);
+    dev.rec = reinterpret_cast<int4 *>(bp + L.offs[12]);
+    return dev;
+}
+
+// Grows a per-slot device table (image records or TMA descriptors) to `need` bytes, keeping its contents.
+gm_status grow_table(gm_ctx *ctx, DevBuf &t, size_t need, size_t min_bytes, cudaStream_t s, const char *what)
+{
+    if (t.bytes >= need) return GM_OK;
+    DevBuf nb;
+    const size_t cap = align_up(std::max(need * 2, min_bytes), 256);
+    if (cudaMalloc(&nb.p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GM_ERR_NOMEM, "image registration: %s table allocation failed", what);
     }
-    // 3. install: replace or take a free slot
-    ImageSlot *img = nullptr;
-    if (it != ctx->images.end()) {
-        img = it->second;
+    nb.bytes = cap;
+    if (t.p) {
+        cudaMemcpyAsync(nb.p, t.p, t.bytes, cudaMemcpyDeviceToDevice, s);
+        cudaStreamSynchronize(s);
+    }
+    free_dev(ctx, t);
+    t = nb;
+    ctx->bytes_work += cap;
+    return GM_OK;
+}
+
+// Registers `count` images (App. A Step 1).  All inputs are validated before anything registered changes; the
+// device work of all images is enqueued back to back with two stream synchronisations in total (after the
+// keypoint check, and at the end).
+gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t on_device, const char *fn)
+{
+    if (!ctx) return fail(GM_ERR_INVALID, "%s: null context", fn);
+    if (count < 0 || (count > 0 && !imgs) || (on_device != 0 && on_device != 1))
+        return fail(GM_ERR_INVALID, "%s: bad arguments", fn);
+    for (int32_t k = 0; k < count; ++k) {
+        const gm_image &g = imgs[k];
+        if (g.image_id < 0 || g.width <= 0 || g.height <= 0 || g.width > (1 << 20) || g.height > (1 << 20) || g.n < 0 ||
+            (g.n > 0 && (!g.xy || !g.desc)))
+            return fail(GM_ERR_INVALID, "%s: bad arguments (id %d, %dx%d, n %d)", fn, g.image_id, g.width, g.height, g.n);
+        for (int32_t l = 0; l < k; ++l)
+            if (imgs[l].image_id == g.image_id) return fail(GM_ERR_INVALID, "%s: image id %d given twice", fn, g.image_id);
+    }
+    if (count == 0) return GM_OK;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    GM_CUDA(cudaSetDevice(ctx->device));
+    std::vector<ImageLayout> L(count);
+    size_t stage_bytes = 0, work_ints = 0, new_bytes = 0, replaced = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        const gm_image &g = imgs[k];
+        L[k] = image_layout(ctx, g.width, g.height, g.n);
+        if (L[k].m + 2 > INT32_MAX / 4) return fail(GM_ERR_INVALID, "%s: grid too large (image %d)", fn, g.image_id);
+        if (!on_device) stage_bytes += align_up(8 * (size_t)g.n + 1, 256) + align_up(128 * (size_t)g.n + 1, 256);
+        work_ints = std::max(work_ints, 2 * (size_t)(L[k].m + 3) + 2 * (size_t)(L[k].m / 1024 + 3));
+        auto it = ctx->images.find(g.image_id);
+        const bool reuse = it != ctx->images.end() && it->second->bytes >= L[k].tot;
         if (!reuse) {
-            cudaFree(img->block);
-            ctx->bytes_images -= img->bytes;
-            img->block = block;
-            img->bytes = tot;
-            ctx->bytes_images += tot;
+            new_bytes += L[k].tot;
+            if (it != ctx->images.end()) replaced += it->second->bytes;
         }
-    } else {
-        img = new ImageSlot();
-        img->id = image_id;
-        int slot = -1;
-        for (size_t k = 0; k < ctx->slots.size(); ++k)
-            if (!ctx->slots[k]) { slot = (int)k; break; }
-        if (slot < 0) {
-            slot = (int)ctx->slots.size();
-            ctx->slots.push_back(nullptr);
-        }
-        img->slot = slot;
-        ctx->slots[slot] = img;
-        ctx->images[image_id] = img;
-        img->block = block;
-        img->bytes = tot;
-        ctx->bytes_images += tot;
     }
-    img->dev = dev;
-    img->scale = d_scale;
-    img->has_scale = n > 0 && scale != nullptr;
-    // device image table (grow keeps old entries)
-    const size_t need = sizeof(ImageDev) * ctx->slots.size();
-    if (ctx->d_imgs.bytes < need) {
-        DevBuf nb;
-        const size_t cap = align_up(std::max(need * 2, (size_t)4096), 256);
-        if (cudaMalloc(&nb.p, cap) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(GM_ERR_NOMEM, "gm_image_put: image table allocation failed");
-        }
-        nb.bytes = cap;
-        if (ctx->d_imgs.p) {
-            cudaMemcpyAsync(nb.p, ctx->d_imgs.p, ctx->d_imgs.bytes, cudaMemcpyDeviceToDevice, s);
-            cudaStreamSynchronize(s);
-        }
-        free_dev(ctx, ctx->d_imgs);
-        ctx->d_imgs = nb;
-        ctx->bytes_work += cap;
-    }
-    GM_CUDA(cudaMemcpyAsync(static_cast<ImageDev *>(ctx->d_imgs.p) + img->slot, &img->dev, sizeof(ImageDev),
-                            cudaMemcpyHostToDevice, s));
-    // TMA descriptors of the image (tcgen05 path)
+    if (ctx->budget && ctx->bytes_images - replaced + new_bytes + ctx->bytes_work > ctx->budget)
+        return fail(GM_ERR_BUDGET, "%s: %zu bytes of images exceed the device-memory budget", fn, new_bytes);
+    cudaStream_t s = ctx->ws.stream;
+    gm_status st;
+    // 1. stage host inputs and check every keypoint (nothing registered is touched yet)
+    std::vector<const float2 *> raw_xy(count);
+    std::vector<const uint8_t *> raw_desc(count);
+    if (!on_device && (st = ensure_dev(ctx, ctx->d_stage, stage_bytes + 256)) != GM_OK) return st;
     {
-        const size_t need_maps = sizeof(TmaMaps) * ctx->slots.size();
-        if (ctx->d_maps.bytes < need_maps) {
-            DevBuf nb;
-            const size_t cap = align_up(std::max(need_maps * 2, (size_t)(sizeof(TmaMaps) * 16)), 256);
-            if (cudaMalloc(&nb.p, cap) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(GM_ERR_NOMEM, "gm_image_put: TMA descriptor table allocation failed");
-            }
-            nb.bytes = cap;
-            if (ctx->d_maps.p) {
-                cudaMemcpyAsync(nb.p, ctx->d_maps.p, ctx->d_maps.bytes, cudaMemcpyDeviceToDevice, s);
-                cudaStreamSynchronize(s);
-            }
-            free_dev(ctx, ctx->d_maps);
-            ctx->d_maps = nb;
-            ctx->bytes_work += cap;
+        char *sp = static_cast<char *>(ctx->d_stage.p);
+        for (int32_t k = 0; k < count; ++k) {
+            const gm_image &g = imgs[k];
+            raw_xy[k] = reinterpret_cast<const float2 *>(g.xy);
+            raw_desc[k] = g.desc;
+            if (on_device || g.n == 0) continue;
+            const size_t N = (size_t)g.n, xy_al = align_up(8 * N + 1, 256);
+            GM_CUDA(cudaMemcpyAsync(sp, g.xy, 8 * N, cudaMemcpyHostToDevice, s));
+            GM_CUDA(cudaMemcpyAsync(sp + xy_al, g.desc, 128 * N, cudaMemcpyHostToDevice, s));
+            raw_xy[k] = reinterpret_cast<const float2 *>(sp);
+            raw_desc[k] = reinterpret_cast<const uint8_t *>(sp + xy_al);
+            sp += xy_al + align_up(128 * N + 1, 256);
         }
+    }
+    if ((st = ensure_dev(ctx, ctx->d_work, sizeof(int32_t) * work_ints)) != GM_OK) return st;
+    if ((st = ensure_dev(ctx, ctx->d_bad, sizeof(unsigned long long) * (size_t)count)) != GM_OK) return st;
+    unsigned long long *d_bad = static_cast<unsigned long long *>(ctx->d_bad.p);
+    int32_t *work = static_cast<int32_t *>(ctx->d_work.p);
+    for (int32_t k = 0; k < count; ++k)
+        GM_CUDA(launch_bucket_count(raw_xy[k], imgs[k].n, imgs[k].width, imgs[k].height, L[k].sh, L[k].gx, L[k].gy, work,
+                                    d_bad + k, s));
+    std::vector<unsigned long long> bad(count);
+    GM_CUDA(cudaMemcpyAsync(bad.data(), d_bad, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, s));
+    GM_CUDA(cudaStreamSynchronize(s));
+    for (int32_t k = 0; k < count; ++k)
+        if (bad[k])
+            return fail(GM_ERR_INVALID, "%s: image %d: %llu keypoints outside [0,%d)x[0,%d)", fn, imgs[k].image_id,
+                        bad[k], imgs[k].width, imgs[k].height);
+    // 2. destination blocks: a replaced image's block when it is large enough (no serving batch may still read it)
+    if (ctx->server) server_drain(ctx->server);
+    std::vector<void *> block(count, nullptr);
+    std::vector<char> fresh(count, 0);
+    for (int32_t k = 0; k < count; ++k) {
+        auto it = ctx->images.find(imgs[k].image_id);
+        if (it != ctx->images.end() && it->second->bytes >= L[k].tot) {
+            block[k] = it->second->block;
+        } else if (cudaMalloc(&block[k], L[k].tot) != cudaSuccess) {
+            cudaGetLastError();
+            for (int32_t l = 0; l < k; ++l)
+                if (fresh[l]) cudaFree(block[l]);
+            return fail(GM_ERR_NOMEM, "%s: cudaMalloc of %zu bytes failed (image %d)", fn, L[k].tot, imgs[k].image_id);
+        } else {
+            fresh[k] = 1;
+        }
+    }
+    // 3. bin every image into its block (the count arrays are recomputed: the shared work buffer holds one image)
+    std::vector<ImageDev> dev(count);
+    cudaError_t e = cudaSuccess;
+    for (int32_t k = 0; k < count && e == cudaSuccess; ++k) {
+        const gm_image &g = imgs[k];
+        const ImageLayout &l = L[k];
+        dev[k] = image_dev(l, block[k], g.width, g.height, g.n);
+        const ImageDev &d = dev[k];
+        e = launch_bucket_count(raw_xy[k], g.n, g.width, g.height, l.sh, l.gx, l.gy, work, d_bad + k, s);
+        if (e == cudaSuccess)
+            e = launch_bucket_build(raw_xy[k], raw_desc[k], g.n, g.width, g.height, l.sh, l.gx, l.gy,
+                                    const_cast<float2 *>(d.xy), const_cast<int32_t *>(d.perm),
+                                    const_cast<int32_t *>(d.inv_perm), const_cast<int8_t *>(d.desc),
+                                    const_cast<int32_t *>(d.norm), const_cast<int32_t *>(d.norm256),
+                                    const_cast<int32_t *>(d.col_off), const_cast<float2 *>(d.xy_r),
+                                    const_cast<int32_t *>(d.idx_r), const_cast<int32_t *>(d.row_off),
+                                    const_cast<uint16_t *>(d.desc_h), const_cast<int4 *>(d.rec), work, s);
+        if (e == cudaSuccess && g.n > 0 && g.scale)
+            e = cudaMemcpyAsync(static_cast<char *>(block[k]) + l.offs[10], g.scale, 4 * (size_t)g.n,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    }
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        for (int32_t k = 0; k < count; ++k)
+            if (fresh[k]) cudaFree(block[k]);
+        return fail(GM_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    }
+    // 4. install: replace or take a free slot; TMA descriptors of each image (tcgen05 path)
+    for (int32_t k = 0; k < count; ++k) {
+        const gm_image &g = imgs[k];
+        auto it = ctx->images.find(g.image_id);
+        ImageSlot *img = nullptr;
+        if (it != ctx->images.end()) {
+            img = it->second;
+            if (fresh[k]) {
+                cudaFree(img->block);   // nothing reads the old block: serving was drained, synchronous calls ended
+                ctx->bytes_images -= img->bytes;
+                img->block = block[k];
+                img->bytes = L[k].tot;
+                ctx->bytes_images += L[k].tot;
+            }
+        } else {
+            img = new ImageSlot();
+            img->id = g.image_id;
+            int slot = -1;
+            for (size_t q = 0; q < ctx->slots.size(); ++q)
+                if (!ctx->slots[q]) { slot = (int)q; break; }
+            if (slot < 0) {
+                slot = (int)ctx->slots.size();
+                ctx->slots.push_back(nullptr);
+            }
+            img->slot = slot;
+            ctx->slots[slot] = img;
+            ctx->images[g.image_id] = img;
+            img->block = block[k];
+            img->bytes = L[k].tot;
+            ctx->bytes_images += L[k].tot;
+        }
+        img->dev = dev[k];
+        img->scale = reinterpret_cast<const float *>(static_cast<char *>(img->block) + L[k].offs[10]);
+        img->has_scale = g.n > 0 && g.scale != nullptr;
         TmaMaps maps;
         std::memset(&maps, 0, sizeof(maps));
-        if (n > 0) {
-            gm_status ms = encode_maps(dev, maps);
-            if (ms != GM_OK) return ms;
-        }
+        if (g.n > 0 && (st = encode_maps(img->dev, maps)) != GM_OK) return st;
         img->maps = maps;
+    }
+    // 5. device tables (grow keeps old entries), one copy each of every slot's entry
+    if ((st = grow_table(ctx, ctx->d_imgs, sizeof(ImageDev) * ctx->slots.size(), 4096, s, "image")) != GM_OK) return st;
+    if ((st = grow_table(ctx, ctx->d_maps, sizeof(TmaMaps) * ctx->slots.size(), sizeof(TmaMaps) * 16, s, "TMA descriptor"))
+        != GM_OK)
+        return st;
+    for (int32_t k = 0; k < count; ++k) {
+        const ImageSlot *img = ctx->images.at(imgs[k].image_id);
+        GM_CUDA(cudaMemcpyAsync(static_cast<ImageDev *>(ctx->d_imgs.p) + img->slot, &img->dev, sizeof(ImageDev),
+                                cudaMemcpyHostToDevice, s));
         GM_CUDA(cudaMemcpyAsync(static_cast<TmaMaps *>(ctx->d_maps.p) + img->slot, &img->maps, sizeof(TmaMaps),
                                 cudaMemcpyHostToDevice, s));
     }
     // the staged inputs and the table entries are read asynchronously: finish before returning
     GM_CUDA(cudaStreamSynchronize(s));
     return GM_OK;
+}
+
+}  // namespace
+}  // namespace gm
+
+extern "C" {
+
+gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t height, int32_t n, const float *xy,
+                       const float *scale, const uint8_t *desc, int32_t on_device)
+{
+    const gm_image g{image_id, width, height, n, xy, scale, desc};
+    return gm::put_images(ctx, 1, &g, on_device, "gm_image_put");
+}
+
+gm_status gm_images_put(gm_ctx *ctx, int32_t count, const gm_image *images, int32_t on_device)
+{
+    return gm::put_images(ctx, count, images, on_device, "gm_images_put");
 }
 
 gm_status gm_image_evict(gm_ctx *ctx, int32_t image_id)

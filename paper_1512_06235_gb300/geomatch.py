@@ -58,6 +58,11 @@ class GmServingStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GmImage(ctypes.Structure):
+    _fields_ = [("image_id", c_i32), ("width", c_i32), ("height", c_i32), ("n", c_i32), ("xy", c_p), ("scale", c_p),
+                ("desc", c_p)]
+
+
 class GmTuneResult(ctypes.Structure):
     _fields_ = [("path", c_i32), ("mma_group", c_i32), ("cell_px", c_i32), ("ms", ctypes.c_float),
                 ("from_cache", c_i32)]
@@ -86,6 +91,7 @@ _SIGNATURES = {
                                    ctypes.POINTER(c_i64)]),
     "gm_band_candidates_static": (c_i32, [c_p, ctypes.POINTER(GmPair), c_i32, c_i32, c_p, c_p, c_i64,
                                           ctypes.POINTER(c_i64)]),
+    "gm_images_put": (c_i32, [c_p, c_i32, ctypes.POINTER(GmImage), c_i32]),
     "gm_autotune": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_i32, ctypes.POINTER(GmTuneResult)]),
     "gm_get_stats": (c_i32, [c_p, ctypes.POINTER(GmStats)]),
     "gm_submit": (c_i32, [c_p, ctypes.POINTER(GmPair), ctypes.POINTER(c_u64)]),
@@ -183,6 +189,28 @@ def gm_image_put(ctx, image_id: int, width: int, height: int, xy, scale, desc):
         raise ValueError("gm_image_put: xy, scale and desc must all be host or all be device memory")
     _check(load_library().gm_image_put(ctx, image_id, width, height, n, pxy, psc, pds, dev_xy), ctx)
     del k1, k2, k3
+
+
+def gm_images_put(ctx, images):
+    """images: list of (image_id, width, height, xy, scale, desc), all host (numpy / pinned) or all device tensors."""
+    arr = (GmImage * max(1, len(images)))()
+    keep, devs = [], set()
+    for k, (iid, w, h, xy, scale, desc) in enumerate(images):
+        pxy, dxy, k1 = _ptr(xy)
+        psc, dsc, k2 = _ptr(scale)
+        pds, dds, k3 = _ptr(desc)
+        keep += [k1, k2, k3]
+        n = int(xy.shape[0])
+        if n:
+            devs.add(dxy)
+            devs.add(dds)
+            if scale is not None:
+                devs.add(dsc)
+        arr[k] = GmImage(iid, w, h, n, pxy, psc, pds)
+    if len(devs) > 1:
+        raise ValueError("gm_images_put: all arrays must be host memory or all device memory")
+    _check(load_library().gm_images_put(ctx, len(images), arr, devs.pop() if devs else 0), ctx)
+    del keep
 
 
 def gm_image_evict(ctx, image_id: int):
@@ -329,6 +357,12 @@ class Context:
             width, height, xy, scale, desc = image.width, image.height, image.xy, image.scale, image.desc
         gm_image_put(self.h, image_id, width, height, xy, scale, desc)
         self.n[image_id] = int(xy.shape[0])
+
+    def put_images(self, images: dict):
+        """images: {image_id: image} (objects with width, height, xy, scale, desc), registered in one call."""
+        gm_images_put(self.h, [(k, im.width, im.height, im.xy, im.scale, im.desc) for k, im in images.items()])
+        for k, im in images.items():
+            self.n[k] = int(im.xy.shape[0])
 
     def evict(self, image_id: int):
         gm_image_evict(self.h, image_id)

@@ -45,15 +45,17 @@ def test_struct_layouts_match_header():
     os.makedirs(os.path.dirname(src), exist_ok=True)
     with open(src, "w") as fh:
         fh.write('#include <stdio.h>\n#include <stddef.h>\n#include "geomatch.h"\nint main(void){\n'
-                 'printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gm_config), sizeof(gm_pair), sizeof(gm_stats), '
-                 'sizeof(gm_serving_stats), offsetof(gm_pair, band_px), offsetof(gm_pair, ratio_den), '
-                 'offsetof(gm_config, cuda_stream), sizeof(gm_tune_result), offsetof(gm_tune_result, ms));\nreturn 0;}\n')
+                 'printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gm_config), sizeof(gm_pair), '
+                 'sizeof(gm_stats), sizeof(gm_serving_stats), offsetof(gm_pair, band_px), offsetof(gm_pair, ratio_den), '
+                 'offsetof(gm_config, cuda_stream), sizeof(gm_tune_result), offsetof(gm_tune_result, ms), '
+                 'sizeof(gm_image), offsetof(gm_image, desc));\nreturn 0;}\n')
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
     vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [ctypes.sizeof(geomatch.GmConfig), ctypes.sizeof(geomatch.GmPair), ctypes.sizeof(geomatch.GmStats),
                     ctypes.sizeof(geomatch.GmServingStats), geomatch.GmPair.band_px.offset,
                     geomatch.GmPair.ratio_den.offset, geomatch.GmConfig.cuda_stream.offset,
-                    ctypes.sizeof(geomatch.GmTuneResult), geomatch.GmTuneResult.ms.offset]
+                    ctypes.sizeof(geomatch.GmTuneResult), geomatch.GmTuneResult.ms.offset,
+                    ctypes.sizeof(geomatch.GmImage), geomatch.GmImage.desc.offset]
 
 
 def test_no_cpu_fallback_when_library_missing(tmp_path):

@@ -266,6 +266,43 @@ def test_autotune_and_cache(gm, facade_scene, tmp_path):
             np.testing.assert_array_equal(got[k], ref[k])
 
 
+def test_images_put_batch_equals_single_puts(gm, facade_scene):
+    """gm_images_put (host arrays, then device tensors) registers the same images as gm_image_put one by one; an
+    out-of-image keypoint in any image of a batch is rejected and leaves the registered images as they were."""
+    import torch
+    sc = facade_scene
+    pairs = sc.pairs[:30]
+    used = sorted({p.a for p in pairs} | {p.b for p in pairs})
+    ref, st_ref = _gpu_rows(gm, sc, pairs=pairs)
+    for on_device in (False, True):
+        with gm.Context(device=0) as ctx:
+            if on_device:
+                imgs = {k: scenes.Image(sc.images[k].width, sc.images[k].height,
+                                        torch.from_numpy(sc.images[k].xy).cuda(), torch.from_numpy(sc.images[k].scale).cuda(),
+                                        torch.from_numpy(sc.images[k].desc).cuda(), sc.images[k].pid) for k in used}
+            else:
+                imgs = {k: sc.images[k] for k in used}
+            ctx.put_images(imgs)
+            off, m = ctx.match_pairs(pairs)
+            got = gm.split_matches(off, m)
+            for k in range(len(pairs)):
+                np.testing.assert_array_equal(got[k], ref[k], err_msg=f"device={on_device} pair {k}")
+            assert ctx.stats()["n_candidates"] == st_ref["n_candidates"]
+            # a bad keypoint in the second image of a new batch: nothing changes
+            bad = scenes.Image(sc.images[used[1]].width, sc.images[used[1]].height, sc.images[used[1]].xy.copy(),
+                               sc.images[used[1]].scale, sc.images[used[1]].desc, sc.images[used[1]].pid)
+            bad.xy[7] = [bad.width + 5.0, 1.0]
+            other = scenes.Image(sc.images[used[0]].width, sc.images[used[0]].height, sc.images[used[0]].xy[::-1].copy(),
+                                 sc.images[used[0]].scale, sc.images[used[0]].desc[::-1].copy(), sc.images[used[0]].pid)
+            with pytest.raises(gm.GeomatchError) as e:
+                ctx.put_images({used[0]: other, used[1]: bad})
+            assert e.value.status == gm.GM_ERR_INVALID
+            off, m = ctx.match_pairs(pairs)
+            got = gm.split_matches(off, m)
+            for k in range(len(pairs)):
+                np.testing.assert_array_equal(got[k], ref[k], err_msg=f"after rejected batch, pair {k}")
+
+
 def test_stream_buffer_overflow_reruns(gm, facade_scene):
     """A candidate-stream buffer far too small for the batch forces the grow-and-rerun path; results unchanged."""
     sc = facade_scene
