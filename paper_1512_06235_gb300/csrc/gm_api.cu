@@ -251,12 +251,13 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
 
     // distance path and work-item size
     int path = ctx->path == GM_PATH_AUTO ? GM_PATH_TC : ctx->path;
-    if (path == GM_PATH_TC) {   // the tcgen05 kernel's run table holds match_tc_max_grid_lines() grid lines
-        for (const PairDev &pd : ws.pd) {
-            const ImageDev &B = ctx->slots[pd.b]->dev;
-            if (std::max(B.gx, B.gy) > match_tc_max_grid_lines()) { path = GM_PATH_MMA; break; }
-        }
+    int32_t max_lines = 1;   // longest grid line count of the batch's target images
+    for (const PairDev &pd : ws.pd) {
+        const ImageDev &B = ctx->slots[pd.b]->dev;
+        max_lines = std::max(max_lines, std::max(B.gx, B.gy));
     }
+    // the tcgen05 kernel's run table holds match_tc_max_grid_lines() grid lines
+    if (path == GM_PATH_TC && max_lines > match_tc_max_grid_lines()) path = GM_PATH_MMA;
     const int mt = ctx->mma_mt;
     const int qpi = path == GM_PATH_SIMT ? kQueriesPerItem : path == GM_PATH_TC ? kTcQueriesPerItem : 16 * mt;
 
@@ -333,7 +334,8 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
                 if (path == GM_PATH_TC) {
                     GM_CUDA(launch_stream(imgs, d_proc, d_item_off, P, qorder, h_item_off[k], h_item_off[k + 1],
                                           static_cast<GroupDesc *>(ws.d_grec.p), static_cast<int32_t *>(ws.d_grows.p),
-                                          static_cast<int32_t *>(ws.d_stream.p), ws.stream_cap, stream_used, ctr, s));
+                                          static_cast<int32_t *>(ws.d_stream.p), ws.stream_cap, stream_used, ctr,
+                                          max_lines, s));
                     ++ws.launches;
                 }
                 GM_CUDA(launch_match(h_item_off[k], h_item_off[k + 1], 0));
@@ -345,7 +347,8 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
             if (path == GM_PATH_TC) {
                 GM_CUDA(launch_stream(imgs, d_proc, d_item_off, P, qorder, 0, n_items,
                                       static_cast<GroupDesc *>(ws.d_grec.p), static_cast<int32_t *>(ws.d_grows.p),
-                                      static_cast<int32_t *>(ws.d_stream.p), ws.stream_cap, stream_used, ctr, s));
+                                      static_cast<int32_t *>(ws.d_stream.p), ws.stream_cap, stream_used, ctr,
+                                      max_lines, s));
                 ++ws.launches;
             }
             GM_CUDA(record(ws.ev[1]));

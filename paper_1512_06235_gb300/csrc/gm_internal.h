@@ -132,7 +132,7 @@ cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const i
 cudaError_t launch_stream(const ImageDev *imgs, const PairDev *pairs, const int64_t *item_off, int32_t n_pairs,
                           const int32_t *qorder, int64_t item_begin, int64_t item_end, GroupDesc *gdesc, int32_t *grows,
                           int32_t *stream, int64_t capacity, unsigned long long *used, BatchCounters *ctr,
-                          cudaStream_t st);
+                          int32_t max_lines, cudaStream_t st);
 int match_tc_blocks_per_sm();
 int match_tc_max_grid_lines();
 

@@ -37,10 +37,13 @@ __global__ void __launch_bounds__(kWarps * 32) stream_kernel(
     const ImageDev *__restrict__ imgs, const PairDev *__restrict__ pairs, const int64_t *__restrict__ item_off,
     int32_t n_pairs, const int32_t *__restrict__ qorder, int64_t item_begin, int64_t item_end,
     GroupDesc *__restrict__ gdesc, int32_t *__restrict__ grows, int32_t *__restrict__ stream, int64_t capacity,
-    unsigned long long *__restrict__ used, BatchCounters *__restrict__ ctr)
+    unsigned long long *__restrict__ used, BatchCounters *__restrict__ ctr, int32_t max_lines)
 {
-    __shared__ int32_t run_start[kWarps][kMaxLines];
-    __shared__ int32_t run_excl[kWarps][kMaxLines + 1];
+    // per warp: run starts [max_lines] and exclusive run offsets [max_lines + 1] (sized for the batch's images, so
+    // that small grids leave room for more resident blocks)
+    extern __shared__ int32_t runs_smem[];
+    int32_t *const run_start_w = runs_smem + (threadIdx.x >> 5) * (2 * max_lines + 1);
+    int32_t *const run_excl_w = run_start_w + max_lines;
     __shared__ int32_t wtotal[kWarps];
     __shared__ unsigned long long wbase[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -162,14 +165,14 @@ __global__ void __launch_bounds__(kWarps * 32) stream_kernel(
                         const int u = __shfl_up_sync(0xffffffffu, incl, s);
                         if (lane >= s) incl += u;
                     }
-                    if (kk < kMaxLines) {
-                        run_start[warp][kk] = st[t];
-                        run_excl[warp][kk] = carry + incl - en[t];
+                    if (kk < max_lines) {
+                        run_start_w[kk] = st[t];
+                        run_excl_w[kk] = carry + incl - en[t];
                     }
                     carry += __shfl_sync(0xffffffffu, incl, 31);
                 }
             }
-            if (lane == 0) run_excl[warp][nlines] = carry;
+            if (lane == 0) run_excl_w[nlines] = carry;
             total = carry;
         }
     }
@@ -223,8 +226,8 @@ __global__ void __launch_bounds__(kWarps * 32) stream_kernel(
     const ImageDev &B = *Bp;
     const int nlines = colwise ? B.gx : B.gy;
     for (int kk = lane; kk < nlines; kk += 32) {
-        const int e0 = run_excl[warp][kk], len = run_excl[warp][kk + 1] - e0;
-        const int st = run_start[warp][kk];
+        const int e0 = run_excl_w[kk], len = run_excl_w[kk + 1] - e0;
+        const int st = run_start_w[kk];
         int32_t *dst = stream + off + e0;
         for (int k = 0; k < len; ++k) dst[k] = colwise ? st + k : B.idx_r[st + k];
     }
@@ -235,12 +238,18 @@ __global__ void __launch_bounds__(kWarps * 32) stream_kernel(
 cudaError_t launch_stream(const ImageDev *imgs, const PairDev *pairs, const int64_t *item_off, int32_t n_pairs,
                           const int32_t *qorder, int64_t item_begin, int64_t item_end, GroupDesc *gdesc, int32_t *grows,
                           int32_t *stream, int64_t capacity, unsigned long long *used, BatchCounters *ctr,
-                          cudaStream_t st)
+                          int32_t max_lines, cudaStream_t st)
 {
     const int64_t n = item_end - item_begin;
     if (n <= 0) return cudaSuccess;
-    stream_kernel<<<(unsigned)((n + kWarps - 1) / kWarps), kWarps * 32, 0, st>>>(
-        imgs, pairs, item_off, n_pairs, qorder, item_begin, item_end, gdesc, grows, stream, capacity, used, ctr);
+    if (max_lines < 1 || max_lines > kMaxLines) return cudaErrorInvalidValue;
+    static const cudaError_t attr = cudaFuncSetAttribute(stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)(sizeof(int32_t) * kWarps * (2 * kMaxLines + 1)));
+    if (attr != cudaSuccess) return attr;
+    const size_t smem = sizeof(int32_t) * kWarps * (2 * (size_t)max_lines + 1);
+    stream_kernel<<<(unsigned)((n + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
+        imgs, pairs, item_off, n_pairs, qorder, item_begin, item_end, gdesc, grows, stream, capacity, used, ctr,
+        max_lines);
     return cudaGetLastError();
 }
 
