@@ -303,6 +303,29 @@ def test_images_put_batch_equals_single_puts(gm, facade_scene):
                 np.testing.assert_array_equal(got[k], ref[k], err_msg=f"after rejected batch, pair {k}")
 
 
+def test_street_uneven_batch_sampled(gm):
+    """Uneven batch (street geometry, 2k-20k keypoints per image, d in [2, 8] per pair) in one call with graph
+    replay and the autotuned setting: every 10th pair exactly as the oracle, all paths equal over the batch."""
+    sc = scenes.street(n_images=120, n_points=150_000, n_pairs=400)
+    with gm.Context(device=0) as ctx:
+        ctx.put_images({k: im for k, im in enumerate(sc.images)})
+        ctx.set_option(gm.GM_OPT_GRAPH, 1)
+        ctx.autotune(sc.pairs, repeats=1)
+        for _ in range(3):   # direct run, capture, replay
+            off, m = ctx.match_pairs(sc.pairs)
+        rows = gm.split_matches(off, m)
+        st = ctx.stats()
+    sample = list(range(0, len(sc.pairs), 10))
+    wants = oracle.match_batch(sc.images, [sc.pairs[k] for k in sample])[0]
+    for k, mj in zip(sample, wants):
+        np.testing.assert_array_equal(rows[k], oracle.matches_from_match_j(mj), err_msg=f"pair {k}")
+    for name, path, group in PATHS:
+        rows2, st2 = _gpu_rows(gm, sc, path=path, group=group)
+        assert st2["n_candidates"] == st["n_candidates"], name
+        for k in range(len(sc.pairs)):
+            np.testing.assert_array_equal(rows2[k], rows[k], err_msg=f"{name} pair {k}")
+
+
 def test_stream_buffer_overflow_reruns(gm, facade_scene):
     """A candidate-stream buffer far too small for the batch forces the grow-and-rerun path; results unchanged."""
     sc = facade_scene
