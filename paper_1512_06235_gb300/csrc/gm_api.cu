@@ -495,7 +495,8 @@ gm_status gm_destroy(gm_ctx *ctx)
     }
     ctx->images.clear();
     workspace_free(ctx, ctx->ws);
-    for (DevBuf *b : {&ctx->d_imgs, &ctx->d_maps, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap, &ctx->d_tune})
+    for (DevBuf *b : {&ctx->d_imgs, &ctx->d_maps, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap, &ctx->d_tune,
+                      &ctx->d_btab})
         free_dev(ctx, *b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -625,6 +626,81 @@ gm_status grow_table(gm_ctx *ctx, DevBuf &t, size_t need, size_t min_bytes, cuda
     return GM_OK;
 }
 
+// Runs the batched counting sort over images [k0, k1): with `build` false only the counts and the per-image
+// out-of-image keypoint counts (bad + k0 ...), with `build` true the whole sort into the images' blocks.  Images
+// are taken in sub-batches so that the shared work arrays stay bounded.
+gm_status bucket_batches(gm_ctx *ctx, int32_t count, const gm_image *imgs, const std::vector<ImageLayout> &L,
+                         const std::vector<const float2 *> &raw_xy, const std::vector<const uint8_t *> &raw_desc,
+                         const std::vector<ImageDev> *dev, unsigned long long *d_bad, cudaStream_t s)
+{
+    constexpr int64_t kMaxS = int64_t(1) << 24;   // count entries per sub-batch
+    constexpr int32_t kMaxK = 4096;
+    int32_t k0 = 0;
+    while (k0 < count) {
+        int32_t k1 = k0;
+        int64_t S = 0;
+        while (k1 < count && k1 - k0 < kMaxK && (k1 == k0 || S + 2 * (L[k1].m + 2) <= kMaxS)) {
+            S += 2 * (L[k1].m + 2);
+            ++k1;
+        }
+        const int32_t K = k1 - k0;
+        // host table: jobs, kp_prefix, cnt_prefix, rec_prefix
+        const size_t jobs_b = align_up(sizeof(BucketJob) * K, 256), pre_b = align_up(sizeof(int64_t) * (K + 1), 256);
+        std::vector<char> tab(jobs_b + 3 * pre_b);
+        BucketJob *J = reinterpret_cast<BucketJob *>(tab.data());
+        int64_t *kp = reinterpret_cast<int64_t *>(tab.data() + jobs_b);
+        int64_t *cp = reinterpret_cast<int64_t *>(tab.data() + jobs_b + pre_b);
+        int64_t *rp = reinterpret_cast<int64_t *>(tab.data() + jobs_b + 2 * pre_b);
+        int64_t nk = 0, ck = 0;
+        for (int32_t k = 0; k < K; ++k) {
+            const gm_image &g = imgs[k0 + k];
+            const ImageLayout &l = L[k0 + k];
+            BucketJob j{};
+            j.xy_raw = raw_xy[k0 + k];
+            j.desc_raw = raw_desc[k0 + k];
+            j.n = g.n; j.width = g.width; j.height = g.height; j.cell_shift = l.sh; j.gx = l.gx; j.gy = l.gy;
+            j.m = (int32_t)(l.m + 1);   // the cells and the out-of-image cell
+            j.kp_base = nk;
+            j.cnt_base = ck;
+            if (dev) {
+                const ImageDev &d = (*dev)[k0 + k];
+                j.xy = const_cast<float2 *>(d.xy); j.xy_r = const_cast<float2 *>(d.xy_r);
+                j.perm = const_cast<int32_t *>(d.perm); j.inv_perm = const_cast<int32_t *>(d.inv_perm);
+                j.norm = const_cast<int32_t *>(d.norm); j.norm256 = const_cast<int32_t *>(d.norm256);
+                j.col_off = const_cast<int32_t *>(d.col_off); j.row_off = const_cast<int32_t *>(d.row_off);
+                j.idx_r = const_cast<int32_t *>(d.idx_r); j.desc = const_cast<int8_t *>(d.desc);
+                j.desc_h = const_cast<uint16_t *>(d.desc_h); j.rec = const_cast<int4 *>(d.rec);
+            }
+            J[k] = j;
+            kp[k] = nk;
+            cp[k] = ck;
+            rp[k] = nk + k;
+            nk += g.n;
+            ck += 2 * ((int64_t)j.m + 1);
+        }
+        kp[K] = nk;
+        cp[K] = ck;
+        rp[K] = nk + K;
+        gm_status st;
+        if ((st = ensure_dev(ctx, ctx->d_btab, tab.size())) != GM_OK) return st;
+        const size_t work_ints = (size_t)ck + (size_t)ck + 1 + (size_t)ck / 1024 + 8;
+        if ((st = ensure_dev(ctx, ctx->d_work, sizeof(int32_t) * work_ints)) != GM_OK) return st;
+        GM_CUDA(cudaMemcpyAsync(ctx->d_btab.p, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
+        char *dt = static_cast<char *>(ctx->d_btab.p);
+        const BucketJob *dJ = reinterpret_cast<const BucketJob *>(dt);
+        const int64_t *dkp = reinterpret_cast<const int64_t *>(dt + jobs_b);
+        const int64_t *dcp = reinterpret_cast<const int64_t *>(dt + jobs_b + pre_b);
+        const int64_t *drp = reinterpret_cast<const int64_t *>(dt + jobs_b + 2 * pre_b);
+        int32_t *work = static_cast<int32_t *>(ctx->d_work.p);
+        GM_CUDA(launch_bucket_batch_count(dJ, dkp, K, nk, work, ck, d_bad + k0, s));
+        if (dev) GM_CUDA(launch_bucket_batch_build(dJ, dkp, dcp, drp, K, nk, work, ck, work + ck, work + 2 * ck + 1, s));
+        // the table is read by the kernels above: the next sub-batch may overwrite it only after them
+        if (k1 < count) GM_CUDA(cudaStreamSynchronize(s));
+        k0 = k1;
+    }
+    return GM_OK;
+}
+
 // Registers `count` images (App. A Step 1).  All inputs are validated before anything registered changes; the
 // device work of all images is enqueued back to back with two stream synchronisations in total (after the
 // keypoint check, and at the end).
@@ -645,13 +721,12 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     GM_CUDA(cudaSetDevice(ctx->device));
     std::vector<ImageLayout> L(count);
-    size_t stage_bytes = 0, work_ints = 0, new_bytes = 0, replaced = 0;
+    size_t stage_bytes = 0, new_bytes = 0, replaced = 0;
     for (int32_t k = 0; k < count; ++k) {
         const gm_image &g = imgs[k];
         L[k] = image_layout(ctx, g.width, g.height, g.n);
         if (L[k].m + 2 > INT32_MAX / 4) return fail(GM_ERR_INVALID, "%s: grid too large (image %d)", fn, g.image_id);
         if (!on_device) stage_bytes += align_up(8 * (size_t)g.n + 1, 256) + align_up(128 * (size_t)g.n + 1, 256);
-        work_ints = std::max(work_ints, 2 * (size_t)(L[k].m + 3) + 2 * (size_t)(L[k].m / 1024 + 3));
         auto it = ctx->images.find(g.image_id);
         const bool reuse = it != ctx->images.end() && it->second->bytes >= L[k].tot;
         if (!reuse) {
@@ -682,13 +757,9 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             sp += xy_al + align_up(128 * N + 1, 256);
         }
     }
-    if ((st = ensure_dev(ctx, ctx->d_work, sizeof(int32_t) * work_ints)) != GM_OK) return st;
     if ((st = ensure_dev(ctx, ctx->d_bad, sizeof(unsigned long long) * (size_t)count)) != GM_OK) return st;
     unsigned long long *d_bad = static_cast<unsigned long long *>(ctx->d_bad.p);
-    int32_t *work = static_cast<int32_t *>(ctx->d_work.p);
-    for (int32_t k = 0; k < count; ++k)
-        GM_CUDA(launch_bucket_count(raw_xy[k], imgs[k].n, imgs[k].width, imgs[k].height, L[k].sh, L[k].gx, L[k].gy, work,
-                                    d_bad + k, s));
+    if ((st = bucket_batches(ctx, count, imgs, L, raw_xy, raw_desc, nullptr, d_bad, s)) != GM_OK) return st;
     std::vector<unsigned long long> bad(count);
     GM_CUDA(cudaMemcpyAsync(bad.data(), d_bad, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, s));
     GM_CUDA(cudaStreamSynchronize(s));
@@ -713,32 +784,20 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             fresh[k] = 1;
         }
     }
-    // 3. bin every image into its block (the count arrays are recomputed: the shared work buffer holds one image)
+    // 3. bin every image into its block (the counts are recomputed: the work arrays hold one sub-batch)
     std::vector<ImageDev> dev(count);
+    for (int32_t k = 0; k < count; ++k) dev[k] = image_dev(L[k], block[k], imgs[k].width, imgs[k].height, imgs[k].n);
+    st = bucket_batches(ctx, count, imgs, L, raw_xy, raw_desc, &dev, d_bad, s);
     cudaError_t e = cudaSuccess;
-    for (int32_t k = 0; k < count && e == cudaSuccess; ++k) {
-        const gm_image &g = imgs[k];
-        const ImageLayout &l = L[k];
-        dev[k] = image_dev(l, block[k], g.width, g.height, g.n);
-        const ImageDev &d = dev[k];
-        e = launch_bucket_count(raw_xy[k], g.n, g.width, g.height, l.sh, l.gx, l.gy, work, d_bad + k, s);
-        if (e == cudaSuccess)
-            e = launch_bucket_build(raw_xy[k], raw_desc[k], g.n, g.width, g.height, l.sh, l.gx, l.gy,
-                                    const_cast<float2 *>(d.xy), const_cast<int32_t *>(d.perm),
-                                    const_cast<int32_t *>(d.inv_perm), const_cast<int8_t *>(d.desc),
-                                    const_cast<int32_t *>(d.norm), const_cast<int32_t *>(d.norm256),
-                                    const_cast<int32_t *>(d.col_off), const_cast<float2 *>(d.xy_r),
-                                    const_cast<int32_t *>(d.idx_r), const_cast<int32_t *>(d.row_off),
-                                    const_cast<uint16_t *>(d.desc_h), const_cast<int4 *>(d.rec), work, s);
-        if (e == cudaSuccess && g.n > 0 && g.scale)
-            e = cudaMemcpyAsync(static_cast<char *>(block[k]) + l.offs[10], g.scale, 4 * (size_t)g.n,
+    for (int32_t k = 0; k < count && st == GM_OK && e == cudaSuccess; ++k)
+        if (imgs[k].n > 0 && imgs[k].scale)
+            e = cudaMemcpyAsync(static_cast<char *>(block[k]) + L[k].offs[10], imgs[k].scale, 4 * (size_t)imgs[k].n,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
-    }
-    if (e != cudaSuccess) {
+    if (st != GM_OK || e != cudaSuccess) {
         cudaStreamSynchronize(s);
         for (int32_t k = 0; k < count; ++k)
             if (fresh[k]) cudaFree(block[k]);
-        return fail(GM_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+        return st != GM_OK ? st : fail(GM_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     }
     // 4. install: replace or take a free slot; TMA descriptors of each image (tcgen05 path)
     for (int32_t k = 0; k < count; ++k) {

@@ -1,7 +1,9 @@
-// gm_bucket.cu -- grid bucketing of one image (App. A Step 1: cell index per feature, sort by cell, prefix scan
-// of the cell counts gives each cell's start).  Done once per image; the result stays resident.
+// gm_bucket.cu -- grid bucketing of images (App. A Step 1: cell index per feature, sort by cell, prefix scan of the
+// cell counts gives each cell's start).  Done once per image; the result stays resident.  Every launch covers all
+// images of a registration batch (each thread finds its image in a prefix table).
 //
-// A counting sort: histogram (atomics) -> exclusive scan (block-parallel, two passes) -> scatter (one thread per
+// A counting sort: histogram (atomics) -> exclusive scan (block-parallel, two passes, over the count arrays of all
+// images at once; each image's offsets are its segment minus the segment start) -> scatter (one thread per
 // keypoint, atomic cursor per cell).  The order inside a cell is whatever the atomics give: no result depends on
 // it (every band decision is per keypoint, and an accepted match has a unique nearest neighbour because ties are
 // rejected).  Two layouts are built: column-major (cells of a grid column contiguous) and row-major.  Descriptors
@@ -30,18 +32,6 @@ __device__ __forceinline__ bool cell_of(float2 p, float W, float H, float inv_cs
     ccol = cx * gy + cy;
     crow = cy * gx + cx;
     return true;
-}
-
-__global__ void bucket_count_kernel(const float2 *__restrict__ xy, int32_t n, float W, float H, float inv_cs,
-                                    int gx, int gy, int32_t *cnt_col, int32_t *cnt_row,
-                                    unsigned long long *bad)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int ccol, crow;
-    if (!cell_of(xy[i], W, H, inv_cs, gx, gy, ccol, crow)) atomicAdd(bad, 1ull);
-    atomicAdd(&cnt_col[ccol], 1);
-    atomicAdd(&cnt_row[crow], 1);
 }
 
 constexpr int kScanBlock = 1024;
@@ -109,128 +99,153 @@ cudaError_t exclusive_scan(const int32_t *cnt, int32_t m, int32_t *off, int32_t 
     return cudaGetLastError();
 }
 
-// Column-major scatter: one thread per keypoint (cur: per-cell cursors, initialised to the offsets).
-__global__ void scatter_col_kernel(const float2 *__restrict__ xy_raw, int32_t n, float W, float H, float inv_cs,
-                                   int gx, int gy, int32_t *__restrict__ cur, float2 *__restrict__ xy,
-                                   int32_t *__restrict__ perm, int32_t *__restrict__ inv_perm)
+__device__ __forceinline__ int find_job(const int64_t *__restrict__ prefix, int K, int64_t g)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float2 p = xy_raw[i];
-    int ccol, crow;
-    cell_of(p, W, H, inv_cs, gx, gy, ccol, crow);
-    const int pos = atomicAdd(&cur[ccol], 1);
-    perm[pos] = i;
-    xy[pos] = p;
-    inv_perm[i] = pos;
+    int lo = 0, hi = K;   // largest k with prefix[k] <= g
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
-// Row-major scatter (after the column-major one: idx_r holds column-major positions).
-__global__ void scatter_row_kernel(const float2 *__restrict__ xy_raw, int32_t n, float W, float H, float inv_cs,
-                                   int gx, int gy, int32_t *__restrict__ cur, const int32_t *__restrict__ inv_perm,
-                                   float2 *__restrict__ xy_r, int32_t *__restrict__ idx_r)
+__global__ void batch_count_kernel(const BucketJob *__restrict__ jobs, const int64_t *__restrict__ kp_prefix, int K,
+                                   int64_t n_total, int32_t *work, unsigned long long *bad)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float2 p = xy_raw[i];
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_total) return;
+    const int k = find_job(kp_prefix, K, g);
+    const BucketJob &J = jobs[k];
     int ccol, crow;
-    cell_of(p, W, H, inv_cs, gx, gy, ccol, crow);
-    const int pos = atomicAdd(&cur[crow], 1);
-    xy_r[pos] = p;
-    idx_r[pos] = inv_perm[i];
+    if (!cell_of(J.xy_raw[g - J.kp_base], (float)J.width, (float)J.height, 1.0f / (float)(1 << J.cell_shift), J.gx,
+                 J.gy, ccol, crow))
+        atomicAdd(&bad[k], 1ull);
+    int32_t *cnt = work + J.cnt_base;
+    atomicAdd(&cnt[ccol], 1);
+    atomicAdd(&cnt[J.m + 1 + crow], 1);
 }
 
-// One warp per sorted row: recentred int8 copy, squared norm and fp16 copy of the descriptor.
-__global__ void desc_permute_kernel(const uint8_t *__restrict__ desc_raw, const int32_t *__restrict__ perm,
-                                    int32_t n, int8_t *__restrict__ desc, int32_t *__restrict__ norm,
-                                    int32_t *__restrict__ norm256, uint16_t *__restrict__ desc_h)
+// scan holds the exclusive scan of the whole work array; each image's offsets are its segment minus the
+// segment's first value, written to the image's col_off / row_off and (for the cells) back into work as cursors.
+__global__ void batch_offsets_kernel(const BucketJob *__restrict__ jobs, const int64_t *__restrict__ cnt_prefix,
+                                     int K, int64_t S, const int32_t *__restrict__ scan, int32_t *work)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S) return;
+    const int k = find_job(cnt_prefix, K, p);
+    const BucketJob &J = jobs[k];
+    const int64_t q = p - J.cnt_base;
+    const bool row = q > J.m;
+    const int c = (int)(row ? q - (J.m + 1) : q);
+    const int64_t seg = J.cnt_base + (row ? J.m + 1 : 0);
+    const int32_t v = scan[p] - scan[seg];
+    (row ? J.row_off : J.col_off)[c] = v;
+    if (c < J.m) work[p] = v;
+}
+
+__global__ void batch_scatter_kernel(const BucketJob *__restrict__ jobs, const int64_t *__restrict__ kp_prefix, int K,
+                                     int64_t n_total, int32_t *work, bool row_pass)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_total) return;
+    const int k = find_job(kp_prefix, K, g);
+    const BucketJob &J = jobs[k];
+    const int i = (int)(g - J.kp_base);
+    const float2 p = J.xy_raw[i];
+    int ccol, crow;
+    cell_of(p, (float)J.width, (float)J.height, 1.0f / (float)(1 << J.cell_shift), J.gx, J.gy, ccol, crow);
+    int32_t *cur = work + J.cnt_base;
+    if (!row_pass) {
+        const int pos = atomicAdd(&cur[ccol], 1);
+        J.perm[pos] = i;
+        J.xy[pos] = p;
+        J.inv_perm[i] = pos;
+    } else {
+        const int pos = atomicAdd(&cur[J.m + 1 + crow], 1);
+        J.xy_r[pos] = p;
+        J.idx_r[pos] = J.inv_perm[i];
+    }
+}
+
+__global__ void batch_desc_kernel(const BucketJob *__restrict__ jobs, const int64_t *__restrict__ kp_prefix, int K,
+                                  int64_t n_total)
+{
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= n) return;
-    const int src = perm[warp];
-    const uint32_t w = reinterpret_cast<const uint32_t *>(desc_raw + (int64_t)src * kDim)[lane] ^ 0x80808080u;
-    reinterpret_cast<uint32_t *>(desc + (int64_t)warp * kDim)[lane] = w;
+    if (g >= n_total) return;
+    const int k = find_job(kp_prefix, K, g);
+    const BucketJob &J = jobs[k];
+    const int row = (int)(g - J.kp_base);
+    const int src = J.perm[row];
+    const uint32_t w = reinterpret_cast<const uint32_t *>(J.desc_raw + (int64_t)src * kDim)[lane] ^ 0x80808080u;
+    reinterpret_cast<uint32_t *>(J.desc + (int64_t)row * kDim)[lane] = w;
     int sq = 0;
     uint32_t h01 = 0, h23 = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int v = (int)(int8_t)((w >> (8 * k)) & 0xffu);
+    for (int t = 0; t < 4; ++t) {
+        const int v = (int)(int8_t)((w >> (8 * t)) & 0xffu);
         sq += v * v;
         const uint16_t hb = __half_as_ushort(__int2half_rn(v));
-        if (k < 2) h01 |= (uint32_t)hb << (16 * k);
-        else h23 |= (uint32_t)hb << (16 * (k - 2));
+        if (t < 2) h01 |= (uint32_t)hb << (16 * t);
+        else h23 |= (uint32_t)hb << (16 * (t - 2));
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
     if (lane == 0) {
-        norm[warp] = sq;
-        norm256[warp] = sq * 256;
+        J.norm[row] = sq;
+        J.norm256[row] = sq * 256;
     }
-    if (desc_h) reinterpret_cast<uint2 *>(desc_h + (int64_t)warp * kDim)[lane] = make_uint2(h01, h23);
+    reinterpret_cast<uint2 *>(J.desc_h + (int64_t)row * kDim)[lane] = make_uint2(h01, h23);
 }
 
-// Point records for the tensor-core path: (x, y, |b'|^2 * 256, column-major position) in column-major order,
-// followed by a sentinel whose NaN coordinates fail every band test.
-__global__ void records_kernel(const float2 *__restrict__ xy, const int32_t *__restrict__ norm256, int32_t n,
-                               int4 *__restrict__ rec)
+// records of every image plus one sentinel each: index g over sum (n + 1), image k owns [kp_base + k, ...]
+__global__ void batch_records_kernel(const BucketJob *__restrict__ jobs, const int64_t *__restrict__ rec_prefix,
+                                     int K, int64_t n_rec)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > n) return;
-    if (i == n) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_rec) return;
+    const int k = find_job(rec_prefix, K, g);
+    const BucketJob &J = jobs[k];
+    const int i = (int)(g - (J.kp_base + k));
+    if (i == J.n) {
         const int nan = 0x7fc00000;
-        rec[n] = make_int4(nan, nan, 0, 0);
+        J.rec[i] = make_int4(nan, nan, 0, 0);
         return;
     }
-    const float2 p = xy[i];
-    rec[i] = make_int4(__float_as_int(p.x), __float_as_int(p.y), norm256[i], i);
+    const float2 p = J.xy[i];
+    J.rec[i] = make_int4(__float_as_int(p.x), __float_as_int(p.y), J.norm256[i], i);
 }
+
+unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 }  // namespace
 
-cudaError_t launch_bucket_count(const float2 *xy_raw, int32_t n, int32_t width, int32_t height, int32_t cell_shift,
-                                int32_t gx, int32_t gy, int32_t *work, unsigned long long *bad, cudaStream_t st)
+cudaError_t launch_bucket_batch_count(const BucketJob *jobs, const int64_t *kp_prefix, int32_t K, int64_t n_total,
+                                      int32_t *work, int64_t S, unsigned long long *bad, cudaStream_t st)
 {
-    // work: two count arrays of gx*gy + 2 entries (the cells, the out-of-image cell, a spare)
-    const int m = gx * gy + 1;
-    const float inv_cs = 1.0f / (float)(1 << cell_shift);
-    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int32_t) * 2 * (m + 1), st);
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int32_t) * (size_t)S, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long) * (size_t)K, st);
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    if (n > 0)
-        bucket_count_kernel<<<(n + 255) / 256, 256, 0, st>>>(xy_raw, n, (float)width, (float)height, inv_cs, gx, gy,
-                                                             work, work + (m + 1), bad);
+    if (n_total > 0) batch_count_kernel<<<blocks_for(n_total, 256), 256, 0, st>>>(jobs, kp_prefix, K, n_total, work, bad);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_build(const float2 *xy_raw, const uint8_t *desc_raw, int32_t n, int32_t width,
-                                int32_t height, int32_t cell_shift, int32_t gx, int32_t gy, float2 *xy, int32_t *perm,
-                                int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *norm256, int32_t *col_off,
-                                float2 *xy_r, int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int4 *rec,
-                                int32_t *work, cudaStream_t st)
+cudaError_t launch_bucket_batch_build(const BucketJob *jobs, const int64_t *kp_prefix, const int64_t *cnt_prefix,
+                                      const int64_t *rec_prefix, int32_t K, int64_t n_total, int32_t *work, int64_t S,
+                                      int32_t *scan, int32_t *bsum, cudaStream_t st)
 {
-    // col_off / row_off hold gx*gy + 2 entries: the cells, the out-of-image cell, the total
-    const int m = gx * gy + 1;
-    const float inv_cs = 1.0f / (float)(1 << cell_shift);
-    int32_t *cnt_col = work, *cnt_row = work + (m + 1), *bsum = work + 2 * (m + 1);
-    cudaError_t e;
-    if ((e = exclusive_scan(cnt_col, m, col_off, bsum, st)) != cudaSuccess) return e;
-    if ((e = exclusive_scan(cnt_row, m, row_off, bsum + (m + kScanBlock - 1) / kScanBlock, st)) != cudaSuccess)
-        return e;
-    // cursors start at the offsets (reuse the count arrays)
-    if ((e = cudaMemcpyAsync(cnt_col, col_off, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-        return e;
-    if ((e = cudaMemcpyAsync(cnt_row, row_off, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-        return e;
-    if (n > 0) {
-        const int nb = (n + 255) / 256;
-        scatter_col_kernel<<<nb, 256, 0, st>>>(xy_raw, n, (float)width, (float)height, inv_cs, gx, gy, cnt_col, xy,
-                                               perm, inv_perm);
-        scatter_row_kernel<<<nb, 256, 0, st>>>(xy_raw, n, (float)width, (float)height, inv_cs, gx, gy, cnt_row,
-                                               inv_perm, xy_r, idx_r);
-        desc_permute_kernel<<<(n + 7) / 8, 256, 0, st>>>(desc_raw, perm, n, desc, norm, norm256, desc_h);
+    if (S > INT32_MAX - 1) return cudaErrorInvalidValue;
+    cudaError_t e = exclusive_scan(work, (int32_t)S, scan, bsum, st);
+    if (e != cudaSuccess) return e;
+    batch_offsets_kernel<<<blocks_for(S, 256), 256, 0, st>>>(jobs, cnt_prefix, K, S, scan, work);
+    if (n_total > 0) {
+        batch_scatter_kernel<<<blocks_for(n_total, 256), 256, 0, st>>>(jobs, kp_prefix, K, n_total, work, false);
+        batch_scatter_kernel<<<blocks_for(n_total, 256), 256, 0, st>>>(jobs, kp_prefix, K, n_total, work, true);
+        batch_desc_kernel<<<blocks_for(n_total * 32, 256), 256, 0, st>>>(jobs, kp_prefix, K, n_total);
     }
-    records_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(xy, norm256, n, rec);
+    // the record index space has one extra entry (the sentinel) per image: rec_prefix[k] = kp_prefix[k] + k
+    batch_records_kernel<<<blocks_for(n_total + K, 256), 256, 0, st>>>(jobs, rec_prefix, K, n_total + K);
     return cudaGetLastError();
 }
 

@@ -88,17 +88,35 @@ struct alignas(16) GroupDesc {
 constexpr int kTcQueriesPerItem = 128;
 
 // ---- launchers (host functions defined in the .cu files) ---------------------------------------------------
-// Image registration (two phases, so that invalid input never touches the destination): the count phase
-// histograms the cells and counts keypoints outside [0,W) x [0,H) into *bad; the build phase (only after *bad
-// was read as 0) scans, scatters and copies the descriptors.  work: int32 scratch of 2*(gx*gy + 2) + 2*(gx*gy/1024
-// + 2) entries, carried from the first phase to the second.  All pointers are device pointers.
-cudaError_t launch_bucket_count(const float2 *xy_raw, int32_t n, int32_t width, int32_t height, int32_t cell_shift,
-                                int32_t gx, int32_t gy, int32_t *work, unsigned long long *bad, cudaStream_t st);
-cudaError_t launch_bucket_build(const float2 *xy_raw, const uint8_t *desc_raw, int32_t n, int32_t width,
-                                int32_t height, int32_t cell_shift, int32_t gx, int32_t gy, float2 *xy, int32_t *perm,
-                                int32_t *inv_perm, int8_t *desc, int32_t *norm, int32_t *norm256, int32_t *col_off,
-                                float2 *xy_r, int32_t *idx_r, int32_t *row_off, uint16_t *desc_h, int4 *rec,
-                                int32_t *work, cudaStream_t st);
+// Image registration, many images per launch, in two phases so that invalid input never touches a destination:
+// the count phase histograms the cells and counts keypoints outside [0,W) x [0,H) per image; the build phase
+// (only after every count was read as 0) scans, scatters and copies the descriptors.  Keypoint g of the batch
+// belongs to image k with kp_base[k] <= g < kp_base[k+1]; the image's two count arrays (column-major then
+// row-major, m + 1 entries each, m = gx * gy + 1) sit at cnt_base in the shared work array.  All pointers are
+// device pointers.
+struct BucketJob {
+    const float2 *xy_raw;
+    const uint8_t *desc_raw;
+    int32_t n, width, height, cell_shift, gx, gy, m;
+    int32_t pad_;
+    int64_t kp_base, cnt_base;
+    float2 *xy, *xy_r;
+    int32_t *perm, *inv_perm, *norm, *norm256, *col_off, *idx_r, *row_off;
+    int8_t *desc;
+    uint16_t *desc_h;
+    int4 *rec;
+};
+
+// Counts of every image of the batch (work[0, S) and bad[0, K) are cleared first); bad[k] counts image k's
+// keypoints outside its image.  kp_prefix[K + 1] and cnt_prefix[K + 1] are the jobs' kp_base / cnt_base with the
+// totals at [K].
+cudaError_t launch_bucket_batch_count(const BucketJob *jobs, const int64_t *kp_prefix, int32_t K, int64_t n_total,
+                                      int32_t *work, int64_t S, unsigned long long *bad, cudaStream_t st);
+// Offsets, scatters, descriptor copies and records of every image (after launch_bucket_batch_count); scan needs
+// S + 1 entries and bsum S / 1024 + 2; rec_prefix[k] = kp_prefix[k] + k (each image's records end with a sentinel).
+cudaError_t launch_bucket_batch_build(const BucketJob *jobs, const int64_t *kp_prefix, const int64_t *cnt_prefix,
+                                      const int64_t *rec_prefix, int32_t K, int64_t n_total, int32_t *work, int64_t S,
+                                      int32_t *scan, int32_t *bsum, cudaStream_t st);
 
 // Query ordering (App. A Step 2 as an order only): per pair, sorts A's queries by the position of their
 // epipolar line in B.  qorder[qoff + k] = column-major position in A of the k-th query.
