@@ -208,8 +208,7 @@ def run_street(args, gm, dev, local, peaks, peak_kind):
     sc = scenes.street()
     stream = __import__("torch").cuda.current_stream(dev)
     ctx = gm.Context(device=local, stream=stream)
-    for k, im in enumerate(sc.images):
-        ctx.put_image(k, im)
+    ctx.put_images({k: im for k, im in enumerate(sc.images)})
     gp = [gm.make_pair(p.a, p.b, p.F, p.d, p.p, p.q) for p in sc.pairs]
     cap = sum(sc.images[p.a].n for p in sc.pairs)
     tune = ctx.autotune(gp, repeats=1)
@@ -247,8 +246,7 @@ def run_dense(args, gm, dev, local, peaks, peak_kind):
     sc = scenes.street(n_kp=16000, n_pairs=30000)
     stream = __import__("torch").cuda.current_stream(dev)
     ctx = gm.Context(device=local, stream=stream)
-    for k, im in enumerate(sc.images):
-        ctx.put_image(k, im)
+    ctx.put_images({k: im for k, im in enumerate(sc.images)})
     ctx.set_option(gm.GM_OPT_GRAPH, 1)
     cap = sum(sc.images[p.a].n for p in sc.pairs)
     sweep = []
@@ -328,8 +326,7 @@ def run_serving(args, gm, dev, local):
            "config": {"workload": "facade_serving_100img_2k-20kp", "pairs": len(sc.pairs)}, "rates": []}
     stream = __import__("torch").cuda.current_stream(dev)
     ctx = gm.Context(device=local, stream=stream, mem_budget_bytes=40 << 30, max_inflight=2)
-    for k, im in enumerate(sc.images):
-        ctx.put_image(k, im)
+    ctx.put_images({k: im for k, im in enumerate(sc.images)})
     gp = [gm.make_pair(p.a, p.b, p.F, p.d, p.p, p.q) for p in sc.pairs]
     for r in (500, 1000, 2000, 5000):
         s = _serving(gm, ctx, gp, r, args.serve_seconds if args.serve_seconds > 0 else 3.0)
@@ -460,8 +457,7 @@ def main():
     if not args.no_graph:
         ctx.set_option(gm.GM_OPT_GRAPH, 1)
     # ---- device-resident measurement: images registered before the timed region
-    for k, im in enumerate(sc.images):
-        ctx.put_image(k, im)
+    ctx.put_images({k: im for k, im in enumerate(sc.images)})
     gp = [gm.make_pair(p.a, p.b, p.F, p.d, p.p, p.q) for p in pairs]
     cap = sum(sc.images[p.a].n for p in pairs)
     off_d = torch.empty(len(pairs) + 1, dtype=torch.int64, device=dev)
