@@ -159,6 +159,21 @@ GM_API gm_status gm_images_put(gm_ctx *ctx, int32_t count, const gm_image *image
 /* Drops image `image_id` from the context.  GM_ERR_NOT_FOUND if unknown. */
 GM_API gm_status gm_image_evict(gm_ctx *ctx, int32_t image_id);
 
+/* Candidate image pairs from point-camera co-visibility (Sec. 6.1): the pairs that gm_match_pairs then matches.
+ * For each query image q the candidates are the images i != q that see more than `threshold` of the points q sees
+ * (|Points(C_q) & Points(C_i)| > T); only the `top_k` of them with the most co-visible points are kept (ties: the
+ * lower image index first), and the result is the set of unique unordered pairs over all queries.
+ *   n_cams:     images 0 .. n_cams-1 (at most 16384; the co-visible counts are a dense n_cams^2 int32 matrix);
+ *   point_off:  int64 [n_points + 1], nondecreasing from 0; point p is seen by point_cams[point_off[p] ..
+ *               point_off[p+1]-1] (distinct cameras; GM_ERR_INVALID otherwise);
+ *   point_cams: int32 [point_off[n_points]];  both host or both device memory;
+ *   pairs:      int32 [cap][3] rows (a, b, count), a < b, sorted by (a, b); host or device;
+ *   *n_written: number of rows; if it exceeds cap, nothing is written and the call returns GM_ERR_NOMEM.
+ * threshold >= -1 (T = -1 admits every image), top_k >= 0. */
+GM_API gm_status gm_select_pairs(gm_ctx *ctx, int32_t n_cams, int64_t n_points, const int64_t *point_off,
+                                 const int32_t *point_cams, int32_t threshold, int32_t top_k, int32_t *pairs,
+                                 int64_t cap, int64_t *n_written);
+
 /* Autotuner (a tuning aid; the paper has no counterpart).  Times gm_match_pairs on this batch for every distance
  * path (tc; mma with 16- and 32-query groups; simt) and grid cell size (4, 8, 16 px), `repeats` timed runs each
  * after one warm-up, and leaves the fastest setting in the context: GM_OPT_PATH, GM_OPT_MMA_GROUP and

@@ -92,6 +92,7 @@ _SIGNATURES = {
     "gm_band_candidates_static": (c_i32, [c_p, ctypes.POINTER(GmPair), c_i32, c_i32, c_p, c_p, c_i64,
                                           ctypes.POINTER(c_i64)]),
     "gm_images_put": (c_i32, [c_p, c_i32, ctypes.POINTER(GmImage), c_i32]),
+    "gm_select_pairs": (c_i32, [c_p, c_i32, c_i64, c_p, c_p, c_i32, c_i32, c_p, c_i64, ctypes.POINTER(c_i64)]),
     "gm_autotune": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_i32, ctypes.POINTER(GmTuneResult)]),
     "gm_get_stats": (c_i32, [c_p, ctypes.POINTER(GmStats)]),
     "gm_submit": (c_i32, [c_p, ctypes.POINTER(GmPair), ctypes.POINTER(c_u64)]),
@@ -211,6 +212,23 @@ def gm_images_put(ctx, images):
         raise ValueError("gm_images_put: all arrays must be host memory or all device memory")
     _check(load_library().gm_images_put(ctx, len(images), arr, devs.pop() if devs else 0), ctx)
     del keep
+
+
+def gm_select_pairs(ctx, n_cams: int, point_off, point_cams, threshold: int, top_k: int, pairs, cap: int) -> int:
+    """point_off int64 [P+1], point_cams int32, pairs int32 [cap, 3]: numpy or torch CUDA tensors."""
+    po, _, k1 = _ptr(point_off)
+    pc, _, k2 = _ptr(point_cams)
+    pp, _, k3 = _ptr(pairs)
+    n = c_i64(0)
+    st = load_library().gm_select_pairs(ctx, n_cams, int(point_off.shape[0]) - 1, po, pc, threshold, top_k, pp, cap,
+                                        ctypes.byref(n))
+    if st == GM_ERR_NOMEM:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = n.value
+        raise err
+    _check(st, ctx)
+    del k1, k2, k3
+    return n.value
 
 
 def gm_image_evict(ctx, image_id: int):
@@ -401,6 +419,19 @@ class Context:
 
     def stats(self) -> dict:
         return gm_get_stats(self.h)
+
+    def select_pairs(self, n_cams: int, point_off, point_cams, threshold: int = 8, top_k: int = 1 << 30):
+        """Candidate pairs (Sec. 6.1) as int32 rows (a, b, count)."""
+        cap = 1024
+        while True:
+            out = np.empty((cap, 3), np.int32)
+            try:
+                n = gm_select_pairs(self.h, n_cams, point_off, point_cams, threshold, top_k, out, cap)
+                return out[:n]
+            except GeomatchError as e:
+                if e.status != GM_ERR_NOMEM:
+                    raise
+                cap = max(e.required, 1)
 
     def autotune(self, pairs, repeats: int = 3) -> dict:
         return gm_autotune(self.h, pairs, repeats)
