@@ -54,20 +54,3 @@ def select_pairs(n_cams: int, point_off, point_cams, threshold: int, top_k: int)
     for r, (a, b) in enumerate(rows):
         out[r] = (a, b, C[a, b])
     return out
-
-
-def visibility_from_scene(scene) -> tuple[np.ndarray, np.ndarray, int]:
-    """Point -> camera CSR of a synthetic scene: point p is seen by camera c iff one of c's keypoints projects p."""
-    n_cams = len(scene.images)
-    cams, pts = [], []
-    for c, im in enumerate(scene.images):
-        pid = np.unique(im.pid[im.pid >= 0])
-        cams.append(np.full(pid.size, c, np.int64))
-        pts.append(pid.astype(np.int64))
-    cams = np.concatenate(cams)
-    pts = np.concatenate(pts)
-    order = np.lexsort((cams, pts))
-    cams, pts = cams[order], pts[order]
-    uniq, start = np.unique(pts, return_index=True)
-    point_off = np.append(start, pts.size).astype(np.int64)
-    return point_off, cams.astype(np.int32), n_cams

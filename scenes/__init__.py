@@ -350,3 +350,22 @@ def _rot_x(deg: float) -> np.ndarray:
 
 RECTIFIED_F = np.array([0, 0, 0, 0, 0, -1, 0, 1, 0], np.float32)
 """F of a rectified pair (pure translation along x, equal intrinsics): l_B = (0, -1, y_A), i.e. y' = y."""
+
+
+def visibility(scene):
+    """Point -> camera CSR of a scene (the coarse model's point-camera visibility, Sec. 6.1): point p is seen by
+    camera c iff one of c's keypoints projects p.  Returns (point_off int64 [P+1], point_cams int32, n_cams); only
+    points seen by at least one camera are listed."""
+    n_cams = len(scene.images)
+    cams, pts = [], []
+    for c, im in enumerate(scene.images):
+        pid = np.unique(im.pid[im.pid >= 0])
+        cams.append(np.full(pid.size, c, np.int64))
+        pts.append(pid.astype(np.int64))
+    cams = np.concatenate(cams)
+    pts = np.concatenate(pts)
+    order = np.lexsort((cams, pts))
+    cams, pts = cams[order], pts[order]
+    _, start = np.unique(pts, return_index=True)
+    point_off = np.append(start, pts.size).astype(np.int64)
+    return point_off, cams.astype(np.int32), n_cams

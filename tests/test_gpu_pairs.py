@@ -39,7 +39,7 @@ def test_random_visibility(gm, n_cams, n_points, max_deg, T, k):
 
 @pytest.mark.parametrize("k", [3, 10, 1000])
 def test_facade_visibility(gm, facade_scene, k):
-    off, cams, n_cams = op.visibility_from_scene(facade_scene)
+    off, cams, n_cams = scenes.visibility(facade_scene)
     with gm.Context(device=0) as ctx:
         got = ctx.select_pairs(n_cams, off, cams, 8, k)
     np.testing.assert_array_equal(got, op.select_pairs(n_cams, off, cams, 8, k))
