@@ -174,6 +174,15 @@ GM_API gm_status gm_select_pairs(gm_ctx *ctx, int32_t n_cams, int64_t n_points, 
                                  const int32_t *point_cams, int32_t threshold, int32_t top_k, int32_t *pairs,
                                  int64_t cap, int64_t *n_written);
 
+/* Track merging (the step after pairwise matching, Sec. 6.2): tracks are the connected components of the matches.
+ * Nodes are features numbered 0 .. n_nodes-1 (e.g. image-major: node = first node of the image + feature index);
+ * every row of `edges` (int64 [n_edges][2]) is a match between two nodes.  labels (int64 [n_nodes]) receives for
+ * every node the smallest node index of its component; *n_tracks the number of components with at least two nodes.
+ * edges and labels may each be host or device memory.  Errors: GM_ERR_INVALID (an endpoint outside the nodes),
+ * GM_ERR_TIMEOUT (a bounded device loop ran out; not expected). */
+GM_API gm_status gm_merge_tracks(gm_ctx *ctx, int64_t n_nodes, int64_t n_edges, const int64_t *edges, int64_t *labels,
+                                 int64_t *n_tracks);
+
 /* Autotuner (a tuning aid; the paper has no counterpart).  Times gm_match_pairs on this batch for every distance
  * path (tc; mma with 16- and 32-query groups; simt) and grid cell size (4, 8, 16 px), `repeats` timed runs each
  * after one warm-up, and leaves the fastest setting in the context: GM_OPT_PATH, GM_OPT_MMA_GROUP and

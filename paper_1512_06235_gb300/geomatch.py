@@ -92,6 +92,7 @@ _SIGNATURES = {
     "gm_band_candidates_static": (c_i32, [c_p, ctypes.POINTER(GmPair), c_i32, c_i32, c_p, c_p, c_i64,
                                           ctypes.POINTER(c_i64)]),
     "gm_images_put": (c_i32, [c_p, c_i32, ctypes.POINTER(GmImage), c_i32]),
+    "gm_merge_tracks": (c_i32, [c_p, c_i64, c_i64, c_p, c_p, ctypes.POINTER(c_i64)]),
     "gm_select_pairs": (c_i32, [c_p, c_i32, c_i64, c_p, c_p, c_i32, c_i32, c_p, c_i64, ctypes.POINTER(c_i64)]),
     "gm_autotune": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_i32, ctypes.POINTER(GmTuneResult)]),
     "gm_get_stats": (c_i32, [c_p, ctypes.POINTER(GmStats)]),
@@ -229,6 +230,16 @@ def gm_select_pairs(ctx, n_cams: int, point_off, point_cams, threshold: int, top
     _check(st, ctx)
     del k1, k2, k3
     return n.value
+
+
+def gm_merge_tracks(ctx, n_nodes: int, edges, labels) -> int:
+    """edges int64 [m, 2], labels int64 [n_nodes] (numpy or torch CUDA); returns the number of tracks."""
+    pe, _, k1 = _ptr(edges)
+    pl, _, k2 = _ptr(labels)
+    nt = c_i64(0)
+    _check(load_library().gm_merge_tracks(ctx, n_nodes, int(edges.shape[0]), pe, pl, ctypes.byref(nt)), ctx)
+    del k1, k2
+    return nt.value
 
 
 def gm_image_evict(ctx, image_id: int):
@@ -432,6 +443,12 @@ class Context:
                 if e.status != GM_ERR_NOMEM:
                     raise
                 cap = max(e.required, 1)
+
+    def merge_tracks(self, n_nodes: int, edges):
+        """(labels int64 [n_nodes], number of tracks) of the match graph."""
+        labels = np.empty(n_nodes, np.int64)
+        nt = gm_merge_tracks(self.h, n_nodes, np.ascontiguousarray(edges, np.int64).reshape(-1, 2), labels)
+        return labels, nt
 
     def autotune(self, pairs, repeats: int = 3) -> dict:
         return gm_autotune(self.h, pairs, repeats)
