@@ -359,6 +359,57 @@ def run_pairs(args, gm, dev, local, peaks, peak_kind):
     print(json.dumps(line), flush=True)
 
 
+def run_tracks(args, gm, dev, local, peaks, peak_kind):
+    """Track merging of the facade batch's matches: connected components over the 800000 features of the 100
+    images, edges from the 1200 pairs' match lists (the step after matching)."""
+    import scenes
+    import torch
+    sc = scenes.facade()
+    stream = torch.cuda.current_stream(dev)
+    ctx = gm.Context(device=local, stream=stream)
+    ctx.put_images({k: im for k, im in enumerate(sc.images)})
+    off, m = ctx.match_pairs(sc.pairs)
+    base = np.concatenate([[0], np.cumsum([im.n for im in sc.images])]).astype(np.int64)
+    k = np.repeat(np.arange(len(sc.pairs)), np.diff(off))
+    a = np.array([p.a for p in sc.pairs], np.int64)[k]
+    b = np.array([p.b for p in sc.pairs], np.int64)[k]
+    edges = np.stack([base[a] + m[:, 0], base[b] + m[:, 1]], 1).astype(np.int64)
+    n_nodes = int(base[-1])
+    d_edges = torch.from_numpy(edges).to(dev)
+    lab = torch.empty(n_nodes, dtype=torch.int64, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        nt = gm.gm_merge_tracks(ctx.h, n_nodes, d_edges, lab)
+    torch.cuda.synchronize(dev)
+    steps = max(args.steps, 5)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for x, y in ev:
+        x.record(stream)
+        nt = gm.gm_merge_tracks(ctx.h, n_nodes, d_edges, lab)
+        y.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = float(np.mean([x.elapsed_time(y) for x, y in ev]))
+    ctx.close()
+    alg = 16.0 * len(edges) + 8.0 * n_nodes * 2
+    line = {"metric": "match edges merged/s", "value": len(edges) / (ms / 1e3), "unit": "edges/s", "n_gpus": 1,
+            "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (facade batch matches)",
+            "config": {"workload": "tracks_facade_100img_1200pairs", "nodes": n_nodes, "edges": int(len(edges)),
+                       "tracks": nt},
+            "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "link_kernel + label_kernel", "algorithmic_bytes": alg,
+                         "peak_source": f"{peak_kind} (STREAM-style copy)"}}
+    if not args.no_cpu_baseline:
+        from oracle import tracks as ot
+        t0 = time.perf_counter()
+        want = ot.labels(n_nodes, edges)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(edges) / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                "sample": f"the whole graph once ({dt:.2f} s)",
+                                "labels_equal": bool((lab.cpu().numpy() == want).all())}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args, gm, dev, local):
     """Serving: Poisson single-pair requests over the facade geometry with per-image keypoints log-uniform in
     [2000, 20000], at 500, 1000, 2000 and 5000 req/s, under a 40 GB device-memory budget."""
@@ -452,10 +503,10 @@ def main():
     ap.add_argument("--pairs", type=int, default=0, help="use only the first N pairs (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch every step directly (no CUDA graph replay)")
-    ap.add_argument("--workload", default="facade", choices=["facade", "two_view", "street", "dense", "serving", "pairs"],
+    ap.add_argument("--workload", default="facade", choices=["facade", "two_view", "street", "dense", "serving", "pairs", "tracks"],
                     help="facade: the headline batch; two_view: one pair; street: uneven autotuned batch; dense: "
                          "16000-keypoint band sweep; "
-                         "serving: Poisson requests; pairs: candidate pair selection")
+                         "serving: Poisson requests; pairs: candidate pair selection; tracks: track merging")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving leg: Poisson arrivals, req/s")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving leg duration (0: skip)")
     args = ap.parse_args()
@@ -489,6 +540,8 @@ def main():
             run_two_view(args, gm, dev, local)
         elif args.workload == "pairs":
             run_pairs(args, gm, dev, local, peaks, peak_kind)
+        elif args.workload == "tracks":
+            run_tracks(args, gm, dev, local, peaks, peak_kind)
         else:
             run_serving(args, gm, dev, local)
         return
