@@ -410,6 +410,77 @@ def run_tracks(args, gm, dev, local, peaks, peak_kind):
     print(json.dumps(line), flush=True)
 
 
+def run_triangulate(args, gm, dev, local, peaks, peak_kind):
+    """Triangulation of the facade batch's tracks (Sec. 6.2 end): the tracks of the 1200 pairs' matches over the
+    800000 features of the 100 images, one FP64 least-squares point per track, cameras P = K [R | t]."""
+    import scenes
+    import torch
+    sc = scenes.facade()
+    stream = torch.cuda.current_stream(dev)
+    ctx = gm.Context(device=local, stream=stream)
+    ctx.put_images({k: im for k, im in enumerate(sc.images)})
+    off, m = ctx.match_pairs(sc.pairs)
+    base = np.concatenate([[0], np.cumsum([im.n for im in sc.images])]).astype(np.int64)
+    k = np.repeat(np.arange(len(sc.pairs)), np.diff(off))
+    a = np.array([p.a for p in sc.pairs], np.int64)[k]
+    b = np.array([p.b for p in sc.pairs], np.int64)[k]
+    edges = np.stack([base[a] + m[:, 0], base[b] + m[:, 1]], 1).astype(np.int64)
+    n_nodes = int(base[-1])
+    lab = torch.empty(n_nodes, dtype=torch.int64, device=dev)
+    gm.gm_merge_tracks(ctx.h, n_nodes, torch.from_numpy(edges).to(dev), lab)
+    P = np.stack([c.K @ np.hstack([c.R, c.t.reshape(3, 1)]) for c in sc.cameras]).reshape(-1, 12)
+    d_P = torch.from_numpy(P).to(dev)
+    ids = np.arange(len(sc.images), dtype=np.int32)
+    X = torch.empty((n_nodes, 3), dtype=torch.float64, device=dev)
+    roots = torch.empty(n_nodes, dtype=torch.int64, device=dev)
+    nv = torch.empty(n_nodes, dtype=torch.int32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        nt = gm.gm_triangulate(ctx.h, ids, d_P, lab, X, roots, nv, n_nodes)
+    torch.cuda.synchronize(dev)
+    steps = max(args.steps, 5)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for x, y in ev:
+        x.record(stream)
+        nt = gm.gm_triangulate(ctx.h, ids, d_P, lab, X, roots, nv, n_nodes)
+        y.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = float(np.mean([x.elapsed_time(y) for x, y in ev]))
+    ctx.close()
+    # labels, coordinates and positions of every node; accumulators, point, root and view count of every track
+    alg = 20.0 * n_nodes + (72.0 + 24.0 + 8.0 + 4.0) * nt
+    n_obs = int(nv[:nt].sum().item())
+    line = {"metric": "tracks triangulated/s", "value": nt / (ms / 1e3), "unit": "tracks/s", "n_gpus": 1,
+            "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (facade batch tracks)",
+            "config": {"workload": "triangulate_facade_100img_1200pairs", "nodes": n_nodes, "tracks": nt,
+                       "observations": n_obs},
+            "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "tri_accum_kernel + tri_solve_kernel", "algorithmic_bytes": alg,
+                         "peak_source": f"{peak_kind} (STREAM-style copy)"}}
+    if not args.no_cpu_baseline:
+        from oracle import triangulate as otri
+        labels = lab.cpu().numpy()
+        Xh, rh, nh = X[:nt].cpu().numpy(), roots[:nt].cpu().numpy(), nv[:nt].cpu().numpy()
+        order = np.argsort(labels, kind="stable")
+        starts = np.searchsorted(labels[order], rh)
+        pick = np.random.default_rng(1512).choice(nt, min(nt, 20000), replace=False)
+        Pk = P.reshape(-1, 3, 4)
+        worst = 0.0
+        t0 = time.perf_counter()
+        for t in pick:
+            nodes = order[starts[t]:starts[t] + nh[t]]
+            img = np.searchsorted(base, nodes, side="right") - 1
+            ref = otri.triangulate([Pk[i] for i in img], [sc.images[i].xy[v - base[i]] for i, v in zip(img, nodes)])
+            if np.isfinite(ref).all():
+                worst = max(worst, float(np.linalg.norm(Xh[t] - ref) / max(np.linalg.norm(ref), 1.0)))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(pick) / dt, "unit": "tracks/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{len(pick)} random tracks of the workload, one by one ({dt:.1f} s)",
+                                "max_rel_diff": worst}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args, gm, dev, local):
     """Serving: Poisson single-pair requests over the facade geometry with per-image keypoints log-uniform in
     [2000, 20000], at 500, 1000, 2000 and 5000 req/s, under a 40 GB device-memory budget."""
@@ -503,10 +574,11 @@ def main():
     ap.add_argument("--pairs", type=int, default=0, help="use only the first N pairs (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch every step directly (no CUDA graph replay)")
-    ap.add_argument("--workload", default="facade", choices=["facade", "two_view", "street", "dense", "serving", "pairs", "tracks"],
+    ap.add_argument("--workload", default="facade", choices=["facade", "two_view", "street", "dense", "serving", "pairs", "tracks",
+                                                       "triangulate"],
                     help="facade: the headline batch; two_view: one pair; street: uneven autotuned batch; dense: "
                          "16000-keypoint band sweep; "
-                         "serving: Poisson requests; pairs: candidate pair selection; tracks: track merging")
+                         "serving: Poisson requests; pairs: candidate pair selection; tracks: track merging; triangulate: track triangulation")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving leg: Poisson arrivals, req/s")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving leg duration (0: skip)")
     args = ap.parse_args()
@@ -542,6 +614,8 @@ def main():
             run_pairs(args, gm, dev, local, peaks, peak_kind)
         elif args.workload == "tracks":
             run_tracks(args, gm, dev, local, peaks, peak_kind)
+        elif args.workload == "triangulate":
+            run_triangulate(args, gm, dev, local, peaks, peak_kind)
         else:
             run_serving(args, gm, dev, local)
         return

@@ -183,6 +183,22 @@ GM_API gm_status gm_select_pairs(gm_ctx *ctx, int32_t n_cams, int64_t n_points, 
 GM_API gm_status gm_merge_tracks(gm_ctx *ctx, int64_t n_nodes, int64_t n_edges, const int64_t *edges, int64_t *labels,
                                  int64_t *n_tracks);
 
+/* Track triangulation (the end of Sec. 6.2: every merged track becomes a 3D point by linear least squares).
+ * Nodes are numbered image-major over image_ids: node = (features of image_ids[0 .. k-1]) + feature index in image
+ * image_ids[k] (the caller's keypoint order); n_nodes must equal the total.  labels (int64 [n_nodes]) are those of
+ * gm_merge_tracks: every label is the smallest node of its component (a label above its node or negative is
+ * GM_ERR_INVALID).  Every component with at least two nodes is a track; tracks are numbered by increasing root.
+ * Observation (x, y) in the image with camera P (3 x 4, row-major, double [12] per image in P[n_images][12])
+ * contributes the rows x P3 - P1 and y P3 - P2 of A = [A3 | a4]; the point X solves (A3^T A3) X = -A3^T a4 in
+ * FP64 (NaN if the system is singular; the FP64 sums run in a data-dependent order, so the last bits may differ
+ * between calls).  Outputs (cap rows each): X double [cap][3], roots int64 [cap] (the track's smallest node),
+ * n_views int32 [cap]; *n_tracks = number of tracks.  If it exceeds cap, nothing is written and the call returns
+ * GM_ERR_NOMEM.  P, labels and the outputs may each be host or device memory (X, roots and n_views all alike).
+ * Errors: GM_ERR_INVALID, GM_ERR_NOT_FOUND (an image not put), GM_ERR_NOMEM, GM_ERR_CUDA. */
+GM_API gm_status gm_triangulate(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids, const double *P,
+                                int64_t n_nodes, const int64_t *labels, int64_t cap, double *X, int64_t *roots,
+                                int32_t *n_views, int64_t *n_tracks);
+
 /* Autotuner (a tuning aid; the paper has no counterpart).  Times gm_match_pairs on this batch for every distance
  * path (tc; mma with 16- and 32-query groups; simt) and grid cell size (4, 8, 16 px), `repeats` timed runs each
  * after one warm-up, and leaves the fastest setting in the context: GM_OPT_PATH, GM_OPT_MMA_GROUP and

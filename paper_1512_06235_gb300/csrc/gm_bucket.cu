@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_add_kernel(const int32_t *__r
     if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) off[m] = base + bsum[blockIdx.x];
 }
 
-cudaError_t exclusive_scan(const int32_t *cnt, int32_t m, int32_t *off, int32_t *bsum, cudaStream_t st)
+cudaError_t exclusive_scan_impl(const int32_t *cnt, int32_t m, int32_t *off, int32_t *bsum, cudaStream_t st)
 {
     const int nb = (m + kScanBlock - 1) / kScanBlock;
     scan_local_kernel<<<nb, kScanBlock, 0, st>>>(cnt, m, off, bsum);
@@ -219,7 +219,17 @@ __global__ void batch_records_kernel(const BucketJob *__restrict__ jobs, const i
 
 unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
+cudaError_t exclusive_scan(const int32_t *cnt, int32_t m, int32_t *off, int32_t *bsum, cudaStream_t st)
+{
+    return exclusive_scan_impl(cnt, m, off, bsum, st);
+}
+
 }  // namespace
+
+cudaError_t launch_exclusive_scan(const int32_t *cnt, int32_t m, int32_t *off, int32_t *bsum, cudaStream_t st)
+{
+    return exclusive_scan_impl(cnt, m, off, bsum, st);
+}
 
 cudaError_t launch_bucket_batch_count(const BucketJob *jobs, const int64_t *kp_prefix, int32_t K, int64_t n_total,
                                       int32_t *work, int64_t S, unsigned long long *bad, cudaStream_t st)

@@ -107,7 +107,7 @@ struct gm_ctx {
     size_t bytes_work = 0;          // every DevBuf of the context and of the server slots
 
     gm::Workspace ws;               // synchronous calls
-    gm::DevBuf d_stage, d_work, d_bad, d_bitmap, d_tune, d_btab, d_pairs, d_pairs_out, d_tracks;
+    gm::DevBuf d_stage, d_work, d_bad, d_bitmap, d_tune, d_btab, d_pairs, d_pairs_out, d_tracks, d_tri, d_tri_out;
     std::string tuner_cache;        // gm_autotune's settings file ("" = none)
     gm_stats stats{};
     std::recursive_mutex mu;        // guards images, slots, budget counters and ws

@@ -107,6 +107,9 @@ struct BucketJob {
     int4 *rec;
 };
 
+// Exclusive scan of m int32 counts into off[0 .. m] (off[m] = total); bsum holds m / 1024 + 1 entries.
+cudaError_t launch_exclusive_scan(const int32_t *cnt, int32_t m, int32_t *off, int32_t *bsum, cudaStream_t st);
+
 // Counts of every image of the batch (work[0, S) and bad[0, K) are cleared first); bad[k] counts image k's
 // keypoints outside its image.  kp_prefix[K + 1] and cnt_prefix[K + 1] are the jobs' kp_base / cnt_base with the
 // totals at [K].

@@ -93,6 +93,7 @@ _SIGNATURES = {
                                           ctypes.POINTER(c_i64)]),
     "gm_images_put": (c_i32, [c_p, c_i32, ctypes.POINTER(GmImage), c_i32]),
     "gm_merge_tracks": (c_i32, [c_p, c_i64, c_i64, c_p, c_p, ctypes.POINTER(c_i64)]),
+    "gm_triangulate": (c_i32, [c_p, c_i32, c_p, c_p, c_i64, c_p, c_i64, c_p, c_p, c_p, ctypes.POINTER(c_i64)]),
     "gm_select_pairs": (c_i32, [c_p, c_i32, c_i64, c_p, c_p, c_i32, c_i32, c_p, c_i64, ctypes.POINTER(c_i64)]),
     "gm_autotune": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_i32, ctypes.POINTER(GmTuneResult)]),
     "gm_get_stats": (c_i32, [c_p, ctypes.POINTER(GmStats)]),
@@ -239,6 +240,27 @@ def gm_merge_tracks(ctx, n_nodes: int, edges, labels) -> int:
     nt = c_i64(0)
     _check(load_library().gm_merge_tracks(ctx, n_nodes, int(edges.shape[0]), pe, pl, ctypes.byref(nt)), ctx)
     del k1, k2
+    return nt.value
+
+
+def gm_triangulate(ctx, image_ids, P, labels, X, roots, n_views, cap: int) -> int:
+    """image_ids int32 [K] (host), P float64 [K, 3, 4], labels int64 [n_nodes], X float64 [cap, 3], roots int64 [cap],
+    n_views int32 [cap] (numpy or torch CUDA); returns the number of tracks (GeomatchError.required on NOMEM)."""
+    ids = np.ascontiguousarray(image_ids, np.int32)
+    pp, _, k1 = _ptr(P)
+    pl, _, k2 = _ptr(labels)
+    px, _, k3 = _ptr(X)
+    pr, _, k4 = _ptr(roots)
+    pv, _, k5 = _ptr(n_views)
+    nt = c_i64(0)
+    st = load_library().gm_triangulate(ctx, int(ids.shape[0]), ids.ctypes.data, pp, int(labels.shape[0]), pl, cap,
+                                       px, pr, pv, ctypes.byref(nt))
+    if st == GM_ERR_NOMEM and nt.value > cap:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = nt.value
+        raise err
+    _check(st, ctx)
+    del k1, k2, k3, k4, k5
     return nt.value
 
 
@@ -449,6 +471,24 @@ class Context:
         labels = np.empty(n_nodes, np.int64)
         nt = gm_merge_tracks(self.h, n_nodes, np.ascontiguousarray(edges, np.int64).reshape(-1, 2), labels)
         return labels, nt
+
+    def triangulate(self, image_ids, P, labels):
+        """Tracks of `labels` (image-major nodes over image_ids) as (X float64 [T, 3], roots int64 [T],
+        n_views int32 [T]); P float64 [K, 3, 4]."""
+        P = np.ascontiguousarray(P, np.float64).reshape(-1, 12)
+        labels = np.ascontiguousarray(labels, np.int64)
+        cap = 1024
+        while True:
+            X = np.empty((cap, 3), np.float64)
+            roots = np.empty(cap, np.int64)
+            nv = np.empty(cap, np.int32)
+            try:
+                n = gm_triangulate(self.h, image_ids, P, labels, X, roots, nv, cap)
+                return X[:n], roots[:n], nv[:n]
+            except GeomatchError as e:
+                if e.status != GM_ERR_NOMEM or not hasattr(e, "required"):
+                    raise
+                cap = max(e.required, 1)
 
     def autotune(self, pairs, repeats: int = 3) -> dict:
         return gm_autotune(self.h, pairs, repeats)
