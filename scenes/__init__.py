@@ -12,7 +12,11 @@ Conventions
   baseline, ``F = K_B^{-T} R_B [C_A - C_B]_x R_A^T K_A^{-1}``.  (Eq. 1 of the paper prints the transposed
   form.)  F is normalised to unit Frobenius norm in FP64 and then rounded to FP32; the FP32 values are the input.
 * Descriptors: a uniform [0, 255] base per 3D point; each view adds N(0, 8^2), rounds and clips to [0, 255].
-  Distractor keypoints are uniform in the image with uniform descriptors.  Scales are log-normal(ln 2, 0.5).
+  Distractor keypoints are uniform in the image with uniform descriptors.
+* Scales: every 3D point has an intrinsic scale, log-normal(ln 2, 0.5) from a generator of its own (seed ^ 0x5CA1E,
+  so that the keypoints and descriptors do not depend on it); a projection's scale is the point's scale times a
+  log-normal(0, 0.125) jitter, so the same points are high-scale in every image that sees them (the property the
+  coarse stage relies on, Sec. 4).  Distractor scales are log-normal(ln 2, 0.5).
 * Keypoint order inside an image is shuffled; ``pid`` keeps the 3D point id (-1 for distractors), which gives
   the known correspondences.
 """
@@ -145,7 +149,13 @@ def _view_desc(rng, base_rows, sigma=8.0):
     return np.clip(noisy, 0, 255).astype(np.uint8)
 
 
-def make_image(rng, w, h, uv_true, pids, base, n_distractors, sigma_px=0.5, sigma_desc=8.0) -> Image:
+def point_scales(seed: int, n_points: int) -> np.ndarray:
+    """Intrinsic scale of every 3D point, from a generator independent of the scene's main one."""
+    return np.random.default_rng(seed ^ 0x5CA1E).lognormal(math.log(2.0), 0.5, n_points)
+
+
+def make_image(rng, w, h, uv_true, pids, base, n_distractors, sigma_px=0.5, sigma_desc=8.0,
+               point_scale=None) -> Image:
     """One image: noisy projections of the given points plus uniform distractors, in shuffled order."""
     uv = _noisy_in_image(rng, uv_true, sigma_px, w, h).astype(np.float32)
     # keep strictly inside after the float32 rounding
@@ -156,7 +166,11 @@ def make_image(rng, w, h, uv_true, pids, base, n_distractors, sigma_px=0.5, sigm
     desc = np.concatenate([_view_desc(rng, base[pids], sigma_desc),
                            rng.integers(0, 256, (n_distractors, DESC_DIM), dtype=np.uint8)])
     pid = np.concatenate([pids.astype(np.int32), np.full(n_distractors, -1, np.int32)])
-    scale = rng.lognormal(math.log(2.0), 0.5, xy.shape[0]).astype(np.float32)
+    scale = rng.lognormal(math.log(2.0), 0.5, xy.shape[0])
+    if point_scale is not None:   # projections: the point's scale with a small jitter from the same draw
+        n_proj = uv.shape[0]
+        scale[:n_proj] = point_scale[pids] * (scale[:n_proj] / 2.0) ** 0.25
+    scale = scale.astype(np.float32)
     order = rng.permutation(xy.shape[0])
     return Image(width=w, height=h, xy=np.ascontiguousarray(xy[order]), scale=scale[order],
                  desc=np.ascontiguousarray(desc[order]), pid=pid[order])
@@ -182,7 +196,9 @@ def two_view(seed: int = SEED_BASE + 1, n_points: int = 1500, n_distractors: int
     pts = pts[:n_points]
     base = rng.integers(0, 256, (n_points, DESC_DIM), dtype=np.uint8)
     pids = np.arange(n_points)
-    images = [make_image(rng, w, h, project(c, pts)[0], pids, base, n_distractors) for c in (cam_a, cam_b)]
+    ps = point_scales(seed, n_points)
+    images = [make_image(rng, w, h, project(c, pts)[0], pids, base, n_distractors, point_scale=ps)
+              for c in (cam_a, cam_b)]
     pairs = [Pair(0, 1, fundamental(cam_a, cam_b), d)]
     return Scene("two_view_2000", images, pairs, [cam_a, cam_b], {"points": pts})
 
@@ -237,6 +253,7 @@ def facade(seed: int = SEED_BASE + 2, n_images: int = 100, n_kp=8000, proj_frac:
                       [radius * math.sin(p), 1.6, radius * math.cos(p)]) for p in phis]
     base = rng.integers(0, 256, (n_points, DESC_DIM), dtype=np.uint8)
     kps = np.broadcast_to(np.asarray(n_kp), (n_images,)).astype(np.int64)
+    ps = point_scales(seed, n_points)
     images, vis_sets = [], []
     for ci, cam in enumerate(cams):
         uv, z = project(cam, X)
@@ -244,7 +261,7 @@ def facade(seed: int = SEED_BASE + 2, n_images: int = 100, n_kp=8000, proj_frac:
         vis = np.nonzero((z > 0.1) & inside(uv, w, h) & facing)[0]
         n_proj = min(int(round(proj_frac * kps[ci])), vis.size)
         sel = np.sort(rng.choice(vis, n_proj, replace=False))
-        images.append(make_image(rng, w, h, uv[sel], sel, base, int(kps[ci]) - n_proj))
+        images.append(make_image(rng, w, h, uv[sel], sel, base, int(kps[ci]) - n_proj, point_scale=ps))
         vis_sets.append(sel)
     chosen = _select_pairs(vis_sets, n_points, n_pairs, min_covis)
     pairs = []
@@ -280,6 +297,7 @@ def street(seed: int = SEED_BASE + 3, n_images: int = 1000, n_points: int = 1_00
     else:
         kps = np.broadcast_to(np.asarray(n_kp), (n_images,)).astype(np.int64)
     base = rng.integers(0, 256, (n_points, DESC_DIM), dtype=np.uint8)
+    ps = point_scales(seed, n_points)
     images, vis_sets = [], []
     order = np.argsort(X[:, 2])
     zs = X[order, 2]
@@ -295,7 +313,7 @@ def street(seed: int = SEED_BASE + 3, n_images: int = 1000, n_points: int = 1_00
         n_proj = min(int(round(proj_frac * kps[ci])), vis.size)
         pick = np.sort(rng.choice(vis.size, n_proj, replace=False))
         sel = vis[pick]
-        images.append(make_image(rng, w, h, uv[pick], sel, base, int(kps[ci]) - n_proj))
+        images.append(make_image(rng, w, h, uv[pick], sel, base, int(kps[ci]) - n_proj, point_scale=ps))
         vis_sets.append(sel)
     chosen = _select_pairs_sparse(vis_sets, n_pairs, min_covis)
     pairs = []
