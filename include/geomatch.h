@@ -199,6 +199,47 @@ GM_API gm_status gm_triangulate(gm_ctx *ctx, int32_t n_images, const int32_t *im
                                 int64_t n_nodes, const int64_t *labels, int64_t cap, double *X, int64_t *roots,
                                 int32_t *n_views, int64_t *n_tracks);
 
+/* Coarse stage (Sec. 4): matching of the high-scale features of image pairs without geometry.  Every image keeps
+ * its floor(n * eta_pct / 100) features of the largest scale (equal scales: the lower feature index first); an
+ * image with fewer than min_features features keeps all of them.  A pair (A, B) is matched in two preemptive
+ * batches with an unbounded band (exhaustive nearest / second-nearest search and the pair's ratio test): first
+ * A's floor(n * first_pct / 100) highest-scale features against B's kept features; then, only if the first batch
+ * gave more than min_matches matches, the rest of A's kept features against the same targets (an image below
+ * min_features is matched with all its features in the first batch and has no second).  Requires scales
+ * (gm_image_put with scale != NULL, no NaN).  A NULL options pointer means the paper's values. */
+typedef struct {
+    int32_t eta_pct;        /* kept features, % of the image by scale, 1..100 (paper: 20) */
+    int32_t first_pct;      /* first query batch, % of the image by scale, 1..eta_pct (paper: 10) */
+    int32_t min_features;   /* images with fewer features keep them all, >= 0 (paper: 1000) */
+    int32_t min_matches;    /* the second batch runs after more than this many first-batch matches, >= 0 (paper: 4) */
+} gm_coarse_opts;
+
+/* Builds (or refreshes, after an image was put again or with other options) the coarse views of the images: the
+ * selections above, registered on the device as internal images (they count toward the memory budget; evicting
+ * an image drops its views).  gm_match_coarse builds missing views itself; this call lets them be built ahead.
+ * Errors: GM_ERR_INVALID (bad options, an image without scales or with a NaN scale), GM_ERR_NOT_FOUND, those of
+ * gm_image_put. */
+GM_API gm_status gm_coarse_prepare(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids,
+                                   const gm_coarse_opts *opts);
+
+/* The selection of one image as ascending feature indices: q1 (first query batch), q2 (second query batch) and t
+ * (targets), cap entries each (host or device, all alike); counts[3] (host) receives their sizes.  If a size
+ * exceeds cap nothing is written and the call returns GM_ERR_NOMEM.  Builds the views if needed. */
+GM_API gm_status gm_coarse_selection(gm_ctx *ctx, int32_t image_id, const gm_coarse_opts *opts, int32_t *q1,
+                                     int32_t *q2, int32_t *t, int32_t cap, int32_t *counts);
+
+/* Coarse matching of n_pairs pairs (img_a, img_b and the ratio of each gm_pair; F and band_px are ignored):
+ *   pair_off: int64 [n_pairs + 1]; pair k's rows are pair_off[k] .. pair_off[k+1]-1: the first batch's matches
+ *             sorted by the feature index of A, then the second batch's, sorted the same way;
+ *   matches:  int32 [cap][2] rows (feature of A, feature of B) in the images' own indices;
+ *   second:   int32 [n_pairs] or NULL: 1 where the second batch ran;
+ *   *n_written: number of rows; if it exceeds cap, pair_off is written, matches not, and the call returns
+ *             GM_ERR_NOMEM.  pair_off, matches and second may each be host or device memory.
+ * Errors: those of gm_coarse_prepare and gm_match_pairs. */
+GM_API gm_status gm_match_coarse(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, const gm_coarse_opts *opts,
+                                 int64_t *pair_off, int32_t *matches, int64_t cap, int64_t *n_written,
+                                 int32_t *second);
+
 /* Autotuner (a tuning aid; the paper has no counterpart).  Times gm_match_pairs on this batch for every distance
  * path (tc; mma with 16- and 32-query groups; simt) and grid cell size (4, 8, 16 px), `repeats` timed runs each
  * after one warm-up, and leaves the fastest setting in the context: GM_OPT_PATH, GM_OPT_MMA_GROUP and

@@ -139,9 +139,10 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Validates one pair and fills its device record (without qoff).
-gm_status prepare_pair(gm_ctx *ctx, const gm_pair &pr, int64_t k, PairDev &pd)
+gm_status prepare_pair(gm_ctx *ctx, const gm_pair &pr, int64_t k, PairDev &pd, bool internal)
 {
+    if (!internal && (pr.img_a < 0 || pr.img_b < 0))
+        return fail(GM_ERR_NOT_FOUND, "pair %lld: image %d not registered", (long long)k, std::min(pr.img_a, pr.img_b));
     auto ia = ctx->images.find(pr.img_a), ib = ctx->images.find(pr.img_b);
     if (ia == ctx->images.end() || ib == ctx->images.end())
         return fail(GM_ERR_NOT_FOUND, "pair %lld: image %d not registered", (long long)k,
@@ -214,14 +215,14 @@ gm_status encode_maps(const ImageDev &dev, TmaMaps &maps)
     return GM_OK;
 }
 
-gm_status engine_plan(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs)
+gm_status engine_plan(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs, bool internal)
 {
     ws.pd.resize(n_pairs);
     ws.n_pairs = n_pairs;
     ws.Q = 0;
     ws.nitems = 0;
     for (int32_t k = 0; k < n_pairs; ++k) {
-        gm_status st = prepare_pair(ctx, pairs[k], k, ws.pd[k]);
+        gm_status st = prepare_pair(ctx, pairs[k], k, ws.pd[k], internal);
         if (st != GM_OK) return st;
         ws.pd[k].qoff = ws.Q;
         ws.Q += ws.pd[k].n_a;
@@ -471,7 +472,7 @@ gm_status gm_create(const gm_config *cfg, gm_ctx **out)
         ctx->own_stream = true;
     }
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
-    if (workspace_init(ctx->ws, ctx->stream) != GM_OK) {
+    if (workspace_init(ctx->ws, ctx->stream) != GM_OK || workspace_init(ctx->ws2, ctx->ws.stream) != GM_OK) {
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
         return GM_ERR_CUDA;
@@ -494,9 +495,13 @@ gm_status gm_destroy(gm_ctx *ctx)
         delete kv.second;
     }
     ctx->images.clear();
+    for (auto &kv : ctx->coarse) free_dev(ctx, kv.second.lists);
+    ctx->coarse.clear();
+    workspace_free(ctx, ctx->ws2);   // shares ws's stream: freed first
     workspace_free(ctx, ctx->ws);
     for (DevBuf *b : {&ctx->d_imgs, &ctx->d_maps, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap, &ctx->d_tune,
-                      &ctx->d_btab, &ctx->d_pairs, &ctx->d_pairs_out, &ctx->d_tracks, &ctx->d_tri, &ctx->d_tri_out})
+                      &ctx->d_btab, &ctx->d_pairs, &ctx->d_pairs_out, &ctx->d_tracks, &ctx->d_tri, &ctx->d_tri_out,
+                      &ctx->d_coarse_tab, &ctx->d_coarse_stage, &ctx->d_coarse_out})
         free_dev(ctx, *b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -701,17 +706,19 @@ gm_status bucket_batches(gm_ctx *ctx, int32_t count, const gm_image *imgs, const
     return GM_OK;
 }
 
-// Registers `count` images (App. A Step 1).  All inputs are validated before anything registered changes; the
-// device work of all images is enqueued back to back with two stream synchronisations in total (after the
-// keypoint check, and at the end).
-gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t on_device, const char *fn)
+}  // namespace
+
+// All inputs are validated before anything registered changes; the device work of all images is enqueued back to
+// back with two stream synchronisations in total (after the keypoint check, and at the end).
+gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t on_device, const char *fn,
+                     bool internal)
 {
     if (!ctx) return fail(GM_ERR_INVALID, "%s: null context", fn);
     if (count < 0 || (count > 0 && !imgs) || (on_device != 0 && on_device != 1))
         return fail(GM_ERR_INVALID, "%s: bad arguments", fn);
     for (int32_t k = 0; k < count; ++k) {
         const gm_image &g = imgs[k];
-        if (g.image_id < 0 || g.width <= 0 || g.height <= 0 || g.width > (1 << 20) || g.height > (1 << 20) || g.n < 0 ||
+        if ((g.image_id < 0) != internal || g.width <= 0 || g.height <= 0 || g.width > (1 << 20) || g.height > (1 << 20) || g.n < 0 ||
             (g.n > 0 && (!g.xy || !g.desc)))
             return fail(GM_ERR_INVALID, "%s: bad arguments (id %d, %dx%d, n %d)", fn, g.image_id, g.width, g.height, g.n);
         for (int32_t l = 0; l < k; ++l)
@@ -831,6 +838,7 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             ctx->bytes_images += L[k].tot;
         }
         img->dev = dev[k];
+        img->gen = ++ctx->image_gen;
         img->scale = reinterpret_cast<const float *>(static_cast<char *>(img->block) + L[k].offs[10]);
         img->has_scale = g.n > 0 && g.scale != nullptr;
         TmaMaps maps;
@@ -855,7 +863,36 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
     return GM_OK;
 }
 
-}  // namespace
+void drop_image(gm_ctx *ctx, int32_t image_id)
+{
+    auto it = ctx->images.find(image_id);
+    if (it == ctx->images.end()) return;
+    cudaStreamSynchronize(ctx->ws.stream);
+    ImageSlot *img = it->second;
+    cudaFree(img->block);
+    ctx->bytes_images -= img->bytes;
+    ctx->slots[img->slot] = nullptr;
+    ctx->images.erase(it);
+    delete img;
+}
+
+gm_status run_batch(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs, bool internal, const char *fn)
+{
+    gm_status st = engine_plan(ctx, ws, n_pairs, pairs, internal);
+    if (st != GM_OK) return st;
+    for (int attempt = 0;; ++attempt) {
+        if ((st = engine_launch(ctx, ws, nullptr)) != GM_OK) return st;
+        GM_CUDA(cudaStreamSynchronize(ws.stream));
+        engine_stats(ctx, ws, ctx->stats);
+        if (!ws.overflow) break;
+        if (attempt >= 2) return fail(GM_ERR_NOMEM, "%s: candidate stream buffer kept overflowing", fn);
+        ws.stream_cap = ws.stream_used + ws.stream_used / 4 + 1024;   // grow to what the batch needed, then rerun
+    }
+    if (ctx->stats.n_device_errors)
+        return fail(GM_ERR_TIMEOUT, "%s: %lld device-side waits ran out", fn, (long long)ctx->stats.n_device_errors);
+    return GM_OK;
+}
+
 }  // namespace gm
 
 extern "C" {
@@ -877,15 +914,18 @@ gm_status gm_image_evict(gm_ctx *ctx, int32_t image_id)
     if (!ctx) return fail(GM_ERR_INVALID, "gm_image_evict: null context");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     auto it = ctx->images.find(image_id);
-    if (it == ctx->images.end()) return fail(GM_ERR_NOT_FOUND, "gm_image_evict: image %d not registered", image_id);
+    if (image_id < 0 || it == ctx->images.end())
+        return fail(GM_ERR_NOT_FOUND, "gm_image_evict: image %d not registered", image_id);
     if (ctx->server) server_drain(ctx->server);
-    cudaStreamSynchronize(ctx->ws.stream);
-    ImageSlot *img = it->second;
-    cudaFree(img->block);
-    ctx->bytes_images -= img->bytes;
-    ctx->slots[img->slot] = nullptr;
-    ctx->images.erase(it);
-    delete img;
+    drop_image(ctx, image_id);
+    auto cv = ctx->coarse.find(image_id);   // the image's coarse-stage views go with it
+    if (cv != ctx->coarse.end()) {
+        if (!cv->second.all)
+            for (int v = 0; v < 3; ++v)
+                if (cv->second.id[v] < 0) drop_image(ctx, cv->second.id[v]);
+        free_dev(ctx, cv->second.lists);
+        ctx->coarse.erase(cv);
+    }
     return GM_OK;
 }
 
@@ -905,18 +945,8 @@ gm_status gm_match_pairs(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int
         ctx->stats = gm_stats{};
         return GM_OK;
     }
-    gm_status st = engine_plan(ctx, ws, n_pairs, pairs);
+    gm_status st = run_batch(ctx, ws, n_pairs, pairs, false, "gm_match_pairs");
     if (st != GM_OK) return st;
-    for (int attempt = 0;; ++attempt) {
-        if ((st = engine_launch(ctx, ws, nullptr)) != GM_OK) return st;
-        GM_CUDA(cudaStreamSynchronize(ws.stream));
-        engine_stats(ctx, ws, ctx->stats);
-        if (!ws.overflow) break;
-        if (attempt >= 2) return fail(GM_ERR_NOMEM, "gm_match_pairs: candidate stream buffer kept overflowing");
-        ws.stream_cap = ws.stream_used + ws.stream_used / 4 + 1024;   // grow to what the batch needed, then rerun
-    }
-    if (ctx->stats.n_device_errors)
-        return fail(GM_ERR_TIMEOUT, "gm_match_pairs: %lld device-side waits ran out", (long long)ctx->stats.n_device_errors);
     const int64_t *h_off = static_cast<const int64_t *>(ws.h_off.p);
     const int64_t total = h_off[n_pairs];
     *n_written = total;

@@ -35,6 +35,21 @@ struct ImageSlot {
     size_t bytes = 0;
     const float *scale = nullptr;   // keypoint scales in the caller's order (inside block)
     bool has_scale = false;
+    uint64_t gen = 0;               // registration generation (changes on every put of this id)
+};
+
+// Coarse-stage views of one registered image (Sec. 4): its high-scale feature subsets registered as internal
+// images (negative ids, invisible to the caller) -- the first query batch, the second query batch and the
+// targets -- with the feature index lists that map a view's features back to the image's.  An image below the
+// minimum feature count is its own query and target view (lists empty = identity).
+struct CoarseViews {
+    uint64_t gen = 0;               // generation of the image the views were built from
+    int32_t eta = 0, first = 0, min_features = 0;
+    bool all = false;
+    int32_t id[3] = {0, 0, 0};      // q1, q2, t: internal ids (the image's own id when `all`; 0 when empty)
+    int32_t n[3] = {0, 0, 0};
+    DevBuf lists;                   // int32: q1, q2, t lists (ascending feature indices)
+    const int32_t *list[3] = {nullptr, nullptr, nullptr};
 };
 
 // Everything one batch needs on the device and in pinned host memory.  The synchronous API owns one; every
@@ -108,6 +123,11 @@ struct gm_ctx {
 
     gm::Workspace ws;               // synchronous calls
     gm::DevBuf d_stage, d_work, d_bad, d_bitmap, d_tune, d_btab, d_pairs, d_pairs_out, d_tracks, d_tri, d_tri_out;
+    gm::Workspace ws2;              // second batch of the coarse stage's preemptive schedule (shares ws's stream)
+    gm::DevBuf d_coarse_tab, d_coarse_stage, d_coarse_out;
+    std::unordered_map<int32_t, gm::CoarseViews> coarse;   // by caller's image id
+    uint64_t image_gen = 0;
+    int32_t next_internal_id = -1;
     std::string tuner_cache;        // gm_autotune's settings file ("" = none)
     gm_stats stats{};
     std::recursive_mutex mu;        // guards images, slots, budget counters and ws
@@ -126,8 +146,20 @@ void free_host(HostBuf &b);
 gm_status workspace_init(Workspace &ws, cudaStream_t stream);
 void workspace_free(gm_ctx *ctx, Workspace &ws);
 
+// Validates one pair and fills its device record (without qoff).  Negative image ids (internal images) are
+// accepted only with `internal`.
+gm_status prepare_pair(gm_ctx *ctx, const gm_pair &pr, int64_t k, PairDev &pd, bool internal = false);
 // Validates the pairs and fills ws.pd / ws.Q / ws.nitems.  Caller holds ctx->mu.
-gm_status engine_plan(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs);
+gm_status engine_plan(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs, bool internal = false);
+// Plans, launches and completes one batch on ws (reruns with a larger stream buffer on overflow); afterwards
+// ws.h_off holds the offsets [P + 1] and ws.d_rows the rows.  Caller holds ctx->mu.
+gm_status run_batch(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs, bool internal, const char *fn);
+// Registers `count` images (App. A Step 1); internal images carry negative ids.
+gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t on_device, const char *fn,
+                     bool internal = false);
+// Drops one registered image (caller holds ctx->mu; serving drained by the caller).
+void drop_image(gm_ctx *ctx, int32_t image_id);
+bool is_device_ptr(const void *p);
 // Enqueues the whole batch on ws.stream: table upload, order, match, count/scan, row writing into rows_dst
 // (device memory or mapped host memory with room for ws.Q rows; nullptr = ws.d_rows), then the D2H copy of the
 // offsets and counters into ws.h_off.  Nothing waits.  Caller holds ctx->mu.

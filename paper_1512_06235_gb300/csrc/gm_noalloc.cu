@@ -26,7 +26,6 @@ static __device__ __align__(256) unsigned char gm_static_scratch[kStaticScratchB
 
 namespace gm {
 
-gm_status prepare_pair(gm_ctx *ctx, const gm_pair &pr, int64_t k, PairDev &pd);
 bool is_device_ptr(const void *p);
 
 namespace {

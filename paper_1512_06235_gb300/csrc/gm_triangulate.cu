@@ -20,9 +20,6 @@
 #include "gm_ctx.h"
 
 namespace gm {
-
-bool is_device_ptr(const void *p);
-
 namespace {
 
 struct TriImage {
@@ -150,7 +147,8 @@ gm_status gm_triangulate(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids
     int64_t total = 0;
     for (int32_t k = 0; k < n_images; ++k) {
         auto it = ctx->images.find(image_ids[k]);
-        if (it == ctx->images.end()) return fail(GM_ERR_NOT_FOUND, "gm_triangulate: image %d not registered", image_ids[k]);
+        if (image_ids[k] < 0 || it == ctx->images.end())
+            return fail(GM_ERR_NOT_FOUND, "gm_triangulate: image %d not registered", image_ids[k]);
         const ImageDev &d = it->second->dev;
         imgs[k] = TriImage{d.xy, d.inv_perm, total, d.n, 0};
         total += d.n;

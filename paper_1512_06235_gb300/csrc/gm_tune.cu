@@ -23,7 +23,6 @@
 
 namespace gm {
 
-gm_status prepare_pair(gm_ctx *ctx, const gm_pair &pr, int64_t k, PairDev &pd);
 
 namespace {
 

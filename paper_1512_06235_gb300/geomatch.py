@@ -63,6 +63,10 @@ class GmImage(ctypes.Structure):
                 ("desc", c_p)]
 
 
+class GmCoarseOpts(ctypes.Structure):
+    _fields_ = [("eta_pct", c_i32), ("first_pct", c_i32), ("min_features", c_i32), ("min_matches", c_i32)]
+
+
 class GmTuneResult(ctypes.Structure):
     _fields_ = [("path", c_i32), ("mma_group", c_i32), ("cell_px", c_i32), ("ms", ctypes.c_float),
                 ("from_cache", c_i32)]
@@ -93,6 +97,10 @@ _SIGNATURES = {
                                           ctypes.POINTER(c_i64)]),
     "gm_images_put": (c_i32, [c_p, c_i32, ctypes.POINTER(GmImage), c_i32]),
     "gm_merge_tracks": (c_i32, [c_p, c_i64, c_i64, c_p, c_p, ctypes.POINTER(c_i64)]),
+    "gm_coarse_prepare": (c_i32, [c_p, c_i32, c_p, ctypes.POINTER(GmCoarseOpts)]),
+    "gm_coarse_selection": (c_i32, [c_p, c_i32, ctypes.POINTER(GmCoarseOpts), c_p, c_p, c_p, c_i32, c_p]),
+    "gm_match_coarse": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), ctypes.POINTER(GmCoarseOpts), c_p, c_p, c_i64,
+                                ctypes.POINTER(c_i64), c_p]),
     "gm_triangulate": (c_i32, [c_p, c_i32, c_p, c_p, c_i64, c_p, c_i64, c_p, c_p, c_p, ctypes.POINTER(c_i64)]),
     "gm_select_pairs": (c_i32, [c_p, c_i32, c_i64, c_p, c_p, c_i32, c_i32, c_p, c_i64, ctypes.POINTER(c_i64)]),
     "gm_autotune": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_i32, ctypes.POINTER(GmTuneResult)]),
@@ -262,6 +270,55 @@ def gm_triangulate(ctx, image_ids, P, labels, X, roots, n_views, cap: int) -> in
     _check(st, ctx)
     del k1, k2, k3, k4, k5
     return nt.value
+
+
+def coarse_opts(eta_pct: int = 20, first_pct: int = 10, min_features: int = 1000, min_matches: int = 4):
+    return GmCoarseOpts(eta_pct, first_pct, min_features, min_matches)
+
+
+def _coarse_pairs_array(pairs):
+    arr = (GmPair * max(1, len(pairs)))()
+    for k, pr in enumerate(pairs):
+        arr[k] = pr if isinstance(pr, GmPair) else make_pair(pr.a, pr.b, np.eye(3), float("inf"), pr.p, pr.q)
+    return arr
+
+
+def gm_coarse_prepare(ctx, image_ids, opts=None):
+    ids = np.ascontiguousarray(image_ids, np.int32)
+    _check(load_library().gm_coarse_prepare(ctx, int(ids.size), ids.ctypes.data, opts), ctx)
+
+
+def gm_coarse_selection(ctx, image_id: int, q1, q2, t, cap: int, opts=None):
+    """Writes the selection lists into q1, q2, t (numpy or torch CUDA, cap entries each); returns the 3 sizes."""
+    counts = np.zeros(3, np.int32)
+    p1, _, k1 = _ptr(q1)
+    p2, _, k2 = _ptr(q2)
+    p3, _, k3 = _ptr(t)
+    st = load_library().gm_coarse_selection(ctx, image_id, opts, p1, p2, p3, cap, counts.ctypes.data)
+    if st == GM_ERR_NOMEM:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = int(counts.max())
+        raise err
+    _check(st, ctx)
+    del k1, k2, k3
+    return tuple(int(c) for c in counts)
+
+
+def gm_match_coarse(ctx, pairs, pair_off, matches, cap: int, second=None, opts=None) -> int:
+    """Coarse-stage matching into caller buffers (numpy or torch CUDA); returns n_written."""
+    arr = _coarse_pairs_array(pairs)
+    po, _, k1 = _ptr(pair_off)
+    pm, _, k2 = _ptr(matches)
+    ps, _, k3 = _ptr(second)
+    n = c_i64(0)
+    st = load_library().gm_match_coarse(ctx, len(pairs), arr, opts, po, pm, cap, ctypes.byref(n), ps)
+    if st == GM_ERR_NOMEM:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = n.value
+        raise err
+    _check(st, ctx)
+    del k1, k2, k3
+    return n.value
 
 
 def gm_image_evict(ctx, image_id: int):
@@ -471,6 +528,22 @@ class Context:
         labels = np.empty(n_nodes, np.int64)
         nt = gm_merge_tracks(self.h, n_nodes, np.ascontiguousarray(edges, np.int64).reshape(-1, 2), labels)
         return labels, nt
+
+    def coarse_selection(self, image_id: int, opts=None):
+        """(q1, q2, t) ascending feature indices of the image's coarse selection (Sec. 4)."""
+        cap = max(1, self.n.get(image_id, 1))
+        q1, q2, t = (np.empty(cap, np.int32) for _ in range(3))
+        c = gm_coarse_selection(self.h, image_id, q1, q2, t, cap, opts)
+        return q1[:c[0]], q2[:c[1]], t[:c[2]]
+
+    def match_coarse(self, pairs, opts=None):
+        """Coarse-stage matching (Sec. 4): (pair_off int64[P+1], matches int32[M,2], second int32[P])."""
+        cap = sum(self.n.get(p.img_a if isinstance(p, GmPair) else p.a, 0) for p in pairs)
+        off = np.empty(len(pairs) + 1, np.int64)
+        sec = np.empty(max(1, len(pairs)), np.int32)
+        m = np.empty((max(cap, 1), 2), np.int32)
+        n = gm_match_coarse(self.h, pairs, off, m, cap, sec, opts)
+        return off, m[:n], sec[:len(pairs)]
 
     def triangulate(self, image_ids, P, labels):
         """Tracks of `labels` (image-major nodes over image_ids) as (X float64 [T, 3], roots int64 [T],
