@@ -14,6 +14,7 @@ the host cores (cpu_baseline), SM clocks sampled during the timed region.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -180,6 +181,13 @@ def _oracle_comparisons(sc, pairs, n_sample=200, seed=1512):
             "pairs_per_s_extrapolated": len(sample) / dt}
 
 
+def _pair_array(gm, pairs, d=None):
+    """The batch's gm_pair array, built once outside the timed region (vectorised)."""
+    return gm.make_pairs([p.a for p in pairs], [p.b for p in pairs],
+                         np.stack([np.asarray(p.F, np.float32).reshape(9) for p in pairs]),
+                         [p.d for p in pairs] if d is None else d, [p.p for p in pairs], [p.q for p in pairs])
+
+
 def _time_batch(gm, ctx, gp, cap, steps, warmup, dev):
     import torch
     off = torch.empty(len(gp) + 1, dtype=torch.int64, device=dev)
@@ -210,7 +218,7 @@ def run_street(args, gm, dev, local, peaks, peak_kind):
     stream = __import__("torch").cuda.current_stream(dev)
     ctx = gm.Context(device=local, stream=stream)
     ctx.put_images({k: im for k, im in enumerate(sc.images)})
-    gp = [gm.make_pair(p.a, p.b, p.F, p.d, p.p, p.q) for p in sc.pairs]
+    gp = _pair_array(gm, sc.pairs)
     cap = sum(sc.images[p.a].n for p in sc.pairs)
     tune = ctx.autotune(gp, repeats=1)
     ctx.set_option(gm.GM_OPT_GRAPH, 1)
@@ -252,11 +260,11 @@ def run_dense(args, gm, dev, local, peaks, peak_kind):
     cap = sum(sc.images[p.a].n for p in sc.pairs)
     sweep = []
     for d in (2.0, 4.0, 8.0, 16.0):
-        gp = [gm.make_pair(p.a, p.b, p.F, d, p.p, p.q) for p in sc.pairs]
+        gp = _pair_array(gm, sc.pairs, d)
         ms, msm, st = _time_batch(gm, ctx, gp, cap, max(1, min(args.steps, 3)), 2, dev)
         sweep.append({"d": d, "path": "tc", "pairs_per_s": len(gp) / (ms / 1e3), "ms_per_step": ms, "ms_match": msm,
                       "comparisons_per_s": st["n_candidates"] / (ms / 1e3), "candidates_per_step": st["n_candidates"]})
-    gp4 = [gm.make_pair(p.a, p.b, p.F, 4.0, p.p, p.q) for p in sc.pairs]
+    gp4 = _pair_array(gm, sc.pairs, 4.0)
     for name, path, group in (("mma16", 2, 16), ("simt", 3, 16)):
         ctx.set_option(gm.GM_OPT_PATH, path)
         ctx.set_option(gm.GM_OPT_MMA_GROUP, group)
@@ -265,7 +273,7 @@ def run_dense(args, gm, dev, local, peaks, peak_kind):
                       "comparisons_per_s": st["n_candidates"] / (ms / 1e3)})
     sub = sc.pairs[:300]
     capi = sum(sc.images[p.a].n for p in sub)
-    gpi = [gm.make_pair(p.a, p.b, p.F, float("inf"), p.p, p.q) for p in sub]
+    gpi = _pair_array(gm, sub, float("inf"))
     for name, path in (("tc", 1), ("mma16", 2)):
         ctx.set_option(gm.GM_OPT_PATH, path)
         ctx.set_option(gm.GM_OPT_MMA_GROUP, 16)
@@ -298,7 +306,7 @@ def run_two_view(args, gm, dev, local):
     for k, im in enumerate(sc.images):
         ctx.put_image(k, im)
     ctx.set_option(gm.GM_OPT_GRAPH, 1)
-    gp = [gm.make_pair(p.a, p.b, p.F, p.d, p.p, p.q) for p in sc.pairs]
+    gp = _pair_array(gm, sc.pairs)
     cap = sc.images[sc.pairs[0].a].n
     steps = max(args.steps, 50)
     ms, msm, st = _time_batch(gm, ctx, gp, cap, steps, max(args.warmup, 5), dev)
@@ -507,18 +515,19 @@ def run_coarse(args, gm, dev, local, peaks, peak_kind):
         torch.cuda.synchronize(dev)
         prep_ms.append(x.elapsed_time(y))
     opts = gm.coarse_opts()
+    cpairs = gm.make_pairs([p.a for p in pairs], [p.b for p in pairs], np.eye(3), float("inf"), 4, 5)
     cap = sum(sc.images[p.a].n for p in pairs) // 5
     off = torch.empty(len(pairs) + 1, dtype=torch.int64, device=dev)
     m = torch.empty((cap, 2), dtype=torch.int32, device=dev)
     sec = torch.empty(len(pairs), dtype=torch.int32, device=dev)
     for _ in range(max(args.warmup, 3)):
-        n = gm.gm_match_coarse(ctx.h, pairs, off, m, cap, sec, opts)
+        n = gm.gm_match_coarse(ctx.h, cpairs, off, m, cap, sec, opts)
     torch.cuda.synchronize(dev)
     steps = max(args.steps, 5)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for x, y in ev:
         x.record(stream)
-        n = gm.gm_match_coarse(ctx.h, pairs, off, m, cap, sec, opts)
+        n = gm.gm_match_coarse(ctx.h, cpairs, off, m, cap, sec, opts)
         y.record(stream)
     torch.cuda.synchronize(dev)
     ms = float(np.mean([x.elapsed_time(y) for x, y in ev]))
@@ -568,7 +577,7 @@ def run_serving(args, gm, dev, local):
     stream = __import__("torch").cuda.current_stream(dev)
     ctx = gm.Context(device=local, stream=stream, mem_budget_bytes=40 << 30, max_inflight=2)
     ctx.put_images({k: im for k, im in enumerate(sc.images)})
-    gp = [gm.make_pair(p.a, p.b, p.F, p.d, p.p, p.q) for p in sc.pairs]
+    gp = _pair_array(gm, sc.pairs)
     for r in (500, 1000, 2000, 5000):
         s = _serving(gm, ctx, gp, r, args.serve_seconds if args.serve_seconds > 0 else 3.0)
         s["budget"] = "40 GB"
@@ -709,7 +718,7 @@ def main():
         ctx.set_option(gm.GM_OPT_GRAPH, 1)
     # ---- device-resident measurement: images registered before the timed region
     ctx.put_images({k: im for k, im in enumerate(sc.images)})
-    gp = [gm.make_pair(p.a, p.b, p.F, p.d, p.p, p.q) for p in pairs]
+    gp = _pair_array(gm, pairs)
     cap = sum(sc.images[p.a].n for p in pairs)
     off_d = torch.empty(len(pairs) + 1, dtype=torch.int64, device=dev)
     rows_d = torch.empty((cap, 2), dtype=torch.int32, device=dev)
@@ -758,7 +767,7 @@ def main():
         h2d += xy.numel() * 4 + scl.numel() * 4 + ds.numel()
     off_h = torch.empty(len(pairs) + 1, dtype=torch.int64).pin_memory()
     rows_h = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
-    h2d += len(gp) * 48
+    h2d += len(gp) * ctypes.sizeof(gm.GmPair)   # the gm_pair records handed to the library
     e2e_ctx = gm.Context(device=local, stream=stream, path=args.path, cell_px=args.cell)
     if args.group != 16:
         e2e_ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)

@@ -23,7 +23,8 @@
 //       the FP32 band test, D = |a'|^2 + |b'|^2 - 2 a'.b' packed with the column into one int32 key and a masked
 //       running top-2 (two interleaved accumulators, no branch in the loop); the rare elements inside the FP32 error
 //       margin are re-decided in FP64 afterwards; at the end of the group the two column halves merge and the
-//       integer ratio test q^2 D1 < p^2 D2 decides (Sec. 2.3).
+//       integer ratio test q^2 D1 < p^2 D2 decides (Sec. 2.3).  With an unbounded band (d = inf: exhaustive
+//       matching, the coarse stage) every real keypoint is a candidate and the per-element band test is skipped.
 //
 // CTA b takes work items b, b + gridDim.x, ... (static order: every role derives the same group sequence).
 // Every mbarrier wait gives up after one second; the CTA then raises the batch error counter, every role leaves its
@@ -461,6 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             const GroupDesc &gd = cl.desc[g];
             const int total = gd.total, nchunks = (total + kN - 1) / kN;
             const float d = gd.d;
+            const bool unbounded = isinf(d);   // the whole image is every row's candidate set
             const int out_i = cl.rinfo[g][row][0];
             const float qx = cl.qxy[g][row].x, qy = cl.qxy[g][row].y;
             float la = 0.0f, lb = 0.0f, lc = 0.0f, llo = -1.0f, lhi = -1.0f;   // no query: never inside
@@ -493,7 +495,36 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 if (!mbar_wait_warp(&cl.stage_full[s], (ck / kStages) & 1)) { ok = false; break; }   // records
                 const int4 *rs = rec + (s * kRecStage) / 16 + 32 * h;
                 const int k1_before = k1;
-                if (32 * h < total - c * kN) {
+                const int nvalid = total - c * kN - 32 * h;   // real columns of this half-chunk (may exceed 32)
+                if (unbounded && nvalid > 0) {
+                    // d = inf: every real keypoint is a candidate (Eq. 2 holds for any line), so only the key and
+                    // the masked-free top-2 remain; columns past the image's end are skipped
+                    int ka1 = k1, ka2 = k2, kb1 = INT_MAX, kb2 = INT_MAX;
+                    const int *rz = reinterpret_cast<const int *>(rs) + 2;   // r.z of record jj at rz[4 * jj]
+                    if (nvalid >= 32) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            const uint32_t bits = (uint32_t)__float_as_int(__int_as_float(v[jj]) + 12582912.0f);
+                            const int key = (int)(Rc + (uint32_t)rz[4 * jj] + (uint32_t)jj - 512u * bits);
+                            if (jj & 1) { kb2 = min(kb2, max(kb1, key)); kb1 = min(kb1, key); }
+                            else { ka2 = min(ka2, max(ka1, key)); ka1 = min(ka1, key); }
+                        }
+                        cnt += 32;
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            if (jj < nvalid) {
+                                const uint32_t bits = (uint32_t)__float_as_int(__int_as_float(v[jj]) + 12582912.0f);
+                                const int key = (int)(Rc + (uint32_t)rz[4 * jj] + (uint32_t)jj - 512u * bits);
+                                if (jj & 1) { kb2 = min(kb2, max(kb1, key)); kb1 = min(kb1, key); }
+                                else { ka2 = min(ka2, max(ka1, key)); ka1 = min(ka1, key); }
+                            }
+                        }
+                        cnt += nvalid;
+                    }
+                    k2 = min(min(ka2, kb2), max(ka1, kb1));
+                    k1 = min(ka1, kb1);
+                } else if (!unbounded && nvalid > 0) {
                     // two interleaved top-2 accumulators (even / odd columns) shorten the dependency chain; bit jj
                     // of mlo marks an element inside by the FP32 test, of mhi one not outside (mhi & ~mlo: within
                     // the error margin, re-decided in FP64 below)

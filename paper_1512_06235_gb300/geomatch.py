@@ -163,7 +163,35 @@ def make_pair(a: int, b: int, F, d: float, p: int = 4, q: int = 5) -> GmPair:
     return pr
 
 
+_PAIR_DTYPE = np.dtype([("img_a", "<i4"), ("img_b", "<i4"), ("F", "<f4", (9,)), ("band_px", "<f4"),
+                        ("ratio_num", "<u2"), ("ratio_den", "<u2")])
+
+
+def make_pairs(a, b, F, d, p=4, q=5):
+    """A ctypes array of gm_pair built from columns (vectorised; broadcast scalars): a, b int [n], F [n, 9] or
+    [9], d, p, q.  Pass it to the C mirrors as the `pairs` argument to skip per-pair marshalling."""
+    a = np.asarray(a)
+    n = a.shape[0]
+    rec = np.zeros(max(n, 1), _PAIR_DTYPE)
+    rec["img_a"][:n] = a
+    rec["img_b"][:n] = b
+    rec["F"][:n] = np.broadcast_to(np.asarray(F, np.float32).reshape(-1, 9), (n, 9))
+    rec["band_px"][:n] = d
+    rec["ratio_num"][:n] = p
+    rec["ratio_den"][:n] = q
+    assert _PAIR_DTYPE.itemsize == ctypes.sizeof(GmPair)
+    arr = (GmPair * max(n, 1)).from_buffer_copy(rec.tobytes())
+    arr._n = n
+    return arr
+
+
+def _n_pairs(pairs):
+    return getattr(pairs, "_n", len(pairs))
+
+
 def _pairs_array(pairs):
+    if isinstance(pairs, ctypes.Array):
+        return pairs
     arr = (GmPair * max(1, len(pairs)))()
     for k, pr in enumerate(pairs):
         arr[k] = pr if isinstance(pr, GmPair) else make_pair(pr.a, pr.b, pr.F, pr.d, pr.p, pr.q)
@@ -277,6 +305,11 @@ def coarse_opts(eta_pct: int = 20, first_pct: int = 10, min_features: int = 1000
 
 
 def _coarse_pairs_array(pairs):
+    if isinstance(pairs, ctypes.Array):
+        return pairs
+    if pairs and not any(isinstance(pr, GmPair) for pr in pairs):   # F and the band are not used
+        return make_pairs([pr.a for pr in pairs], [pr.b for pr in pairs], np.eye(3), float("inf"),
+                          [pr.p for pr in pairs], [pr.q for pr in pairs])
     arr = (GmPair * max(1, len(pairs)))()
     for k, pr in enumerate(pairs):
         arr[k] = pr if isinstance(pr, GmPair) else make_pair(pr.a, pr.b, np.eye(3), float("inf"), pr.p, pr.q)
@@ -311,7 +344,7 @@ def gm_match_coarse(ctx, pairs, pair_off, matches, cap: int, second=None, opts=N
     pm, _, k2 = _ptr(matches)
     ps, _, k3 = _ptr(second)
     n = c_i64(0)
-    st = load_library().gm_match_coarse(ctx, len(pairs), arr, opts, po, pm, cap, ctypes.byref(n), ps)
+    st = load_library().gm_match_coarse(ctx, _n_pairs(pairs), arr, opts, po, pm, cap, ctypes.byref(n), ps)
     if st == GM_ERR_NOMEM:
         err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
         err.required = n.value
@@ -332,7 +365,7 @@ def gm_match_pairs(ctx, pairs, pair_off, matches, cap: int) -> int:
     po, _, k1 = _ptr(pair_off)
     pm, _, k2 = _ptr(matches)
     n = c_i64(0)
-    st = load_library().gm_match_pairs(ctx, len(pairs), arr, po, pm, cap, ctypes.byref(n))
+    st = load_library().gm_match_pairs(ctx, _n_pairs(pairs), arr, po, pm, cap, ctypes.byref(n))
     if st == GM_ERR_NOMEM:
         err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
         err.required = n.value
@@ -376,7 +409,7 @@ def gm_band_candidates_static(ctx, pair, query_begin: int, query_count: int, can
 def gm_autotune(ctx, pairs, repeats: int = 3) -> dict:
     arr = _pairs_array(pairs)
     r = GmTuneResult()
-    _check(load_library().gm_autotune(ctx, len(pairs), arr, repeats, ctypes.byref(r)), ctx)
+    _check(load_library().gm_autotune(ctx, _n_pairs(pairs), arr, repeats, ctypes.byref(r)), ctx)
     return r.as_dict()
 
 
