@@ -11,8 +11,8 @@ What it computes for a pair (A, B, F, d, p/q) with cell half-size h = d * cell_s
    (ox, oy); that cell's centre is (ox + (2i + 1) h, oy + (2j + 1) h).
 2. Lines and groups (Sec. 6.2.2, App. A Step 2): every query's epipolar line l = F (x, y, 1) meets B's border
    [0, W] x [0, H] in a chord; its two ends, as positions t1 <= t2 along the border, are the query's key.  Queries
-   sorted by (t1, t2, index) form groups: a query starts a new group when its t1 or t2 differs from the previous
-   query's by more than 2 px.  Queries whose line misses the image each form their own group.
+   sorted by (t1, t2, index) form groups: a query starts a new group when its t1 or t2 differs from those of the
+   group's first query by more than 2 px.  Queries whose line misses the image each form their own group.
 3. Candidates (Eqs. 4-5, App. A Step 3): on the chord of the group's first query, with K = ceil(|AB| / h), the
    K + 1 equidistant points x_k = (k x_A + (K - k) x_B) / K (k = 0 .. K); for each, the cell with the nearest centre
    among its four cells (ties: the lower grid); C' = every point of B binned into a chosen cell (a set).
@@ -25,7 +25,10 @@ Readings (the paper is garbled or silent here):
   a chord of length 0 gives the single point A;
 - chord ends are ordered by the border position t (counter-clockwise from (0, 0): bottom edge t = x, right edge
   W + y, top edge 2W + H - x, left edge 2W + 2H - y; no wrap-around), A = the lower t;
-- "within 2 pixels" compares t1 and t2 with the previous query in sorted order (chaining);
+- "within 2 pixels" compares t1 and t2 with the group's first query.  App. A Step 2's stencil compares with the
+  previous query, but lines through a common epipole are nearly parallel, so in a dense query set consecutive
+  lines are always closer than 2 px and that chain puts almost every query of a pair in one group; Sec. 6.2.2
+  wants every query of a group to share one line;
 - the geometry (lines, chords, keys, samples, cells) is FP32 with every operation rounded in the order written
   here (no fused multiply-add); the descriptor distances are exact integers;
 - the group's candidate set comes from its first query's line; the 2-NN over C' is exact (no Kd-tree).
@@ -164,13 +167,13 @@ def groups(F, xyA, W, H):
             keyed.append((float(e[0][2]), float(e[1][2]), q))
     keyed.sort()
     out = []
-    prev = None
+    lead = None
     for t1, t2, q in keyed:
-        if prev is None or abs(f32(f32(t1) - f32(prev[0]))) > two or abs(f32(f32(t2) - f32(prev[1]))) > two:
+        if lead is None or abs(f32(f32(t1) - f32(lead[0]))) > two or abs(f32(f32(t2) - f32(lead[1]))) > two:
             out.append([q])
+            lead = (t1, t2)
         else:
             out[-1].append(q)
-        prev = (t1, t2)
     out += [[q] for q in lineless]
     return out, ends
 

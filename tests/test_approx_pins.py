@@ -47,8 +47,8 @@ def test_groups_of_a_rectified_pair():
     ys = [30.0, 10.0, 20.5, 13.0, 11.5, 20.0, 500.0]    # the last line misses B (H = 100)
     xy = np.stack([np.full(len(ys), 3.0), ys], 1).astype(np.float32)
     gs, _ = oa.groups(RECTIFIED, xy, 120.0, 100.0)
-    # sorted by t1 = W + y: 10, 11.5, 13 chain (steps of 1.5), 20 / 20.5 chain, 30 alone; the lineless query last
-    assert gs == [[1, 4, 3], [5, 2], [0], [6]]
+    # sorted by t1 = W + y: 10 leads 11.5 (1.5 px) but not 13 (3 px); 20 leads 20.5; 30 alone; the lineless one last
+    assert gs == [[1, 4], [3], [5, 2], [0], [6]]
 
 
 def _segment_distance(q, a, b):
