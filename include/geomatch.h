@@ -14,7 +14,8 @@
  * Image B's features are binned into a uniform grid (App. A Step 1); each band is walked cell by cell and every
  * visited point gets an exact membership decision (FP32 with a proven error margin, FP64 for points inside the
  * margin), so C_i is exactly the set of Eq. 2 -- not the approximate set C' of the paper's overlapping grids.
- * Results are bit-identical to a plain FP64 evaluation of the definition above.
+ * Results are bit-identical to a plain FP64 evaluation of the definition above.  The paper's approximate search
+ * itself (overlapping grids, centre-most cells, one C' per group of nearly equal lines) is gm_match_pairs_approx.
  *
  * Conventions for every entry point
  *   - Every function returns a gm_status; nothing throws across the ABI.  gm_last_error() gives the message of
@@ -239,6 +240,31 @@ GM_API gm_status gm_coarse_selection(gm_ctx *ctx, int32_t image_id, const gm_coa
 GM_API gm_status gm_match_coarse(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, const gm_coarse_opts *opts,
                                  int64_t *pair_off, int32_t *matches, int64_t cap, int64_t *n_written,
                                  int32_t *second);
+
+/* Counters of one gm_match_pairs_approx call. */
+typedef struct {
+    int64_t n_groups;       /* dual-line groups over all pairs (each shares one candidate set) */
+    int64_t n_candidates;   /* sum over queries of |C'| */
+    int64_t n_cells;        /* chord samples, i.e. centre-most cells looked up (sum over groups of K + 1) */
+} gm_approx_stats;
+
+/* The paper's approximate geometry-aware matching (Sec. 6.2.1 grid-based search, Sec. 6.2.2 dual-line groups,
+ * App. A Steps 1-4), next to the exact gm_match_pairs for its recall / speed trade-off.  For a pair with cell
+ * half-size h = band_px * cell_scale (FP32):
+ *   - B's keypoints are binned into four grids of 2h x 2h cells offset by (0, 0), (h, 0), (0, h), (h, h);
+ *   - every query's epipolar line meets B's border [0, W] x [0, H] in a chord whose ends, as positions t1 <= t2
+ *     along the border (counter-clockwise from (0, 0)), key the query; queries sorted by (t1, t2, index) form
+ *     groups that start wherever t1 or t2 differs from the group's first query by more than 2 px; a query whose
+ *     line misses B is a group of its own with no candidates;
+ *   - a group's candidate set C' is every keypoint of B in the centre-most of the four cells around each of the
+ *     K + 1 equidistant points (K = ceil(|AB| / h)) of its first query's chord;
+ *   - every query of the group takes exact squared distances to C', nearest and second-nearest, and the integer
+ *     ratio test q^2 D1 < p^2 D2 with |C'| >= 2.
+ * All geometry is FP32, each operation rounded in a fixed order (no fused multiply-add).  Output layout, cap and
+ * errors as gm_match_pairs; band_px must be finite and h >= 0.5 px; stats may be NULL. */
+GM_API gm_status gm_match_pairs_approx(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, float cell_scale,
+                                       int64_t *pair_off, int32_t *matches, int64_t cap, int64_t *n_written,
+                                       gm_approx_stats *stats);
 
 /* Autotuner (a tuning aid; the paper has no counterpart).  Times gm_match_pairs on this batch for every distance
  * path (tc; mma with 16- and 32-query groups; simt) and grid cell size (4, 8, 16 px), `repeats` timed runs each

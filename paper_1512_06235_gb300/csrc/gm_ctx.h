@@ -125,6 +125,7 @@ struct gm_ctx {
     gm::DevBuf d_stage, d_work, d_bad, d_bitmap, d_tune, d_btab, d_pairs, d_pairs_out, d_tracks, d_tri, d_tri_out;
     gm::Workspace ws2;              // second batch of the coarse stage's preemptive schedule (shares ws's stream)
     gm::DevBuf d_coarse_tab, d_coarse_stage, d_coarse_out;
+    gm::DevBuf d_approx;            // gm_match_pairs_approx: every array of one call
     std::unordered_map<int32_t, gm::CoarseViews> coarse;   // by caller's image id
     uint64_t image_gen = 0;
     int32_t next_internal_id = -1;

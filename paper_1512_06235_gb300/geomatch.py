@@ -67,6 +67,13 @@ class GmCoarseOpts(ctypes.Structure):
     _fields_ = [("eta_pct", c_i32), ("first_pct", c_i32), ("min_features", c_i32), ("min_matches", c_i32)]
 
 
+class GmApproxStats(ctypes.Structure):
+    _fields_ = [("n_groups", c_i64), ("n_candidates", c_i64), ("n_cells", c_i64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GmTuneResult(ctypes.Structure):
     _fields_ = [("path", c_i32), ("mma_group", c_i32), ("cell_px", c_i32), ("ms", ctypes.c_float),
                 ("from_cache", c_i32)]
@@ -97,6 +104,8 @@ _SIGNATURES = {
                                           ctypes.POINTER(c_i64)]),
     "gm_images_put": (c_i32, [c_p, c_i32, ctypes.POINTER(GmImage), c_i32]),
     "gm_merge_tracks": (c_i32, [c_p, c_i64, c_i64, c_p, c_p, ctypes.POINTER(c_i64)]),
+    "gm_match_pairs_approx": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), ctypes.c_float, c_p, c_p, c_i64,
+                                      ctypes.POINTER(c_i64), ctypes.POINTER(GmApproxStats)]),
     "gm_coarse_prepare": (c_i32, [c_p, c_i32, c_p, ctypes.POINTER(GmCoarseOpts)]),
     "gm_coarse_selection": (c_i32, [c_p, c_i32, ctypes.POINTER(GmCoarseOpts), c_p, c_p, c_p, c_i32, c_p]),
     "gm_match_coarse": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), ctypes.POINTER(GmCoarseOpts), c_p, c_p, c_i64,
@@ -354,6 +363,24 @@ def gm_match_coarse(ctx, pairs, pair_off, matches, cap: int, second=None, opts=N
     return n.value
 
 
+def gm_match_pairs_approx(ctx, pairs, pair_off, matches, cap: int, cell_scale: float = 1.0):
+    """The paper's approximate matching into caller buffers (numpy or torch CUDA); returns (n_written, stats)."""
+    arr = _pairs_array(pairs)
+    po, _, k1 = _ptr(pair_off)
+    pm, _, k2 = _ptr(matches)
+    n = c_i64(0)
+    stats = GmApproxStats()
+    st = load_library().gm_match_pairs_approx(ctx, _n_pairs(pairs), arr, cell_scale, po, pm, cap, ctypes.byref(n),
+                                              ctypes.byref(stats))
+    if st == GM_ERR_NOMEM:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = n.value
+        raise err
+    _check(st, ctx)
+    del k1, k2
+    return n.value, stats.as_dict()
+
+
 def gm_image_evict(ctx, image_id: int):
     _check(load_library().gm_image_evict(ctx, image_id), ctx)
 
@@ -561,6 +588,14 @@ class Context:
         labels = np.empty(n_nodes, np.int64)
         nt = gm_merge_tracks(self.h, n_nodes, np.ascontiguousarray(edges, np.int64).reshape(-1, 2), labels)
         return labels, nt
+
+    def match_pairs_approx(self, pairs, cell_scale: float = 1.0):
+        """Approximate matching (Sec. 6.2.1-6.2.2): (pair_off int64[P+1], matches int32[M,2], stats dict)."""
+        cap = sum(self.n.get(p.img_a if isinstance(p, GmPair) else p.a, 0) for p in pairs)
+        off = np.empty(_n_pairs(pairs) + 1, np.int64)
+        m = np.empty((max(cap, 1), 2), np.int32)
+        n, stats = gm_match_pairs_approx(self.h, pairs, off, m, cap, cell_scale)
+        return off, m[:n], stats
 
     def coarse_selection(self, image_id: int, opts=None):
         """(q1, q2, t) ascending feature indices of the image's coarse selection (Sec. 4)."""
