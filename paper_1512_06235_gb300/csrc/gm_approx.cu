@@ -34,7 +34,8 @@ namespace {
 struct ApproxJob {              // Step 1: grids of one target image for one cell half-size
     const float2 *xy;           // B's points, column-major order
     int32_t n;
-    float h;
+    float h, h2, inv_h2;        // cell half-size, cell size 2h, and 1 / 2h when 2h is a power of two
+    int32_t pow2;               // 2h is a power of two: dividing by it is the exact scaling by inv_h2
     int32_t nx, ny;             // cells per grid row / column (cell index + 1)
     int64_t cell_base;          // first of this job's 4 * nx * ny cells
 };
@@ -79,35 +80,36 @@ struct Chord {
     bool ok;
 };
 
-// ends of the line inside [0, W] x [0, H], the lower border position first
-__device__ Chord chord32(float a, float b, float c, float W, float H)
+// ends of the line inside [0, W] x [0, H], the lower border position first (candidates in the order left, right,
+// bottom, top edge; the first of equal positions wins)
+__device__ __forceinline__ void chord_add(Chord &r, float x, float y, float W, float H)
 {
-    float cx[4], cy[4];
-    int n = 0;
+    const float t = border_t(x, y, W, H);
+    if (!r.ok) {
+        r.xa = r.xb = x; r.ya = r.yb = y; r.ta = r.tb = t;
+        r.ok = true;
+        return;
+    }
+    if (t < r.ta) { r.xa = x; r.ya = y; r.ta = t; }
+    if (t > r.tb) { r.xb = x; r.yb = y; r.tb = t; }
+}
+
+__device__ __forceinline__ Chord chord32(float a, float b, float c, float W, float H)
+{
+    Chord r{};
+    r.ok = false;
     if (b != 0.0f) {
         const float y0 = __fdiv_rn(-c, b);
-        if (0.0f <= y0 && y0 <= H) { cx[n] = 0.0f; cy[n] = y0; ++n; }
+        if (0.0f <= y0 && y0 <= H) chord_add(r, 0.0f, y0, W, H);
         const float yW = __fdiv_rn(-__fadd_rn(__fmul_rn(a, W), c), b);
-        if (0.0f <= yW && yW <= H) { cx[n] = W; cy[n] = yW; ++n; }
+        if (0.0f <= yW && yW <= H) chord_add(r, W, yW, W, H);
     }
     if (a != 0.0f) {
         const float x0 = __fdiv_rn(-c, a);
-        if (0.0f <= x0 && x0 <= W) { cx[n] = x0; cy[n] = 0.0f; ++n; }
+        if (0.0f <= x0 && x0 <= W) chord_add(r, x0, 0.0f, W, H);
         const float xH = __fdiv_rn(-__fadd_rn(__fmul_rn(b, H), c), a);
-        if (0.0f <= xH && xH <= W) { cx[n] = xH; cy[n] = H; ++n; }
+        if (0.0f <= xH && xH <= W) chord_add(r, xH, H, W, H);
     }
-    Chord r{};
-    r.ok = n > 0;
-    if (!n) return r;
-    int lo = 0, hi = 0;
-    float tlo = border_t(cx[0], cy[0], W, H), thi = tlo;
-    for (int k = 1; k < n; ++k) {
-        const float t = border_t(cx[k], cy[k], W, H);
-        if (t < tlo) { tlo = t; lo = k; }
-        if (t > thi) { thi = t; hi = k; }
-    }
-    r.xa = cx[lo]; r.ya = cy[lo]; r.ta = tlo;
-    r.xb = cx[hi]; r.yb = cy[hi]; r.tb = thi;
     return r;
 }
 
@@ -126,12 +128,17 @@ __device__ __forceinline__ void sample(const Chord &e, int K, int k, float &x, f
     y = __fdiv_rn(__fadd_rn(__fmul_rn(kf, e.ya), __fmul_rn(rk, e.yb)), Kf);
 }
 
-__device__ __forceinline__ void cell_of(int g, float x, float y, float h, int &i, int &j)
+// v / 2h, correctly rounded: when 2h is a power of two the product with its exact reciprocal is the same value
+__device__ __forceinline__ float div_h2(const ApproxJob &J, float v)
 {
-    const float h2 = __fadd_rn(h, h);
-    const float ox = (g & 1) ? h : 0.0f, oy = (g >> 1) ? h : 0.0f;
-    i = (int)floorf(__fdiv_rn(__fsub_rn(x, ox), h2));
-    j = (int)floorf(__fdiv_rn(__fsub_rn(y, oy), h2));
+    return J.pow2 ? __fmul_rn(v, J.inv_h2) : __fdiv_rn(v, J.h2);
+}
+
+__device__ __forceinline__ void cell_of(const ApproxJob &J, int g, float x, float y, int &i, int &j)
+{
+    const float ox = (g & 1) ? J.h : 0.0f, oy = (g >> 1) ? J.h : 0.0f;
+    i = (int)floorf(div_h2(J, __fsub_rn(x, ox)));
+    j = (int)floorf(div_h2(J, __fsub_rn(y, oy)));
 }
 
 // linear cell index of (g, i, j) in a job, or -1 outside the job's grids
@@ -141,23 +148,31 @@ __device__ __forceinline__ int64_t cell_index(const ApproxJob &J, int g, int i, 
     return J.cell_base + ((int64_t)g * J.ny + (j + 1)) * J.nx + (i + 1);
 }
 
+// The grids share their x offsets pairwise (grids 0, 2: 0; grids 1, 3: h) and their y offsets likewise, so the two
+// cell columns, the two cell rows and their squared centre offsets are computed once each.
 __device__ __forceinline__ int64_t chosen_cell(const ApproxJob &J, float px, float py)
 {
     const float h = J.h;
+    int ci[2], cj[2];
+    float ex[2], ey[2];
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        const float ox = o ? h : 0.0f;
+        ci[o] = (int)floorf(div_h2(J, __fsub_rn(px, ox)));
+        cj[o] = (int)floorf(div_h2(J, __fsub_rn(py, ox)));
+        const float dx = __fsub_rn(px, __fadd_rn(ox, __fmul_rn((float)(2 * ci[o] + 1), h)));
+        const float dy = __fsub_rn(py, __fadd_rn(ox, __fmul_rn((float)(2 * cj[o] + 1), h)));
+        ex[o] = __fmul_rn(dx, dx);
+        ey[o] = __fmul_rn(dy, dy);
+    }
     float best = 0.0f;
-    int bg = 0, bi = 0, bj = 0;
+    int bg = 0;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        int i, j;
-        cell_of(g, px, py, h, i, j);
-        const float ox = (g & 1) ? h : 0.0f, oy = (g >> 1) ? h : 0.0f;
-        const float cx = __fadd_rn(ox, __fmul_rn((float)(2 * i + 1), h));
-        const float cy = __fadd_rn(oy, __fmul_rn((float)(2 * j + 1), h));
-        const float dx = __fsub_rn(px, cx), dy = __fsub_rn(py, cy);
-        const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-        if (g == 0 || d2 < best) { best = d2; bg = g; bi = i; bj = j; }
+        const float d2 = __fadd_rn(ex[g & 1], ey[g >> 1]);
+        if (g == 0 || d2 < best) { best = d2; bg = g; }
     }
-    return cell_index(J, bg, bi, bj);
+    return cell_index(J, bg, ci[bg & 1], cj[bg >> 1]);
 }
 
 template <typename T>
@@ -185,7 +200,7 @@ __global__ void bin_count_kernel(const ApproxJob *__restrict__ jobs, const int64
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             int i, j;
-            cell_of(g, p.x, p.y, J.h, i, j);
+            cell_of(J, g, p.x, p.y, i, j);
             const int64_t c = cell_index(J, g, i, j);
             if (c < 0) atomicAdd(&ctr->bad, 1ull);
             else atomicAdd(&cnt[c], 1);
@@ -206,7 +221,7 @@ __global__ void bin_scatter_kernel(const ApproxJob *__restrict__ jobs, const int
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             int i, j;
-            cell_of(g, p.x, p.y, J.h, i, j);
+            cell_of(J, g, p.x, p.y, i, j);
             const int64_t c = cell_index(J, g, i, j);
             if (c >= 0) members[off[c] + atomicAdd(&cursor[c], 1)] = pos;
         }
@@ -341,8 +356,10 @@ __global__ void group_start_kernel(const int32_t *__restrict__ flag, const int32
 // ---------------------------------------------------------------- Steps 3-4: one warp per group
 
 constexpr int kQChunk = 4;           // queries of a group scored together
+constexpr int kListCap = 1024;       // compacted candidate positions per round (32 bitmap words)
+constexpr int kMatchThreads = 128;
 
-__global__ void approx_match_kernel(const ApproxPair *__restrict__ P, const int64_t *__restrict__ qoff, int n_pairs,
+__global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const ApproxPair *__restrict__ P, const int64_t *__restrict__ qoff, int n_pairs,
                                     const ApproxJob *__restrict__ jobs, const ImageDev *__restrict__ imgs,
                                     const int32_t *__restrict__ cell_off, const int32_t *__restrict__ members,
                                     const int32_t *__restrict__ order, const uint8_t *__restrict__ has,
@@ -353,7 +370,7 @@ __global__ void approx_match_kernel(const ApproxPair *__restrict__ P, const int6
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int64_t g = (int64_t)blockIdx.x * wpb + wib;
     if (g >= G) return;
-    uint32_t *bm = reinterpret_cast<uint32_t *>(sm + (size_t)wib * ((size_t)words * 4 + kQChunk * kDim));
+    uint32_t *bm = reinterpret_cast<uint32_t *>(sm + (size_t)wib * ((size_t)words * 4 + kQChunk * kDim + 4 * kListCap));
     int8_t *qd = reinterpret_cast<int8_t *>(bm + words);
     const int32_t s0 = gstart[g], s1 = gstart[g + 1];
     const int k = upper_index(qoff, n_pairs, (int64_t)s0);
@@ -390,7 +407,9 @@ __global__ void approx_match_kernel(const ApproxPair *__restrict__ P, const int6
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if (lane == 0) atomicAdd(&ctr->candidates, (unsigned long long)cnt * (unsigned long long)(s1 - s0));
-    // Step 4: exact distances from each query of the group to C', top-2, ratio test
+    // Step 4: exact distances from each query of the group to C', top-2, ratio test.  The bitmap is compacted into a
+    // list (at most kListCap positions at a time) so that the candidates spread evenly over the lanes.
+    int32_t *list = reinterpret_cast<int32_t *>(qd + kQChunk * kDim);
     for (int32_t c0 = s0; c0 < s1; c0 += kQChunk) {
         const int nq = min(kQChunk, s1 - c0);
         int32_t qpos[kQChunk], qn[kQChunk];
@@ -409,11 +428,31 @@ __global__ void approx_match_kernel(const ApproxPair *__restrict__ P, const int6
         int D1[kQChunk], D2[kQChunk], J1[kQChunk];
 #pragma unroll
         for (int t = 0; t < kQChunk; ++t) { D1[t] = INT_MAX; D2[t] = INT_MAX; J1[t] = INT_MAX; }
-        for (int32_t w = lane; w < nw; w += 32) {
-            uint32_t bits = bm[w];
-            while (bits) {
-                const int32_t j = (w << 5) + __ffs(bits) - 1;
-                bits &= bits - 1u;
+        for (int32_t w0 = 0; w0 < nw;) {
+            int32_t nl = 0;
+            while (w0 < nw) {   // 32 words per round hold at most kListCap bits, so every round fits an empty list
+                const int32_t w = w0 + lane;
+                uint32_t bits = w < nw ? bm[w] : 0u;
+                const int c = __popc(bits);
+                int inc = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                const int tot = __shfl_sync(0xffffffffu, inc, 31);
+                if (nl + tot > kListCap) break;
+                int at = nl + inc - c;
+                while (bits) {
+                    list[at++] = (w << 5) + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                }
+                nl += tot;
+                w0 += 32;
+            }
+            __syncwarp();
+            for (int32_t e = lane; e < nl; e += 32) {
+                const int32_t j = list[e];
                 const int4 *brow = reinterpret_cast<const int4 *>(B.desc + (size_t)j * kDim);
                 int dot[kQChunk] = {};
 #pragma unroll
@@ -436,6 +475,7 @@ __global__ void approx_match_kernel(const ApproxPair *__restrict__ P, const int6
                     else if (D < D2[t]) D2[t] = D;
                 }
             }
+            __syncwarp();
         }
         // merge the lanes' top-2 lists
 #pragma unroll
@@ -539,6 +579,10 @@ gm_status gm_match_pairs_approx(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pai
             J.xy = B.xy;
             J.n = B.n;
             J.h = h;
+            J.h2 = h + h;   // exact: a doubling
+            int ex2 = 0;
+            J.pow2 = std::frexp(J.h2, &ex2) == 0.5f;
+            J.inv_h2 = J.pow2 ? std::ldexp(1.0f, 1 - ex2) : 0.0f;
             J.nx = (int32_t)std::floor((double)B.width / (2.0 * h)) + 3;   // cell index -1 .. floor(W / 2h) + 1
             J.ny = (int32_t)std::floor((double)B.height / (2.0 * h)) + 3;
             J.cell_base = cells;
@@ -631,7 +675,7 @@ gm_status gm_match_pairs_approx(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pai
     GM_CUDA_A(cudaStreamSynchronize(s));
     // Steps 3-4
     const int32_t words = ((max_nb + 31) / 32 + 3) & ~3;   // a multiple of 4 words keeps the query rows 16-byte aligned
-    const size_t per_warp = (size_t)words * 4 + kQChunk * kDim;
+    const size_t per_warp = (size_t)words * 4 + kQChunk * kDim + 4 * kListCap;
     int wpb = 4;
     while (wpb > 1 && per_warp * wpb > 200 * 1024) --wpb;
     if (per_warp * wpb > 200 * 1024) return fail(GM_ERR_INVALID, "%s: target image too large for the bitmap", fn);
