@@ -858,7 +858,7 @@ def main():
     if not args.no_graph:
         e2e_ctx.set_option(gm.GM_OPT_GRAPH, 1)
 
-    batch = [(k, w, h, xy, scl, ds) for k, (w, h, xy, scl, ds) in enumerate(pinned)]
+    batch = gm.make_images([(k, w, h, xy, scl, ds) for k, (w, h, xy, scl, ds) in enumerate(pinned)])
 
     def e2e_step():   # all images of the step in one gm_images_put call, then the batch
         gm.gm_images_put(e2e_ctx.h, batch)

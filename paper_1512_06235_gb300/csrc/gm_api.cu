@@ -837,26 +837,49 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             img->bytes = L[k].tot;
             ctx->bytes_images += L[k].tot;
         }
+        // the TMA descriptors depend only on the descriptor rows, the records and n: a re-put into the same block
+        // with as many keypoints keeps them
+        const bool same_maps = g.n > 0 && img->dev.n == dev[k].n && img->dev.desc_h == dev[k].desc_h &&
+                               img->dev.rec == dev[k].rec;
         img->dev = dev[k];
         img->gen = ++ctx->image_gen;
         img->scale = reinterpret_cast<const float *>(static_cast<char *>(img->block) + L[k].offs[10]);
         img->has_scale = g.n > 0 && g.scale != nullptr;
-        TmaMaps maps;
-        std::memset(&maps, 0, sizeof(maps));
-        if (g.n > 0 && (st = encode_maps(img->dev, maps)) != GM_OK) return st;
-        img->maps = maps;
+        if (!same_maps) {
+            TmaMaps maps;
+            std::memset(&maps, 0, sizeof(maps));
+            if (g.n > 0 && (st = encode_maps(img->dev, maps)) != GM_OK) return st;
+            img->maps = maps;
+        }
     }
     // 5. device tables (grow keeps old entries), one copy each of every slot's entry
     if ((st = grow_table(ctx, ctx->d_imgs, sizeof(ImageDev) * ctx->slots.size(), 4096, s, "image")) != GM_OK) return st;
     if ((st = grow_table(ctx, ctx->d_maps, sizeof(TmaMaps) * ctx->slots.size(), sizeof(TmaMaps) * 16, s, "TMA descriptor"))
         != GM_OK)
         return st;
-    for (int32_t k = 0; k < count; ++k) {
-        const ImageSlot *img = ctx->images.at(imgs[k].image_id);
-        GM_CUDA(cudaMemcpyAsync(static_cast<ImageDev *>(ctx->d_imgs.p) + img->slot, &img->dev, sizeof(ImageDev),
+    std::vector<ImageDev> tab_dev;
+    std::vector<TmaMaps> tab_maps;
+    if (count >= 8) {   // many images: both whole tables in two copies instead of two per image
+        tab_dev.assign(ctx->slots.size(), ImageDev{});
+        tab_maps.resize(ctx->slots.size());
+        std::memset(tab_maps.data(), 0, sizeof(TmaMaps) * tab_maps.size());
+        for (size_t q = 0; q < ctx->slots.size(); ++q)
+            if (ctx->slots[q]) {
+                tab_dev[q] = ctx->slots[q]->dev;
+                tab_maps[q] = ctx->slots[q]->maps;
+            }
+        GM_CUDA(cudaMemcpyAsync(ctx->d_imgs.p, tab_dev.data(), sizeof(ImageDev) * tab_dev.size(), cudaMemcpyHostToDevice,
+                                s));
+        GM_CUDA(cudaMemcpyAsync(ctx->d_maps.p, tab_maps.data(), sizeof(TmaMaps) * tab_maps.size(),
                                 cudaMemcpyHostToDevice, s));
-        GM_CUDA(cudaMemcpyAsync(static_cast<TmaMaps *>(ctx->d_maps.p) + img->slot, &img->maps, sizeof(TmaMaps),
-                                cudaMemcpyHostToDevice, s));
+    } else {
+        for (int32_t k = 0; k < count; ++k) {
+            const ImageSlot *img = ctx->images.at(imgs[k].image_id);
+            GM_CUDA(cudaMemcpyAsync(static_cast<ImageDev *>(ctx->d_imgs.p) + img->slot, &img->dev, sizeof(ImageDev),
+                                    cudaMemcpyHostToDevice, s));
+            GM_CUDA(cudaMemcpyAsync(static_cast<TmaMaps *>(ctx->d_maps.p) + img->slot, &img->maps, sizeof(TmaMaps),
+                                    cudaMemcpyHostToDevice, s));
+        }
     }
     // the staged inputs and the table entries are read asynchronously: finish before returning
     GM_CUDA(cudaStreamSynchronize(s));

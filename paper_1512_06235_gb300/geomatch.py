@@ -239,26 +239,40 @@ def gm_image_put(ctx, image_id: int, width: int, height: int, xy, scale, desc):
     del k1, k2, k3
 
 
-def gm_images_put(ctx, images):
+class ImageBatch:
+    """A prebuilt gm_image array (the arrays' addresses, sizes and memory kind) for gm_images_put.  The arrays must
+    stay alive and keep their addresses while the batch is used; their contents may change between calls."""
+
+    def __init__(self, images):
+        self.n = len(images)
+        self.arr = (GmImage * max(1, self.n))()
+        self.keep, devs = [], set()
+        for k, (iid, w, h, xy, scale, desc) in enumerate(images):
+            pxy, dxy, k1 = _ptr(xy)
+            psc, dsc, k2 = _ptr(scale)
+            pds, dds, k3 = _ptr(desc)
+            self.keep += [k1, k2, k3]
+            n = int(xy.shape[0])
+            if n:
+                devs.add(dxy)
+                devs.add(dds)
+                if scale is not None:
+                    devs.add(dsc)
+            self.arr[k] = GmImage(iid, w, h, n, pxy, psc, pds)
+        if len(devs) > 1:
+            raise ValueError("gm_images_put: all arrays must be host memory or all device memory")
+        self.on_device = devs.pop() if devs else 0
+
+
+def make_images(images) -> ImageBatch:
     """images: list of (image_id, width, height, xy, scale, desc), all host (numpy / pinned) or all device tensors."""
-    arr = (GmImage * max(1, len(images)))()
-    keep, devs = [], set()
-    for k, (iid, w, h, xy, scale, desc) in enumerate(images):
-        pxy, dxy, k1 = _ptr(xy)
-        psc, dsc, k2 = _ptr(scale)
-        pds, dds, k3 = _ptr(desc)
-        keep += [k1, k2, k3]
-        n = int(xy.shape[0])
-        if n:
-            devs.add(dxy)
-            devs.add(dds)
-            if scale is not None:
-                devs.add(dsc)
-        arr[k] = GmImage(iid, w, h, n, pxy, psc, pds)
-    if len(devs) > 1:
-        raise ValueError("gm_images_put: all arrays must be host memory or all device memory")
-    _check(load_library().gm_images_put(ctx, len(images), arr, devs.pop() if devs else 0), ctx)
-    del keep
+    return ImageBatch(images)
+
+
+def gm_images_put(ctx, images):
+    """images: an ImageBatch, or a list of (image_id, width, height, xy, scale, desc) (all host or all device)."""
+    b = images if isinstance(images, ImageBatch) else ImageBatch(images)
+    _check(load_library().gm_images_put(ctx, b.n, b.arr, b.on_device), ctx)
 
 
 def gm_select_pairs(ctx, n_cams: int, point_off, point_cams, threshold: int, top_k: int, pairs, cap: int) -> int:
