@@ -139,6 +139,39 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked host memory that the device may read directly (cudaMallocHost /
+// cudaHostAlloc / mapped registrations), or nullptr for any other pointer (pageable memory is always copied).
+const void *mapped_host_ptr(const void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+namespace {
+
+struct CopySeg {
+    const void *src;
+    void *dst;
+    int64_t words;              // 4-byte words
+};
+
+// Copies of 4-byte-aligned segments (blockIdx.y: segment), e.g. from mapped host memory into image blocks.
+__global__ void copy_segments_kernel(const CopySeg *__restrict__ segs)
+{
+    const CopySeg g = segs[blockIdx.y];
+    const uint32_t *src = static_cast<const uint32_t *>(g.src);
+    uint32_t *dst = static_cast<uint32_t *>(g.dst);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.words; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+}  // namespace
+
 gm_status prepare_pair(gm_ctx *ctx, const gm_pair &pr, int64_t k, PairDev &pd, bool internal)
 {
     if (!internal && (pr.img_a < 0 || pr.img_b < 0))
@@ -472,7 +505,10 @@ gm_status gm_create(const gm_config *cfg, gm_ctx **out)
         ctx->own_stream = true;
     }
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
-    if (workspace_init(ctx->ws, ctx->stream) != GM_OK || workspace_init(ctx->ws2, ctx->ws.stream) != GM_OK) {
+    if (workspace_init(ctx->ws, ctx->stream) != GM_OK || workspace_init(ctx->ws2, ctx->ws.stream) != GM_OK ||
+        cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_desc, cudaEventDisableTiming) != cudaSuccess) {
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
         return GM_ERR_CUDA;
@@ -490,6 +526,7 @@ gm_status gm_destroy(gm_ctx *ctx)
         ctx->server = nullptr;
     }
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
     for (auto &kv : ctx->images) {
         cudaFree(kv.second->block);
         delete kv.second;
@@ -501,8 +538,11 @@ gm_status gm_destroy(gm_ctx *ctx)
     workspace_free(ctx, ctx->ws);
     for (DevBuf *b : {&ctx->d_imgs, &ctx->d_maps, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap, &ctx->d_tune,
                       &ctx->d_btab, &ctx->d_pairs, &ctx->d_pairs_out, &ctx->d_tracks, &ctx->d_tri, &ctx->d_tri_out,
-                      &ctx->d_coarse_tab, &ctx->d_coarse_stage, &ctx->d_coarse_out, &ctx->d_approx})
+                      &ctx->d_coarse_tab, &ctx->d_coarse_stage, &ctx->d_coarse_out, &ctx->d_approx, &ctx->d_segs})
         free_dev(ctx, *b);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->ev_stage) cudaEventDestroy(ctx->ev_stage);
+    if (ctx->ev_desc) cudaEventDestroy(ctx->ev_desc);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return GM_OK;
@@ -699,8 +739,8 @@ gm_status bucket_batches(gm_ctx *ctx, int32_t count, const gm_image *imgs, const
         int32_t *work = static_cast<int32_t *>(ctx->d_work.p);
         GM_CUDA(launch_bucket_batch_count(dJ, dkp, K, nk, work, ck, d_bad + k0, s));
         if (dev) GM_CUDA(launch_bucket_batch_build(dJ, dkp, dcp, drp, K, nk, work, ck, work + ck, work + 2 * ck + 1, s));
-        // the table is read by the kernels above: the next sub-batch may overwrite it only after them
-        if (k1 < count) GM_CUDA(cudaStreamSynchronize(s));
+        // the next sub-batch's table and work arrays are written in stream order, after the kernels above (a
+        // reallocation goes through cudaFree, which waits for the device)
         k0 = k1;
     }
     return GM_OK;
@@ -749,6 +789,16 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
     std::vector<const float2 *> raw_xy(count);
     std::vector<const uint8_t *> raw_desc(count);
     if (!on_device && (st = ensure_dev(ctx, ctx->d_stage, stage_bytes + 256)) != GM_OK) return st;
+    // coordinates go up on the stream (the keypoint check needs them); descriptors on the copy stream, so that their
+    // upload overlaps the check and is waited for only before the descriptors are binned
+    const bool side = !on_device && ctx->copy_stream;
+    if (side) {
+        // the staging area is free once earlier work on s and an earlier call's uploads (even one that failed before
+        // its binning) are done
+        GM_CUDA(cudaStreamWaitEvent(s, ctx->ev_desc, 0));
+        GM_CUDA(cudaEventRecord(ctx->ev_stage, s));
+        GM_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_stage, 0));
+    }
     {
         char *sp = static_cast<char *>(ctx->d_stage.p);
         for (int32_t k = 0; k < count; ++k) {
@@ -756,20 +806,30 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             raw_xy[k] = reinterpret_cast<const float2 *>(g.xy);
             raw_desc[k] = g.desc;
             if (on_device || g.n == 0) continue;
+            // page-locked inputs are read by the binning kernels in place (one pass over the link, no staging copy)
+            const void *mxy = mapped_host_ptr(g.xy), *mds = mxy ? mapped_host_ptr(g.desc) : nullptr;
+            if (mxy && mds && (reinterpret_cast<uintptr_t>(mxy) & 7) == 0) {
+                raw_xy[k] = static_cast<const float2 *>(mxy);
+                raw_desc[k] = static_cast<const uint8_t *>(mds);
+                continue;
+            }
             const size_t N = (size_t)g.n, xy_al = align_up(8 * N + 1, 256);
             GM_CUDA(cudaMemcpyAsync(sp, g.xy, 8 * N, cudaMemcpyHostToDevice, s));
-            GM_CUDA(cudaMemcpyAsync(sp + xy_al, g.desc, 128 * N, cudaMemcpyHostToDevice, s));
+            GM_CUDA(cudaMemcpyAsync(sp + xy_al, g.desc, 128 * N, cudaMemcpyHostToDevice, side ? ctx->copy_stream : s));
             raw_xy[k] = reinterpret_cast<const float2 *>(sp);
             raw_desc[k] = reinterpret_cast<const uint8_t *>(sp + xy_al);
             sp += xy_al + align_up(128 * N + 1, 256);
         }
     }
+    if (side) GM_CUDA(cudaEventRecord(ctx->ev_desc, ctx->copy_stream));
     if ((st = ensure_dev(ctx, ctx->d_bad, sizeof(unsigned long long) * (size_t)count)) != GM_OK) return st;
     unsigned long long *d_bad = static_cast<unsigned long long *>(ctx->d_bad.p);
     if ((st = bucket_batches(ctx, count, imgs, L, raw_xy, raw_desc, nullptr, d_bad, s)) != GM_OK) return st;
     std::vector<unsigned long long> bad(count);
     GM_CUDA(cudaMemcpyAsync(bad.data(), d_bad, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, s));
     GM_CUDA(cudaStreamSynchronize(s));
+    // everything later on s (the binning of the descriptors, or the next call's staging) comes after the upload
+    if (side) GM_CUDA(cudaStreamWaitEvent(s, ctx->ev_desc, 0));
     for (int32_t k = 0; k < count; ++k)
         if (bad[k])
             return fail(GM_ERR_INVALID, "%s: image %d: %llu keypoints outside [0,%d)x[0,%d)", fn, imgs[k].image_id,
@@ -796,10 +856,27 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
     for (int32_t k = 0; k < count; ++k) dev[k] = image_dev(L[k], block[k], imgs[k].width, imgs[k].height, imgs[k].n);
     st = bucket_batches(ctx, count, imgs, L, raw_xy, raw_desc, &dev, d_bad, s);
     cudaError_t e = cudaSuccess;
+    std::vector<CopySeg> segs;   // scales read in place from page-locked memory, all in one launch
     for (int32_t k = 0; k < count && st == GM_OK && e == cudaSuccess; ++k)
-        if (imgs[k].n > 0 && imgs[k].scale)
-            e = cudaMemcpyAsync(static_cast<char *>(block[k]) + L[k].offs[10], imgs[k].scale, 4 * (size_t)imgs[k].n,
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        if (imgs[k].n > 0 && imgs[k].scale) {
+            char *dst = static_cast<char *>(block[k]) + L[k].offs[10];
+            const void *msc = on_device ? nullptr : mapped_host_ptr(imgs[k].scale);
+            if (msc && (reinterpret_cast<uintptr_t>(msc) & 3) == 0)
+                segs.push_back(CopySeg{msc, dst, (int64_t)imgs[k].n});
+            else
+                e = cudaMemcpyAsync(dst, imgs[k].scale, 4 * (size_t)imgs[k].n,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        }
+    if (st == GM_OK && e == cudaSuccess && !segs.empty()) {
+        if ((st = ensure_dev(ctx, ctx->d_segs, sizeof(CopySeg) * segs.size())) == GM_OK) {
+            e = cudaMemcpyAsync(ctx->d_segs.p, segs.data(), sizeof(CopySeg) * segs.size(), cudaMemcpyHostToDevice, s);
+            for (size_t j0 = 0; j0 < segs.size() && e == cudaSuccess; j0 += 65535) {
+                const dim3 grid(8, (unsigned)std::min<size_t>(segs.size() - j0, 65535));
+                copy_segments_kernel<<<grid, 256, 0, s>>>(static_cast<const CopySeg *>(ctx->d_segs.p) + j0);
+                e = cudaGetLastError();
+            }
+        }
+    }
     if (st != GM_OK || e != cudaSuccess) {
         cudaStreamSynchronize(s);
         for (int32_t k = 0; k < count; ++k)

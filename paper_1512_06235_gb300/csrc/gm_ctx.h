@@ -126,6 +126,9 @@ struct gm_ctx {
     gm::Workspace ws2;              // second batch of the coarse stage's preemptive schedule (shares ws's stream)
     gm::DevBuf d_coarse_tab, d_coarse_stage, d_coarse_out;
     gm::DevBuf d_approx;            // gm_match_pairs_approx: every array of one call
+    gm::DevBuf d_segs;              // image registration: copy segments of the scales
+    cudaStream_t copy_stream = nullptr;   // image registration: descriptor uploads beside the keypoint check
+    cudaEvent_t ev_stage = nullptr, ev_desc = nullptr;
     std::unordered_map<int32_t, gm::CoarseViews> coarse;   // by caller's image id
     uint64_t image_gen = 0;
     int32_t next_internal_id = -1;

@@ -267,27 +267,33 @@ def test_autotune_and_cache(gm, facade_scene, tmp_path):
 
 
 def test_images_put_batch_equals_single_puts(gm, facade_scene):
-    """gm_images_put (host arrays, then device tensors) registers the same images as gm_image_put one by one; an
-    out-of-image keypoint in any image of a batch is rejected and leaves the registered images as they were."""
+    """gm_images_put (pageable host arrays, device tensors, page-locked host tensors read in place) registers the same
+    images as gm_image_put one by one, scales included; an out-of-image keypoint in any image of a batch is rejected
+    and leaves the registered images as they were."""
     import torch
+    from oracle import coarse as oc
     sc = facade_scene
     pairs = sc.pairs[:30]
     used = sorted({p.a for p in pairs} | {p.b for p in pairs})
     ref, st_ref = _gpu_rows(gm, sc, pairs=pairs)
-    for on_device in (False, True):
+    for mode in ("host", "device", "pinned"):
+        on_device = mode == "device"
         with gm.Context(device=0) as ctx:
-            if on_device:
-                imgs = {k: scenes.Image(sc.images[k].width, sc.images[k].height,
-                                        torch.from_numpy(sc.images[k].xy).cuda(), torch.from_numpy(sc.images[k].scale).cuda(),
-                                        torch.from_numpy(sc.images[k].desc).cuda(), sc.images[k].pid) for k in used}
-            else:
+            if mode == "host":
                 imgs = {k: sc.images[k] for k in used}
+            else:
+                put = (lambda a: torch.from_numpy(a).cuda()) if on_device else (lambda a: torch.from_numpy(a).pin_memory())
+                imgs = {k: scenes.Image(sc.images[k].width, sc.images[k].height, put(sc.images[k].xy),
+                                        put(sc.images[k].scale), put(sc.images[k].desc), sc.images[k].pid) for k in used}
             ctx.put_images(imgs)
             off, m = ctx.match_pairs(pairs)
             got = gm.split_matches(off, m)
             for k in range(len(pairs)):
-                np.testing.assert_array_equal(got[k], ref[k], err_msg=f"device={on_device} pair {k}")
+                np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{mode} pair {k}")
             assert ctx.stats()["n_candidates"] == st_ref["n_candidates"]
+            for k in used[:3]:   # the scales arrived: the coarse selection equals the oracle's
+                for g, w in zip(ctx.coarse_selection(k), oc.select_by_scale(sc.images[k].scale)):
+                    np.testing.assert_array_equal(g, w)
             # a bad keypoint in the second image of a new batch: nothing changes
             bad = scenes.Image(sc.images[used[1]].width, sc.images[used[1]].height, sc.images[used[1]].xy.copy(),
                                sc.images[used[1]].scale, sc.images[used[1]].desc, sc.images[used[1]].pid)
