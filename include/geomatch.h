@@ -185,8 +185,9 @@ GM_API gm_status gm_merge_tracks(gm_ctx *ctx, int64_t n_nodes, int64_t n_edges, 
                                  int64_t *n_tracks);
 
 /* Track triangulation (the end of Sec. 6.2: every merged track becomes a 3D point by linear least squares).
- * Nodes are numbered image-major over image_ids: node = (features of image_ids[0 .. k-1]) + feature index in image
- * image_ids[k] (the caller's keypoint order); n_nodes must equal the total.  labels (int64 [n_nodes]) are those of
+ * Nodes are numbered image-major over image_ids (int32 [n_images], host memory): node = (features of
+ * image_ids[0 .. k-1]) + feature index in image image_ids[k] (the caller's keypoint order); n_nodes must equal the
+ * total.  labels (int64 [n_nodes]) are those of
  * gm_merge_tracks: every label is the smallest node of its component (a label above its node or negative is
  * GM_ERR_INVALID).  Every component with at least two nodes is a track; tracks are numbered by increasing root.
  * Observation (x, y) in the image with camera P (3 x 4, row-major, double [12] per image in P[n_images][12])
@@ -215,7 +216,8 @@ typedef struct {
     int32_t min_matches;    /* the second batch runs after more than this many first-batch matches, >= 0 (paper: 4) */
 } gm_coarse_opts;
 
-/* Builds (or refreshes, after an image was put again or with other options) the coarse views of the images: the
+/* Builds (or refreshes, after an image was put again or with other options) the coarse views of the images
+ * (image_ids: int32 [n_images], host memory): the
  * selections above, registered on the device as internal images (they count toward the memory budget; evicting
  * an image drops its views).  gm_match_coarse builds missing views itself; this call lets them be built ahead.
  * Errors: GM_ERR_INVALID (bad options, an image without scales or with a NaN scale), GM_ERR_NOT_FOUND, those of
