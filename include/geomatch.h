@@ -217,9 +217,8 @@ typedef struct {
 } gm_coarse_opts;
 
 /* Builds (or refreshes, after an image was put again or with other options) the coarse views of the images
- * (image_ids: int32 [n_images], host memory): the
- * selections above, registered on the device as internal images (they count toward the memory budget; evicting
- * an image drops its views).  gm_match_coarse builds missing views itself; this call lets them be built ahead.
+ * (image_ids: int32 [n_images], host memory): the selections above, registered on the device as internal images
+ * (they count toward the memory budget; evicting an image drops its views).  gm_match_coarse builds missing views itself; this call lets them be built ahead.
  * Errors: GM_ERR_INVALID (bad options, an image without scales or with a NaN scale), GM_ERR_NOT_FOUND, those of
  * gm_image_put. */
 GM_API gm_status gm_coarse_prepare(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids,
