@@ -621,7 +621,7 @@ def run_approx(args, gm, dev, local, peaks, peak_kind):
     alg = _algorithmic_bytes(sc, sc.pairs, head["matches"])
     line = {"metric": "image pairs/s (approximate search)", "value": head["pairs_per_s"], "unit": "pairs/s",
             "n_gpus": 1, "steps": max(args.steps, 5), "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8 dp4a, FP32 geometry",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8 (mma.sync s8), FP32 geometry",
             "data": "synthetic (seeded facade scene)",
             "config": {"workload": "approx_facade_100img_8000kp_1200pairs_d4", "cell_scale": 1.0,
                        "l2": "flushed between steps (512 MB write)"},

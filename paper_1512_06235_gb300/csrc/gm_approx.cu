@@ -14,8 +14,9 @@
 //   Step 3  one warp per group: the K + 1 equidistant points of the leader's chord (K = ceil(|AB| / h)), for each
 //           the cell with the nearest centre among its four cells, every point binned there into a shared-memory
 //           bitmap over B's points (C' as a set);
-//   Step 4  the same warp: exact squared distances (dp4a over the recentred int8 descriptors) from each query of
-//           the group to every point of C', top-2, ratio test q^2 D1 < p^2 D2 with |C'| >= 2.
+//   Step 4  the same warp: exact squared distances from each query of the group to every point of C' (16 queries x
+//           8 candidates per mma.sync.m16n8k32 over the recentred int8 descriptors), top-2, ratio test
+//           q^2 D1 < p^2 D2 with |C'| >= 2.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -355,8 +356,17 @@ __global__ void group_start_kernel(const int32_t *__restrict__ flag, const int32
 
 // ---------------------------------------------------------------- Steps 3-4: one warp per group
 
-constexpr int kQChunk = 4;           // queries of a group scored together
+constexpr int kQTile = 16;           // queries of a group scored together (the mma m dimension)
 constexpr int kListCap = 1024;       // compacted candidate positions per round (32 bitmap words)
+constexpr size_t kWarpExtra = kQTile * kDim + 4 * kListCap + 4 * kQTile;   // query rows, list, query norms
+
+__device__ __forceinline__ void mma_s8(int (&d)[4], const int (&a)[4], int b0, int b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 constexpr int kMatchThreads = 128;
 
 __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const ApproxPair *__restrict__ P, const int64_t *__restrict__ qoff, int n_pairs,
@@ -370,7 +380,7 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int64_t g = (int64_t)blockIdx.x * wpb + wib;
     if (g >= G) return;
-    uint32_t *bm = reinterpret_cast<uint32_t *>(sm + (size_t)wib * ((size_t)words * 4 + kQChunk * kDim + 4 * kListCap));
+    uint32_t *bm = reinterpret_cast<uint32_t *>(sm + (size_t)wib * ((size_t)words * 4 + kWarpExtra));
     int8_t *qd = reinterpret_cast<int8_t *>(bm + words);
     const int32_t s0 = gstart[g], s1 = gstart[g + 1];
     const int k = upper_index(qoff, n_pairs, (int64_t)s0);
@@ -407,27 +417,36 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if (lane == 0) atomicAdd(&ctr->candidates, (unsigned long long)cnt * (unsigned long long)(s1 - s0));
-    // Step 4: exact distances from each query of the group to C', top-2, ratio test.  The bitmap is compacted into a
-    // list (at most kListCap positions at a time) so that the candidates spread evenly over the lanes.
-    int32_t *list = reinterpret_cast<int32_t *>(qd + kQChunk * kDim);
-    for (int32_t c0 = s0; c0 < s1; c0 += kQChunk) {
-        const int nq = min(kQChunk, s1 - c0);
-        int32_t qpos[kQChunk], qn[kQChunk];
-#pragma unroll
-        for (int t = 0; t < kQChunk; ++t) {
-            const int32_t idx = t < nq ? order[c0 + t] : order[c0];
-            qpos[t] = A.inv_perm[idx];
-            qn[t] = A.norm[qpos[t]];
+    // Step 4: exact distances from each query of the group to C', top-2, ratio test.  The group's queries are
+    // scored 16 at a time against 8 candidates at a time by mma.sync.m16n8k32.s8 (the int32 accumulator holds the
+    // exact dot product a'.b'); the bitmap is compacted into a list of at most kListCap positions per round.
+    // Fragments (lane = 4 g + t): A rows g and g + 8, bytes 4t .. 4t + 3 and 16 + 4t .. of each 32-byte K step;
+    // B column g (a candidate), the same bytes; accumulator element 2 h + e = (row g + 8 h, column 2 t + e).
+    int32_t *list = reinterpret_cast<int32_t *>(qd + kQTile * kDim);
+    int32_t *qn_s = list + kListCap;
+    const int gq = lane >> 2, t4 = lane & 3;
+    for (int32_t c0 = s0; c0 < s1; c0 += kQTile) {
+        const int nq = min(kQTile, s1 - c0);
+        __syncwarp();
+        for (int t = 0; t < kQTile; ++t) {   // 128 bytes per query row (zeros past the group), one word per lane
+            int32_t w = 0;
+            if (t < nq) w = reinterpret_cast<const int32_t *>(A.desc + (size_t)A.inv_perm[order[c0 + t]] * kDim)[lane];
+            reinterpret_cast<int32_t *>(qd + t * kDim)[lane] = w;
         }
+        if (lane < kQTile) qn_s[lane] = lane < nq ? A.norm[A.inv_perm[order[c0 + lane]]] : 0;
         __syncwarp();
+        int afr[4][4];
 #pragma unroll
-        for (int t = 0; t < kQChunk; ++t)   // 128 bytes per query: one 4-byte word per lane
-            reinterpret_cast<int32_t *>(qd + t * kDim)[lane] =
-                reinterpret_cast<const int32_t *>(A.desc + (size_t)qpos[t] * kDim)[lane];
-        __syncwarp();
-        int D1[kQChunk], D2[kQChunk], J1[kQChunk];
-#pragma unroll
-        for (int t = 0; t < kQChunk; ++t) { D1[t] = INT_MAX; D2[t] = INT_MAX; J1[t] = INT_MAX; }
+        for (int ks = 0; ks < 4; ++ks) {
+            const int8_t *r0 = qd + gq * kDim + ks * 32 + 4 * t4;
+            const int8_t *r1 = qd + (gq + 8) * kDim + ks * 32 + 4 * t4;
+            afr[ks][0] = *reinterpret_cast<const int *>(r0);
+            afr[ks][1] = *reinterpret_cast<const int *>(r1);
+            afr[ks][2] = *reinterpret_cast<const int *>(r0 + 16);
+            afr[ks][3] = *reinterpret_cast<const int *>(r1 + 16);
+        }
+        const int qn0 = qn_s[gq], qn1 = qn_s[gq + 8];
+        int D1[2] = {INT_MAX, INT_MAX}, D2[2] = {INT_MAX, INT_MAX}, J1[2] = {INT_MAX, INT_MAX};
         for (int32_t w0 = 0; w0 < nw;) {
             int32_t nl = 0;
             while (w0 < nw) {   // 32 words per round hold at most kListCap bits, so every round fits an empty list
@@ -451,60 +470,60 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
                 w0 += 32;
             }
             __syncwarp();
-            for (int32_t e = lane; e < nl; e += 32) {
-                const int32_t j = list[e];
-                const int4 *brow = reinterpret_cast<const int4 *>(B.desc + (size_t)j * kDim);
-                int dot[kQChunk] = {};
+            for (int32_t n0 = 0; n0 < nl; n0 += 8) {   // one n-tile of 8 candidates
+                const int cj = n0 + gq < nl ? list[n0 + gq] : list[n0];   // padding columns repeat a real one
+                const int8_t *brow = B.desc + (size_t)cj * kDim + 4 * t4;
+                int acc[4] = {0, 0, 0, 0};
 #pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    const int4 bv = __ldg(brow + v);
-#pragma unroll
-                    for (int t = 0; t < kQChunk; ++t) {
-                        const int4 av = reinterpret_cast<const int4 *>(qd + t * kDim)[v];
-                        dot[t] = __dp4a(av.x, bv.x, dot[t]);
-                        dot[t] = __dp4a(av.y, bv.y, dot[t]);
-                        dot[t] = __dp4a(av.z, bv.z, dot[t]);
-                        dot[t] = __dp4a(av.w, bv.w, dot[t]);
-                    }
+                for (int ks = 0; ks < 4; ++ks) {
+                    const int b0 = __ldg(reinterpret_cast<const int *>(brow + ks * 32));
+                    const int b1 = __ldg(reinterpret_cast<const int *>(brow + ks * 32 + 16));
+                    mma_s8(acc, afr[ks], b0, b1);
                 }
-                const int nb = __ldg(B.norm + j);
 #pragma unroll
-                for (int t = 0; t < kQChunk; ++t) {
-                    const int D = qn[t] + nb - 2 * dot[t];
-                    if (D < D1[t] || (D == D1[t] && j < J1[t])) { D2[t] = D1[t]; D1[t] = D; J1[t] = j; }
-                    else if (D < D2[t]) D2[t] = D;
+                for (int e = 0; e < 2; ++e) {
+                    const int col = n0 + 2 * t4 + e;
+                    if (col >= nl) continue;
+                    const int j = list[col];
+                    const int nb = __ldg(B.norm + j);
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int D = (hh ? qn1 : qn0) + nb - 2 * acc[2 * hh + e];
+                        if (D < D1[hh] || (D == D1[hh] && j < J1[hh])) { D2[hh] = D1[hh]; D1[hh] = D; J1[hh] = j; }
+                        else if (D < D2[hh]) D2[hh] = D;
+                    }
                 }
             }
             __syncwarp();
         }
-        // merge the lanes' top-2 lists
+        // merge the top-2 lists of the four lanes of each row pair (t = 0 .. 3)
 #pragma unroll
-        for (int t = 0; t < kQChunk; ++t) {
+        for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const int od1 = __shfl_xor_sync(0xffffffffu, D1[t], o);
-                const int od2 = __shfl_xor_sync(0xffffffffu, D2[t], o);
-                const int oj1 = __shfl_xor_sync(0xffffffffu, J1[t], o);
-                if (od1 < D1[t] || (od1 == D1[t] && oj1 < J1[t])) {
-                    D2[t] = min(D1[t], od2);
-                    D1[t] = od1;
-                    J1[t] = oj1;
+            for (int o = 1; o < 4; o <<= 1) {
+                const int od1 = __shfl_xor_sync(0xffffffffu, D1[hh], o);
+                const int od2 = __shfl_xor_sync(0xffffffffu, D2[hh], o);
+                const int oj1 = __shfl_xor_sync(0xffffffffu, J1[hh], o);
+                if (od1 < D1[hh] || (od1 == D1[hh] && oj1 < J1[hh])) {
+                    D2[hh] = min(D1[hh], od2);
+                    D1[hh] = od1;
+                    J1[hh] = oj1;
                 } else {
-                    D2[t] = min(D2[t], od1);
+                    D2[hh] = min(D2[hh], od1);
                 }
             }
         }
-        if (lane == 0) {
+        if (t4 == 0) {
 #pragma unroll
-            for (int t = 0; t < kQChunk; ++t) {
-                if (t >= nq) break;
+            for (int hh = 0; hh < 2; ++hh) {
+                const int t = gq + 8 * hh;
+                if (t >= nq) continue;
                 const int64_t pp = pr.p, qq = pr.q;
                 int out = -1;
-                if (cnt >= 2 && qq * qq * (int64_t)D1[t] < pp * pp * (int64_t)D2[t]) out = B.perm[J1[t]];
+                if (cnt >= 2 && qq * qq * (int64_t)D1[hh] < pp * pp * (int64_t)D2[hh]) out = B.perm[J1[hh]];
                 match_j[q0 + order[c0 + t]] = out;
             }
         }
-        __syncwarp();
     }
 }
 
@@ -675,7 +694,7 @@ gm_status gm_match_pairs_approx(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pai
     GM_CUDA_A(cudaStreamSynchronize(s));
     // Steps 3-4
     const int32_t words = ((max_nb + 31) / 32 + 3) & ~3;   // a multiple of 4 words keeps the query rows 16-byte aligned
-    const size_t per_warp = (size_t)words * 4 + kQChunk * kDim + 4 * kListCap;
+    const size_t per_warp = (size_t)words * 4 + kWarpExtra;
     int wpb = 4;
     while (wpb > 1 && per_warp * wpb > 200 * 1024) --wpb;
     if (per_warp * wpb > 200 * 1024) return fail(GM_ERR_INVALID, "%s: target image too large for the bitmap", fn);
