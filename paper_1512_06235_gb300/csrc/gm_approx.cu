@@ -357,6 +357,7 @@ __global__ void group_start_kernel(const int32_t *__restrict__ flag, const int32
 // ---------------------------------------------------------------- Steps 3-4: one warp per group
 
 constexpr int kQTile = 16;           // queries of a group scored together (the mma m dimension)
+constexpr int kSampleBatch = 4;      // chord samples a lane looks up at a time
 constexpr int kListCap = 1024;       // compacted candidate positions per round (32 bitmap words)
 constexpr size_t kWarpExtra = kQTile * kDim + 4 * kListCap + 4 * kQTile;   // query rows, list, query norms
 
@@ -399,15 +400,27 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
         line32(pr.F, pt.x, pt.y, a, b, c);
         const Chord e = chord32(a, b, c, pr.W, pr.H);
         const int K = samples_k(e, pr.h);
-        for (int kk = lane; kk <= K; kk += 32) {
-            float x, y;
-            sample(e, K, kk, x, y);
-            const int64_t cidx = chosen_cell(J, x, y);
-            if (cidx < 0) continue;
-            for (int32_t m = cell_off[cidx]; m < cell_off[cidx + 1]; ++m) {
-                const int32_t pos = members[m];
-                atomicOr(&bm[pos >> 5], 1u << (pos & 31));
+        for (int base = 0; base <= K; base += 32 * kSampleBatch) {
+            // kSampleBatch samples per lane at a time: their cell lookups are independent loads in flight together
+            int lo[kSampleBatch], hi[kSampleBatch];
+#pragma unroll
+            for (int t = 0; t < kSampleBatch; ++t) {
+                const int kk = base + lane + 32 * t;
+                int64_t cidx = -1;
+                if (kk <= K) {
+                    float x, y;
+                    sample(e, K, kk, x, y);
+                    cidx = chosen_cell(J, x, y);
+                }
+                lo[t] = cidx >= 0 ? __ldg(cell_off + cidx) : 0;
+                hi[t] = cidx >= 0 ? __ldg(cell_off + cidx + 1) : 0;
             }
+#pragma unroll
+            for (int t = 0; t < kSampleBatch; ++t)
+                for (int32_t m = lo[t]; m < hi[t]; ++m) {
+                    const int32_t pos = __ldg(members + m);
+                    atomicOr(&bm[pos >> 5], 1u << (pos & 31));
+                }
         }
         if (lane == 0) atomicAdd(&ctr->cells, (unsigned long long)(K + 1));
     }
