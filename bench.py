@@ -504,7 +504,11 @@ def run_coarse(args, gm, dev, local, peaks, peak_kind):
     ctx = gm.Context(device=local, stream=stream)
     ctx.put_images({k: im for k, im in enumerate(sc.images)})
     ids = np.arange(n_img, dtype=np.int32)
-    # view build: alternate min_features 1000 / 999 (same selection for 8000 features) so every call rebuilds
+    # view build: first the kernels' first launches on a small context, then the first build of the 100 images'
+    # views, then rebuilds (min_features alternating 1000 / 999: the same selection, so every call rebuilds)
+    with gm.Context(device=local, stream=stream) as warm:
+        warm.put_images({0: sc.images[0]})
+        gm.gm_coarse_prepare(warm.h, np.zeros(1, np.int32), gm.coarse_opts())
     prep_ms = []
     for r in range(4):
         opts = gm.coarse_opts(20, 10, 1000 - (r % 2), 4)
@@ -546,7 +550,7 @@ def run_coarse(args, gm, dev, local, peaks, peak_kind):
             "data": "synthetic (seeded facade scene, per-point scales)",
             "config": {"workload": f"coarse_facade_{n_img}img_all_{len(pairs)}pairs_eta20_first10",
                        "matches": n, "second_batches": int(second.sum()), "comparisons": comps,
-                       "view_build_ms": float(np.median(prep_ms))},
+                       "view_build_ms": prep_ms[0], "view_rebuild_ms": float(np.median(prep_ms[1:]))},
             "comparisons_per_s": comps / (ms / 1e3),
             "roofline": {"bound": "tensor", "achieved": ops / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": ops / (ms / 1e3) / 1e12 / peak, "traffic": None,

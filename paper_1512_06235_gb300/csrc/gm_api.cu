@@ -528,7 +528,7 @@ gm_status gm_destroy(gm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
     for (auto &kv : ctx->images) {
-        cudaFree(kv.second->block);
+        release_block(kv.second);
         delete kv.second;
     }
     ctx->images.clear();
@@ -836,20 +836,31 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
                         bad[k], imgs[k].width, imgs[k].height);
     // 2. destination blocks: a replaced image's block when it is large enough (no serving batch may still read it)
     if (ctx->server) server_drain(ctx->server);
+    // every new block of the call comes out of one allocation (one cudaMalloc instead of one per image)
     std::vector<void *> block(count, nullptr);
     std::vector<char> fresh(count, 0);
+    std::vector<size_t> slab_off(count, 0);
+    size_t slab_bytes = 0;
     for (int32_t k = 0; k < count; ++k) {
         auto it = ctx->images.find(imgs[k].image_id);
         if (it != ctx->images.end() && it->second->bytes >= L[k].tot) {
             block[k] = it->second->block;
-        } else if (cudaMalloc(&block[k], L[k].tot) != cudaSuccess) {
-            cudaGetLastError();
-            for (int32_t l = 0; l < k; ++l)
-                if (fresh[l]) cudaFree(block[l]);
-            return fail(GM_ERR_NOMEM, "%s: cudaMalloc of %zu bytes failed (image %d)", fn, L[k].tot, imgs[k].image_id);
         } else {
             fresh[k] = 1;
+            slab_off[k] = slab_bytes;
+            slab_bytes += align_up(L[k].tot, 256);
         }
+    }
+    Slab *slab = nullptr;
+    if (slab_bytes) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, slab_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GM_ERR_NOMEM, "%s: cudaMalloc of %zu bytes failed", fn, slab_bytes);
+        }
+        slab = new Slab{p, 0};
+        for (int32_t k = 0; k < count; ++k)
+            if (fresh[k]) block[k] = static_cast<char *>(p) + slab_off[k];
     }
     // 3. bin every image into its block (the counts are recomputed: the work arrays hold one sub-batch)
     std::vector<ImageDev> dev(count);
@@ -879,8 +890,10 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
     }
     if (st != GM_OK || e != cudaSuccess) {
         cudaStreamSynchronize(s);
-        for (int32_t k = 0; k < count; ++k)
-            if (fresh[k]) cudaFree(block[k]);
+        if (slab) {   // no image holds it yet
+            cudaFree(slab->p);
+            delete slab;
+        }
         return st != GM_OK ? st : fail(GM_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     }
     // 4. install: replace or take a free slot; TMA descriptors of each image (tcgen05 path)
@@ -891,9 +904,11 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
         if (it != ctx->images.end()) {
             img = it->second;
             if (fresh[k]) {
-                cudaFree(img->block);   // nothing reads the old block: serving was drained, synchronous calls ended
+                release_block(img);   // nothing reads the old block: serving was drained, synchronous calls ended
                 ctx->bytes_images -= img->bytes;
                 img->block = block[k];
+                img->slab = slab;
+                ++slab->refs;
                 img->bytes = L[k].tot;
                 ctx->bytes_images += L[k].tot;
             }
@@ -911,6 +926,8 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             ctx->slots[slot] = img;
             ctx->images[g.image_id] = img;
             img->block = block[k];
+            img->slab = slab;
+            ++slab->refs;
             img->bytes = L[k].tot;
             ctx->bytes_images += L[k].tot;
         }
@@ -963,13 +980,23 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
     return GM_OK;
 }
 
+void release_block(ImageSlot *img)
+{
+    if (img->slab && --img->slab->refs == 0) {
+        cudaFree(img->slab->p);
+        delete img->slab;
+    }
+    img->slab = nullptr;
+    img->block = nullptr;
+}
+
 void drop_image(gm_ctx *ctx, int32_t image_id)
 {
     auto it = ctx->images.find(image_id);
     if (it == ctx->images.end()) return;
     cudaStreamSynchronize(ctx->ws.stream);
     ImageSlot *img = it->second;
-    cudaFree(img->block);
+    release_block(img);
     ctx->bytes_images -= img->bytes;
     ctx->slots[img->slot] = nullptr;
     ctx->images.erase(it);

@@ -220,15 +220,6 @@ gm_status resolve_opts(const gm_coarse_opts *opts, Opts &o, const char *fn)
     return GM_OK;
 }
 
-void drop_views(gm_ctx *ctx, CoarseViews &v)
-{
-    if (!v.all)
-        for (int k = 0; k < 3; ++k)
-            if (v.id[k] < 0) drop_image(ctx, v.id[k]);
-    free_dev(ctx, v.lists);
-    v = CoarseViews{};
-}
-
 // Builds the views of every listed image that has none, or stale ones (image put again, other options).
 gm_status ensure_views(gm_ctx *ctx, const std::vector<int32_t> &ids, const Opts &o, const char *fn)
 {
@@ -368,16 +359,28 @@ gm_status ensure_views(gm_ctx *ctx, const std::vector<int32_t> &ids, const Opts 
                 GM_CUDA_C(cudaGetLastError());
             }
         }
-        for (size_t w = 0; w < views.size(); ++w) views[w].image_id = ctx->next_internal_id - (int32_t)w;
+        // a rebuilt view keeps its internal id, so that its block is reused when large enough
+        int32_t fresh_ids = 0;
+        for (size_t w = 0; w < views.size(); ++w) {
+            auto cv = ctx->coarse.find(todo[view_of[w].first]);
+            const int32_t old = cv != ctx->coarse.end() && !cv->second.all ? cv->second.id[view_of[w].second] : 0;
+            views[w].image_id = old < 0 ? old : ctx->next_internal_id - fresh_ids++;
+        }
         if (!views.empty()) {
             if ((st = put_images(ctx, (int32_t)views.size(), views.data(), 1, fn, true)) != GM_OK) return cleanup(), st;
-            ctx->next_internal_id -= (int32_t)views.size();
+            ctx->next_internal_id -= fresh_ids;
         }
         for (size_t w = 0; w < views.size(); ++w) nv[view_of[w].first].id[view_of[w].second] = views[w].image_id;
     }
     for (size_t u = 0; u < todo.size(); ++u) {
         auto cv = ctx->coarse.find(todo[u]);
-        if (cv != ctx->coarse.end()) drop_views(ctx, cv->second);
+        if (cv != ctx->coarse.end()) {   // the old views not carried over, and the old index lists
+            CoarseViews &o = cv->second;
+            if (!o.all)
+                for (int v = 0; v < 3; ++v)
+                    if (o.id[v] < 0 && o.id[v] != nv[u].id[v]) drop_image(ctx, o.id[v]);
+            free_dev(ctx, o.lists);
+        }
         ctx->coarse[todo[u]] = nv[u];
     }
     return GM_OK;

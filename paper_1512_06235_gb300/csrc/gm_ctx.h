@@ -26,12 +26,19 @@ struct HostBuf {
     bool mapped = false;
 };
 
+// One device allocation shared by the images that one registration call created; freed with its last image.
+struct Slab {
+    void *p = nullptr;
+    int32_t refs = 0;
+};
+
 struct ImageSlot {
     int32_t id = -1;
     int32_t slot = -1;
     ImageDev dev{};
     TmaMaps maps{};
-    void *block = nullptr;
+    void *block = nullptr;          // inside slab
+    Slab *slab = nullptr;
     size_t bytes = 0;
     const float *scale = nullptr;   // keypoint scales in the caller's order (inside block)
     bool has_scale = false;
@@ -163,6 +170,8 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
                      bool internal = false);
 // Drops one registered image (caller holds ctx->mu; serving drained by the caller).
 void drop_image(gm_ctx *ctx, int32_t image_id);
+// Gives up an image's block: the slab is freed with its last image.
+void release_block(ImageSlot *img);
 bool is_device_ptr(const void *p);
 // Enqueues the whole batch on ws.stream: table upload, order, match, count/scan, row writing into rows_dst
 // (device memory or mapped host memory with room for ws.Q rows; nullptr = ws.d_rows), then the D2H copy of the
