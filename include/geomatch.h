@@ -72,7 +72,11 @@ enum {
                                automatic (the default: 4 px, coarser only for images wider than 4096 px) */
     GM_OPT_GRAPH = 4,       /* 1 = replay batches through a captured CUDA graph when the shape repeats */
     GM_OPT_MMA_GROUP = 5,   /* queries per group of the mma path: 16 (default) or 32 */
-    GM_OPT_STREAM_CAP = 6   /* entries of the tcgen05 path's candidate-stream buffer (grown automatically) */
+    GM_OPT_STREAM_CAP = 6,  /* entries of the tcgen05 path's candidate-stream buffer (grown automatically) */
+    GM_OPT_EVICT_LRU = 7    /* 1 = an image put that would exceed the memory budget first evicts the least recently
+                               used images (last put or matched), with their coarse views, as gm_image_evict would
+                               -- never one of the images being put nor one that an unfinished serving request
+                               names; 0 (default) = refuse with GM_ERR_BUDGET */
 };
 
 typedef struct {
@@ -159,6 +163,20 @@ GM_API gm_status gm_images_put(gm_ctx *ctx, int32_t count, const gm_image *image
 
 /* Drops image `image_id` from the context.  GM_ERR_NOT_FOUND if unknown. */
 GM_API gm_status gm_image_evict(gm_ctx *ctx, int32_t image_id);
+
+/* Whether image `image_id` is resident: GM_OK with *n = its keypoint count (n may be NULL), or GM_ERR_NOT_FOUND. */
+GM_API gm_status gm_image_info(gm_ctx *ctx, int32_t image_id, int32_t *n);
+
+/* Pins (pin = 1) or unpins (pin = 0) a resident image: GM_OPT_EVICT_LRU never evicts a pinned image.  Pins count;
+ * gm_image_evict drops an image whatever its pins.  Errors: GM_ERR_NOT_FOUND, GM_ERR_INVALID (unpinning an image
+ * that is not pinned). */
+GM_API gm_status gm_image_pin(gm_ctx *ctx, int32_t image_id, int32_t pin);
+
+/* The resident-image cache: caller images resident, device bytes of all resident images (coarse views included),
+ * device bytes of the context's work buffers (they count toward the budget too) and images evicted by
+ * GM_OPT_EVICT_LRU so far.  Any pointer may be NULL. */
+GM_API gm_status gm_image_cache_stats(gm_ctx *ctx, int64_t *images, int64_t *bytes, int64_t *work_bytes,
+                                      int64_t *evicted);
 
 /* Candidate image pairs from point-camera co-visibility (Sec. 6.1): the pairs that gm_match_pairs then matches.
  * For each query image q the candidates are the images i != q that see more than `threshold` of the points q sees

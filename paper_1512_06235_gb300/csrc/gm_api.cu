@@ -15,6 +15,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "gm_ctx.h"
@@ -257,6 +258,7 @@ gm_status engine_plan(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair
     for (int32_t k = 0; k < n_pairs; ++k) {
         gm_status st = prepare_pair(ctx, pairs[k], k, ws.pd[k], internal);
         if (st != GM_OK) return st;
+        ctx->slots[ws.pd[k].a]->last_use = ctx->slots[ws.pd[k].b]->last_use = ++ctx->use_tick;
         ws.pd[k].qoff = ws.Q;
         ws.Q += ws.pd[k].n_a;
         ws.nitems += (ws.pd[k].n_a + kQueriesPerItem - 1) / kQueriesPerItem;
@@ -586,6 +588,10 @@ gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value)
         if (value < 0 || value > 1) return fail(GM_ERR_INVALID, "bad graph flag");
         ctx->graph = (int32_t)value;
         return GM_OK;
+    case GM_OPT_EVICT_LRU:
+        if (value < 0 || value > 1) return fail(GM_ERR_INVALID, "bad eviction flag");
+        ctx->evict_lru = (int32_t)value;
+        return GM_OK;
     default:
         return fail(GM_ERR_INVALID, "unknown option %d", key);
     }
@@ -748,6 +754,46 @@ gm_status bucket_batches(gm_ctx *ctx, int32_t count, const gm_image *imgs, const
 
 }  // namespace
 
+int64_t user_image_bytes(gm_ctx *ctx, int32_t id);
+int64_t evict_user_image(gm_ctx *ctx, int32_t id);
+
+namespace {
+
+// Caller images that may be evicted for this call: not among the images being put, and not referenced by a serving
+// request that has not finished.
+std::vector<int32_t> evictable(gm_ctx *ctx, const gm_image *imgs, int32_t count)
+{
+    std::unordered_set<int32_t> keep;
+    for (int32_t k = 0; k < count; ++k) keep.insert(imgs[k].image_id);
+    if (ctx->server) server_referenced(ctx->server, keep);
+    std::vector<int32_t> ids;
+    for (auto &kv : ctx->images)
+        if (kv.first >= 0 && kv.second->pins == 0 && !keep.count(kv.first)) ids.push_back(kv.first);
+    return ids;
+}
+
+// Bytes that evicting every evictable image (with its coarse views) would free.
+int64_t evictable_bytes(gm_ctx *ctx, const gm_image *imgs, int32_t count)
+{
+    int64_t b = 0;
+    for (int32_t id : evictable(ctx, imgs, count)) b += user_image_bytes(ctx, id);
+    return b;
+}
+
+// Evicts evictable images, least recently used first, until `need` bytes are free.
+void evict_lru_images(gm_ctx *ctx, const gm_image *imgs, int32_t count, int64_t need)
+{
+    std::vector<std::pair<uint64_t, int32_t>> order;
+    for (int32_t id : evictable(ctx, imgs, count)) order.push_back({ctx->images.at(id)->last_use, id});
+    std::sort(order.begin(), order.end());
+    for (size_t k = 0; k < order.size() && need > 0; ++k) {
+        need -= evict_user_image(ctx, order[k].second);
+        ++ctx->images_evicted;
+    }
+}
+
+}  // namespace
+
 // All inputs are validated before anything registered changes; the device work of all images is enqueued back to
 // back with two stream synchronisations in total (after the keypoint check, and at the end).
 gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t on_device, const char *fn,
@@ -781,8 +827,13 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             if (it != ctx->images.end()) replaced += it->second->bytes;
         }
     }
-    if (ctx->budget && ctx->bytes_images - replaced + new_bytes + ctx->bytes_work > ctx->budget)
-        return fail(GM_ERR_BUDGET, "%s: %zu bytes of images exceed the device-memory budget", fn, new_bytes);
+    int64_t over = ctx->budget ? (int64_t)(ctx->bytes_images - replaced + new_bytes + ctx->bytes_work) -
+                                     (int64_t)ctx->budget
+                               : 0;
+    if (over > 0) {   // without eviction, or when evicting every other image would not make room: refuse now
+        if (!ctx->evict_lru || internal || evictable_bytes(ctx, imgs, count) < over)
+            return fail(GM_ERR_BUDGET, "%s: %zu bytes of images exceed the device-memory budget", fn, new_bytes);
+    }
     cudaStream_t s = ctx->ws.stream;
     gm_status st;
     // 1. stage host inputs and check every keypoint (nothing registered is touched yet)
@@ -836,6 +887,7 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
                         bad[k], imgs[k].width, imgs[k].height);
     // 2. destination blocks: a replaced image's block when it is large enough (no serving batch may still read it)
     if (ctx->server) server_drain(ctx->server);
+    if (over > 0) evict_lru_images(ctx, imgs, count, over);   // the inputs are valid and nothing reads the images
     // every new block of the call comes out of one allocation (one cudaMalloc instead of one per image)
     std::vector<void *> block(count, nullptr);
     std::vector<char> fresh(count, 0);
@@ -937,6 +989,7 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
                                img->dev.rec == dev[k].rec;
         img->dev = dev[k];
         img->gen = ++ctx->image_gen;
+        img->last_use = ++ctx->use_tick;
         img->scale = reinterpret_cast<const float *>(static_cast<char *>(img->block) + L[k].offs[10]);
         img->has_scale = g.n > 0 && g.scale != nullptr;
         if (!same_maps) {
@@ -1003,6 +1056,37 @@ void drop_image(gm_ctx *ctx, int32_t image_id)
     delete img;
 }
 
+// Device bytes of a caller image and of its coarse views.
+int64_t user_image_bytes(gm_ctx *ctx, int32_t id)
+{
+    auto it = ctx->images.find(id);
+    if (it == ctx->images.end()) return 0;
+    int64_t b = (int64_t)it->second->bytes;
+    auto cv = ctx->coarse.find(id);
+    if (cv != ctx->coarse.end() && !cv->second.all)
+        for (int v = 0; v < 3; ++v) {
+            auto iv = cv->second.id[v] < 0 ? ctx->images.find(cv->second.id[v]) : ctx->images.end();
+            if (iv != ctx->images.end()) b += (int64_t)iv->second->bytes;
+        }
+    return b;
+}
+
+// Drops a caller image and its coarse views; returns the bytes freed (caller holds ctx->mu, serving drained).
+int64_t evict_user_image(gm_ctx *ctx, int32_t id)
+{
+    const int64_t b = user_image_bytes(ctx, id);
+    drop_image(ctx, id);
+    auto cv = ctx->coarse.find(id);
+    if (cv != ctx->coarse.end()) {
+        if (!cv->second.all)
+            for (int v = 0; v < 3; ++v)
+                if (cv->second.id[v] < 0) drop_image(ctx, cv->second.id[v]);
+        free_dev(ctx, cv->second.lists);
+        ctx->coarse.erase(cv);
+    }
+    return b;
+}
+
 gm_status run_batch(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *pairs, bool internal, const char *fn)
 {
     gm_status st = engine_plan(ctx, ws, n_pairs, pairs, internal);
@@ -1044,15 +1128,44 @@ gm_status gm_image_evict(gm_ctx *ctx, int32_t image_id)
     if (image_id < 0 || it == ctx->images.end())
         return fail(GM_ERR_NOT_FOUND, "gm_image_evict: image %d not registered", image_id);
     if (ctx->server) server_drain(ctx->server);
-    drop_image(ctx, image_id);
-    auto cv = ctx->coarse.find(image_id);   // the image's coarse-stage views go with it
-    if (cv != ctx->coarse.end()) {
-        if (!cv->second.all)
-            for (int v = 0; v < 3; ++v)
-                if (cv->second.id[v] < 0) drop_image(ctx, cv->second.id[v]);
-        free_dev(ctx, cv->second.lists);
-        ctx->coarse.erase(cv);
-    }
+    evict_user_image(ctx, image_id);   // the image's coarse-stage views go with it
+    return GM_OK;
+}
+
+gm_status gm_image_info(gm_ctx *ctx, int32_t image_id, int32_t *n)
+{
+    if (!ctx) return fail(GM_ERR_INVALID, "gm_image_info: null context");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto it = ctx->images.find(image_id);
+    if (image_id < 0 || it == ctx->images.end())
+        return fail(GM_ERR_NOT_FOUND, "gm_image_info: image %d not registered", image_id);
+    if (n) *n = it->second->dev.n;
+    return GM_OK;
+}
+
+gm_status gm_image_pin(gm_ctx *ctx, int32_t image_id, int32_t pin)
+{
+    if (!ctx || (pin != 0 && pin != 1)) return fail(GM_ERR_INVALID, "gm_image_pin: bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto it = ctx->images.find(image_id);
+    if (image_id < 0 || it == ctx->images.end())
+        return fail(GM_ERR_NOT_FOUND, "gm_image_pin: image %d not registered", image_id);
+    ImageSlot *img = it->second;
+    if (!pin && img->pins == 0) return fail(GM_ERR_INVALID, "gm_image_pin: image %d is not pinned", image_id);
+    img->pins += pin ? 1 : -1;
+    return GM_OK;
+}
+
+gm_status gm_image_cache_stats(gm_ctx *ctx, int64_t *images, int64_t *bytes, int64_t *work_bytes, int64_t *evicted)
+{
+    if (!ctx) return fail(GM_ERR_INVALID, "gm_image_cache_stats: null context");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    int64_t c = 0;
+    for (auto &kv : ctx->images) c += kv.first >= 0;
+    if (images) *images = c;
+    if (bytes) *bytes = (int64_t)ctx->bytes_images;
+    if (work_bytes) *work_bytes = (int64_t)ctx->bytes_work;
+    if (evicted) *evicted = ctx->images_evicted;
     return GM_OK;
 }
 

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/geomatch.h"
@@ -43,6 +44,8 @@ struct ImageSlot {
     const float *scale = nullptr;   // keypoint scales in the caller's order (inside block)
     bool has_scale = false;
     uint64_t gen = 0;               // registration generation (changes on every put of this id)
+    uint64_t last_use = 0;          // tick of its last put or batch (least recently used images are evicted first)
+    int32_t pins = 0;               // gm_image_pin count: a pinned image is never evicted
 };
 
 // Coarse-stage views of one registered image (Sec. 4): its high-scale feature subsets registered as internal
@@ -117,6 +120,9 @@ struct gm_ctx {
     int32_t schedule = 0;
     int32_t cell_shift = 0;          // 0: automatic per image
     int32_t graph = 0;
+    int32_t evict_lru = 0;           // GM_OPT_EVICT_LRU
+    uint64_t use_tick = 0;
+    int64_t images_evicted = 0;
     int32_t max_inflight = 2;
     int32_t num_sms = 0;
     int32_t mma_mt = 1;             // m16 tiles per query group of the tensor-core path
@@ -191,6 +197,8 @@ void server_drain(Server *srv);
 gm_status server_stats(Server *srv, gm_serving_stats *out);
 // Waits until every submitted request has completed (caller must not hold ctx->mu).
 void server_wait_idle(Server *srv);
+// Image ids referenced by serving requests not yet finished (they are never evicted).
+void server_referenced(Server *srv, std::unordered_set<int32_t> &ids);
 const char *last_error();
 
 }  // namespace gm

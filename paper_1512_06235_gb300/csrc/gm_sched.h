@@ -111,6 +111,17 @@ public:
         return GM_OK;
     }
 
+    // The image ids of every request not yet finished (queued, or taken into a batch): images that must stay
+    // resident.  Never blocks on the engine (the scheduler holds mu_ only for its own bookkeeping).
+    template <typename Set>
+    void referenced_images(Set &ids)
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        for (auto &r : pending_) { ids.insert(r->pair.img_a); ids.insert(r->pair.img_b); }
+        for (auto &sl : slots_)
+            for (auto &r : sl.reqs) { ids.insert(r->pair.img_a); ids.insert(r->pair.img_b); }
+    }
+
     // Blocks until nothing is queued or in flight.
     void drain()
     {

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <unordered_set>
 #include <vector>
 
 #include "gm_ctx.h"
@@ -215,5 +216,7 @@ gm_status server_stats(Server *srv, gm_serving_stats *out)
 }
 
 void server_wait_idle(Server *srv) { srv->sched->drain(); }
+
+void server_referenced(Server *srv, std::unordered_set<int32_t> &ids) { srv->sched->referenced_images(ids); }
 
 }  // namespace gm

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libgeomatch.so")
 GM_OK, GM_ERR_INVALID, GM_ERR_NOMEM, GM_ERR_BUDGET, GM_ERR_NOT_FOUND, GM_ERR_CUDA, GM_ERR_TIMEOUT, \
     GM_ERR_CANCELLED, GM_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6, -7, -8
 GM_PATH_AUTO, GM_PATH_TC, GM_PATH_MMA, GM_PATH_SIMT = 0, 1, 2, 3
-GM_OPT_PATH, GM_OPT_SCHEDULE, GM_OPT_CELL_PX, GM_OPT_GRAPH, GM_OPT_MMA_GROUP, GM_OPT_STREAM_CAP = 1, 2, 3, 4, 5, 6
+GM_OPT_PATH, GM_OPT_SCHEDULE, GM_OPT_CELL_PX, GM_OPT_GRAPH, GM_OPT_MMA_GROUP, GM_OPT_STREAM_CAP, GM_OPT_EVICT_LRU = \
+    1, 2, 3, 4, 5, 6, 7
 
 _STATUS_NAMES = {0: "GM_OK", -1: "GM_ERR_INVALID", -2: "GM_ERR_NOMEM", -3: "GM_ERR_BUDGET", -4: "GM_ERR_NOT_FOUND",
                  -5: "GM_ERR_CUDA", -6: "GM_ERR_TIMEOUT", -7: "GM_ERR_CANCELLED", -8: "GM_ERR_BUSY"}
@@ -97,6 +98,10 @@ _SIGNATURES = {
     "gm_set_option": (c_i32, [c_p, c_i32, c_i64]),
     "gm_image_put": (c_i32, [c_p, c_i32, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i32]),
     "gm_image_evict": (c_i32, [c_p, c_i32]),
+    "gm_image_info": (c_i32, [c_p, c_i32, ctypes.POINTER(c_i32)]),
+    "gm_image_pin": (c_i32, [c_p, c_i32, c_i32]),
+    "gm_image_cache_stats": (c_i32, [c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
+                                     ctypes.POINTER(c_i64)]),
     "gm_match_pairs": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_p, c_p, c_i64, ctypes.POINTER(c_i64)]),
     "gm_band_candidates": (c_i32, [c_p, ctypes.POINTER(GmPair), c_i32, c_i32, c_p, c_p, c_i64,
                                    ctypes.POINTER(c_i64)]),
@@ -397,6 +402,27 @@ def gm_match_pairs_approx(ctx, pairs, pair_off, matches, cap: int, cell_scale: f
 
 def gm_image_evict(ctx, image_id: int):
     _check(load_library().gm_image_evict(ctx, image_id), ctx)
+
+
+def gm_image_info(ctx, image_id: int):
+    """Keypoint count of a resident image, or None if it is not resident."""
+    n = c_i32(0)
+    st = load_library().gm_image_info(ctx, image_id, ctypes.byref(n))
+    if st == GM_ERR_NOT_FOUND:
+        return None
+    _check(st, ctx)
+    return n.value
+
+
+def gm_image_pin(ctx, image_id: int, pin: bool = True):
+    _check(load_library().gm_image_pin(ctx, image_id, 1 if pin else 0), ctx)
+
+
+def gm_image_cache_stats(ctx) -> dict:
+    a, b, w, c = c_i64(0), c_i64(0), c_i64(0), c_i64(0)
+    _check(load_library().gm_image_cache_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(w),
+                                               ctypes.byref(c)), ctx)
+    return {"images": a.value, "bytes": b.value, "work_bytes": w.value, "evicted": c.value}
 
 
 def gm_match_pairs(ctx, pairs, pair_off, matches, cap: int) -> int:
