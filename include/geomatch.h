@@ -285,6 +285,13 @@ GM_API gm_status gm_match_pairs_approx(gm_ctx *ctx, int32_t n_pairs, const gm_pa
                                        int64_t *pair_off, int32_t *matches, int64_t cap, int64_t *n_written,
                                        gm_approx_stats *stats);
 
+/* Self-test of the device-side failure path (the paper has no counterpart).  Every wait in the library's kernels
+ * gives up after a time limit, records the failure in device memory and returns; the host reports GM_ERR_TIMEOUT and
+ * the context stays usable.  This call runs that pattern alone: one device thread waits for a flag with a bounded
+ * spin of limit_us microseconds (1 .. 1000000); with set_flag = 1 the host sets the flag first and the call returns
+ * GM_OK, with set_flag = 0 nothing sets it and the call returns GM_ERR_TIMEOUT. */
+GM_API gm_status gm_selftest_wait(gm_ctx *ctx, int32_t limit_us, int32_t set_flag);
+
 /* Autotuner (a tuning aid; the paper has no counterpart).  Times gm_match_pairs on this batch for every distance
  * path (tc; mma with 16- and 32-query groups; simt) and grid cell size (4, 8, 16 px), `repeats` timed runs each
  * after one warm-up, and leaves the fastest setting in the context: GM_OPT_PATH, GM_OPT_MMA_GROUP and

@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "-Xptxas", "-O3", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 SOURCES = ["gm_api.cu", "gm_serve.cu", "gm_bucket.cu", "gm_order.cu", "gm_match_simt.cu", "gm_match_mma.cu", "gm_match_tc.cu", "gm_noalloc.cu", "gm_tune.cu", "gm_pairs.cu", "gm_tracks.cu",
-           "gm_triangulate.cu", "gm_coarse.cu", "gm_approx.cu",
+           "gm_triangulate.cu", "gm_coarse.cu", "gm_approx.cu", "gm_selftest.cu",
            "gm_stream.cu", "gm_compact.cu"]
 
 

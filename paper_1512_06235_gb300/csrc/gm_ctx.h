@@ -140,6 +140,7 @@ struct gm_ctx {
     gm::DevBuf d_coarse_tab, d_coarse_stage, d_coarse_out;
     gm::DevBuf d_approx;            // gm_match_pairs_approx: every array of one call
     gm::DevBuf d_segs;              // image registration: copy segments of the scales
+    gm::DevBuf d_selftest;          // gm_selftest_wait: the flag and the status
     cudaStream_t copy_stream = nullptr;   // image registration: descriptor uploads beside the keypoint check
     cudaEvent_t ev_stage = nullptr, ev_desc = nullptr;
     std::unordered_map<int32_t, gm::CoarseViews> coarse;   // by caller's image id

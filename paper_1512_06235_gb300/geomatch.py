@@ -100,6 +100,7 @@ _SIGNATURES = {
     "gm_image_evict": (c_i32, [c_p, c_i32]),
     "gm_image_info": (c_i32, [c_p, c_i32, ctypes.POINTER(c_i32)]),
     "gm_image_pin": (c_i32, [c_p, c_i32, c_i32]),
+    "gm_selftest_wait": (c_i32, [c_p, c_i32, c_i32]),
     "gm_image_cache_stats": (c_i32, [c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
                                      ctypes.POINTER(c_i64)]),
     "gm_match_pairs": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_p, c_p, c_i64, ctypes.POINTER(c_i64)]),
@@ -412,6 +413,14 @@ def gm_image_info(ctx, image_id: int):
         return None
     _check(st, ctx)
     return n.value
+
+
+def gm_selftest_wait(ctx, limit_us: int, set_flag: bool) -> int:
+    """Status of the bounded device-wait self-test (GM_OK or GM_ERR_TIMEOUT); raises on other errors."""
+    st = load_library().gm_selftest_wait(ctx, limit_us, 1 if set_flag else 0)
+    if st not in (GM_OK, GM_ERR_TIMEOUT):
+        _check(st, ctx)
+    return st
 
 
 def gm_image_pin(ctx, image_id: int, pin: bool = True):

@@ -367,3 +367,39 @@ def test_serving_alone_equals_mix(gm, facade_scene):
         np.testing.assert_array_equal(got, batch_rows[7])
         ss = ctx.serving_stats()
         assert ss["completed"] == len(pairs) + 1 and ss["failed"] == 0
+
+
+@pytest.mark.parametrize("path", PATHS, ids=[p[0] for p in PATHS])
+def test_extreme_descriptors_exact(gm, path):
+    """Distances at the top of the range (descriptors of 0 and 255 only, D up to 128 * 255^2 < 2^23) decide the
+    ratio test exactly: a query of zeros against all-255 (D2 = 8323200) and 81 x 255 + v (D1 = 5267025 + v^2)
+    matches for v = 244 (25 D1 = 133164025 < 16 D2 = 133171200) and not for v = 245 (133176250); random 0/255
+    descriptors besides, in every band setting, equal the oracle."""
+    rng = np.random.default_rng(17)
+    W, H = 256, 256
+    def img(desc):
+        n = len(desc)
+        xy = np.stack([rng.uniform(0, W, n), rng.uniform(0, H, n)], 1).astype(np.float32)
+        return scenes.Image(W, H, xy, np.ones(n, np.float32), np.asarray(desc, np.uint8), np.full(n, -1, np.int32))
+    zeros = np.zeros((4, 128), np.uint8)
+    def near(v):
+        d = np.zeros(128, np.uint8)
+        d[:81] = 255
+        d[81] = v
+        return d
+    full = np.full(128, 255, np.uint8)
+    binary = (rng.integers(0, 2, (300, 128)) * 255).astype(np.uint8)
+    alt = np.tile(np.array([0, 255], np.uint8), 64)
+    images = [img(zeros), img([full, near(244)]), img([full, near(245)]),
+              img(np.concatenate([binary, alt[None], alt[::-1][None], zeros[:1], full[None]])),
+              img(np.concatenate([binary[::-1], full[None], alt[None]]))]
+    F = scenes.random_small(3, 4, 4, w=W, h=H).pairs[0].F
+    pairs = [scenes.Pair(0, 1, F, math.inf), scenes.Pair(0, 2, F, math.inf), scenes.Pair(3, 4, F, math.inf),
+             scenes.Pair(4, 3, F, math.inf), scenes.Pair(3, 4, F, 20.0)]
+    sc = scenes.Scene("extremes", images, pairs)
+    rows, _ = _gpu_rows(gm, sc, path=path[1], group=path[2])
+    for k, pr in enumerate(pairs):
+        want, _ = _oracle_rows(sc, pr)
+        np.testing.assert_array_equal(rows[k], want, err_msg=f"pair {k}")
+    assert rows[0].shape[0] == 4 and (rows[0][:, 1] == 1).all()   # every zero query picks 81 x 255 + 244
+    assert rows[1].shape[0] == 0
