@@ -800,6 +800,7 @@ void evict_lru_images(gm_ctx *ctx, const gm_image *imgs, int32_t count, int64_t 
 gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t on_device, const char *fn,
                      bool internal)
 {
+    gm::NvtxRange nvtx_(fn);
     if (!ctx) return fail(GM_ERR_INVALID, "%s: null context", fn);
     if (count < 0 || (count > 0 && !imgs) || (on_device != 0 && on_device != 1))
         return fail(GM_ERR_INVALID, "%s: bad arguments", fn);
@@ -1173,6 +1174,7 @@ gm_status gm_image_cache_stats(gm_ctx *ctx, int64_t *images, int64_t *bytes, int
 gm_status gm_match_pairs(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int64_t *pair_off, int32_t *matches,
                          int64_t cap, int64_t *n_written)
 {
+    gm::NvtxRange nvtx_("gm_match_pairs");
     if (!ctx) return fail(GM_ERR_INVALID, "gm_match_pairs: null context");
     if (n_pairs < 0 || (n_pairs > 0 && !pairs) || !pair_off || !n_written || cap < 0 || (cap > 0 && !matches))
         return fail(GM_ERR_INVALID, "gm_match_pairs: bad arguments");

@@ -555,6 +555,7 @@ gm_status gm_match_pairs_approx(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pai
                                 int64_t *pair_off, int32_t *matches, int64_t cap, int64_t *n_written,
                                 gm_approx_stats *stats)
 {
+    gm::NvtxRange nvtx_("gm_match_pairs_approx");
     using namespace gm;
     const char *fn = "gm_match_pairs_approx";
     if (!ctx || n_pairs < 0 || (n_pairs > 0 && !pairs) || !pair_off || !n_written || cap < 0 || (cap > 0 && !matches) ||

@@ -440,6 +440,7 @@ gm_status gm_coarse_selection(gm_ctx *ctx, int32_t image_id, const gm_coarse_opt
 gm_status gm_match_coarse(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, const gm_coarse_opts *opts,
                           int64_t *pair_off, int32_t *matches, int64_t cap, int64_t *n_written, int32_t *second)
 {
+    gm::NvtxRange nvtx_("gm_match_coarse");
     using namespace gm;
     const char *fn = "gm_match_coarse";
     if (!ctx || n_pairs < 0 || (n_pairs > 0 && !pairs) || !pair_off || !n_written || cap < 0 || (cap > 0 && !matches))

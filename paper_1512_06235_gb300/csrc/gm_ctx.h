@@ -2,6 +2,7 @@
 // loop (gm_serve.cu).  C++ only; not part of the public ABI.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <condition_variable>
 #include <cstdint>
@@ -154,6 +155,14 @@ struct gm_ctx {
 };
 
 namespace gm {
+
+// NVTX range over one entry point (visible in Nsight timelines; a no-op when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 gm_status fail(gm_status st, const char *fmt, ...);
 size_t align_up(size_t v, size_t a);

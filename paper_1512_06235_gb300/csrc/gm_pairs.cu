@@ -224,6 +224,7 @@ gm_status gm_select_pairs(gm_ctx *ctx, int32_t n_cams, int64_t n_points, const i
                           const int32_t *point_cams, int32_t threshold, int32_t top_k, int32_t *pairs, int64_t cap,
                           int64_t *n_written)
 {
+    gm::NvtxRange nvtx_("gm_select_pairs");
     using namespace gm;
     if (!ctx || n_cams < 0 || n_cams > kMaxCams || n_points < 0 || (n_points > 0 && (!point_off || !point_cams)) ||
         threshold < -1 || top_k < 0 || cap < 0 || (cap > 0 && !pairs) || !n_written)

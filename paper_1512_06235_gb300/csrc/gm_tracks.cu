@@ -114,6 +114,7 @@ extern "C" {
 gm_status gm_merge_tracks(gm_ctx *ctx, int64_t n_nodes, int64_t n_edges, const int64_t *edges, int64_t *labels,
                           int64_t *n_tracks)
 {
+    gm::NvtxRange nvtx_("gm_merge_tracks");
     using namespace gm;
     if (!ctx || n_nodes < 0 || n_edges < 0 || (n_edges > 0 && !edges) || (n_nodes > 0 && !labels) || !n_tracks)
         return fail(GM_ERR_INVALID, "gm_merge_tracks: bad arguments");

@@ -135,6 +135,7 @@ gm_status gm_triangulate(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids
                          const int64_t *labels, int64_t cap, double *X, int64_t *roots, int32_t *n_views,
                          int64_t *n_tracks)
 {
+    gm::NvtxRange nvtx_("gm_triangulate");
     using namespace gm;
     if (!ctx || n_images < 0 || (n_images > 0 && (!image_ids || !P)) || n_nodes < 0 || (n_nodes > 0 && !labels) ||
         cap < 0 || (cap > 0 && (!X || !roots || !n_views)) || !n_tracks)
