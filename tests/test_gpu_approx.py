@@ -53,6 +53,20 @@ def test_two_view(gm, two_view_scene, cell_scale):
         assert off[1] > 500 and st["n_groups"] > 50
 
 
+def test_facade_full_batch_sampled(gm, facade_scene):
+    """The whole 1200-pair facade batch in one call (the benchmark's launch); eight sampled pairs against the
+    oracle."""
+    sc = facade_scene
+    with gm.Context(device=0) as ctx:
+        ctx.put_images({k: im for k, im in enumerate(sc.images)})
+        off, m, st = ctx.match_pairs_approx([gm.make_pair(p.a, p.b, p.F, p.d, p.p, p.q) for p in sc.pairs])
+    pick = np.random.default_rng(12).choice(len(sc.pairs), 8, replace=False)
+    rows, _, _ = _want(sc.images, [sc.pairs[k] for k in pick], 1.0)
+    for k, r in zip(pick, rows):
+        np.testing.assert_array_equal(m[off[k]:off[k + 1]], r, err_msg=f"pair {k}")
+    assert st["n_groups"] > 100000
+
+
 def test_facade_pairs(gm, facade_scene):
     sc = facade_scene
     pairs = sc.pairs[:6]

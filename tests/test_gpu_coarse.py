@@ -156,6 +156,22 @@ def test_device_outputs_cap_and_refresh(gm, small_facade):
         assert e.value.status == gm.GM_ERR_NOT_FOUND
 
 
+def test_full_facade_all_pairs_sampled(gm, facade_scene):
+    """The benchmark's launch: every unordered pair of the 100 facade images (4950) in one call; 40 sampled pairs
+    against the oracle, rows and second-batch flags."""
+    sc = facade_scene
+    n = len(sc.images)
+    pairs = [SimpleNamespace(a=a, b=b, p=4, q=5) for a in range(n) for b in range(a + 1, n)]
+    with gm.Context(device=0) as ctx:
+        ctx.put_images({k: im for k, im in enumerate(sc.images)})
+        off, m, sec = ctx.match_coarse(pairs)
+    pick = np.random.default_rng(9).choice(len(pairs), 40, replace=False)
+    want = oc.match_coarse(sc.images, [pairs[k] for k in pick])
+    for k, (rows, ran) in zip(pick, want):
+        np.testing.assert_array_equal(m[off[k]:off[k + 1]], rows, err_msg=f"pair {k}")
+        assert bool(sec[k]) == ran
+
+
 def test_errors(gm):
     rng = np.random.default_rng(2)
     n = 1200
