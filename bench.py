@@ -136,6 +136,34 @@ def _profiled_traffic(kernel, src_file, workload):
         return None
 
 
+class _GcPauses:
+    """Times the interpreter's garbage-collection pauses inside a load-generator loop (after collecting and freezing
+    the heap built before it), so that a latency tail can be told apart from the library's own."""
+
+    def __enter__(self):
+        import gc
+        gc.collect()
+        gc.freeze()
+        self.pauses, self._t = [], None
+
+        def cb(phase, info):
+            if phase == "start":
+                self._t = time.perf_counter()
+            elif self._t is not None:
+                self.pauses.append(time.perf_counter() - self._t)
+        self._cb = cb
+        gc.callbacks.append(cb)
+        return self
+
+    def __exit__(self, *exc):
+        import gc
+        gc.callbacks.remove(self._cb)
+        gc.unfreeze()
+
+    def summary(self):
+        return {"gc_collections": len(self.pauses), "gc_max_pause_ms": max(self.pauses, default=0.0) * 1e3}
+
+
 def _serving(gm, ctx, pairs, rate, seconds, seed=1512):
     """Poisson arrivals of single-pair requests (drawn from the batch's pairs) at `rate` req/s for `seconds`,
     through gm_submit / gm_poll on the resident images; per-request latency from submission to completion."""
@@ -144,74 +172,91 @@ def _serving(gm, ctx, pairs, rate, seconds, seed=1512):
     gaps = rng.exponential(1.0 / rate, n)
     picks = rng.integers(0, len(pairs), n)
     tickets = []
-    t0 = time.perf_counter()
-    t_next = t0
-    for k in range(n):
-        t_next += gaps[k]
-        while time.perf_counter() < t_next:
-            pass
-        tickets.append(ctx.submit(pairs[picks[k]]))
-    lat = []
-    for t in tickets:
-        _, us = ctx.poll(t, timeout_ms=60000)
-        lat.append(us)
-    wall = time.perf_counter() - t0
+    with _GcPauses() as gcp:
+        t0 = time.perf_counter()
+        t_next = t0
+        for k in range(n):
+            t_next += gaps[k]
+            while time.perf_counter() < t_next:
+                pass
+            tickets.append(ctx.submit(pairs[picks[k]]))
+        lat = []
+        for t in tickets:
+            _, us = ctx.poll(t, timeout_ms=60000)
+            lat.append(us)
+        wall = time.perf_counter() - t0
     ss = ctx.serving_stats()
     lat = np.asarray(lat)
     return {"rate_req_s": rate, "requests": n, "seconds": wall, "throughput_req_s": n / wall,
             "p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3,
             "batches": ss["batches"], "max_batch_pairs": ss["max_batch_pairs"],
-            "peak_inflight_batches": ss["peak_inflight_batches"],
+            "peak_inflight_batches": ss["peak_inflight_batches"], "max_ms": float(lat.max()) / 1e3, **gcp.summary(),
             "requests_from": "pairs of the batch workload, 1 pair per request, resident images"}
 
 
-def _serving_cache(gm, ctx, sc, pairs, images, rate, seconds, seed=1513):
+def _serving_cache(gm, ctx, sc, pairs, images, rate, seconds, seed=1513, warmup=32):
     """Poisson single-pair requests under a memory budget that holds about a fifth of the images: a request whose
     images are resident is submitted at once (hit); otherwise its missing images are put first (cold: upload and
-    binning, with least-recently-used eviction making room).  Latency from arrival to completion."""
+    binning, with least-recently-used eviction making room).  Latency from arrival to completion.  A warm-up of
+    `warmup` requests (first use of the context's work buffers) runs first and is not counted."""
     rng = np.random.default_rng(seed)
     n = max(1, int(rate * seconds))
     gaps = rng.exponential(1.0 / rate, n)
     picks = rng.integers(0, len(pairs), n)
+    for k in rng.integers(0, len(pairs), warmup):
+        ctx.poll(_serve_one(gm, ctx, pairs[k], images)[0], timeout_ms=60000)
+    evicted0 = gm.gm_image_cache_stats(ctx.h)["evicted"]
     reqs = []
-    t0 = time.perf_counter()
-    t_next = t0
-    for k in range(n):
-        t_next += gaps[k]
-        while time.perf_counter() < t_next:
-            pass
-        p = pairs[picks[k]]
-        missing = [i for i in {p.img_a, p.img_b} if gm.gm_image_info(ctx.h, i) is None]
-        held = [i for i in {p.img_a, p.img_b} if i not in missing]
-        for i in held:   # a resident image of the request stays while the other one is put
-            gm.gm_image_pin(ctx.h, i, True)
-        cold = bool(missing)
-        if missing:   # both images in one call, so that neither is evicted to make room for the other
-            batch = gm.make_images([images[i] for i in missing])
-            try:
-                gm.gm_images_put(ctx.h, batch)
-            except gm.GeomatchError as e:   # every resident image is still needed: let the queue drain
-                if e.status != gm.GM_ERR_BUDGET:
-                    raise
-                gm.gm_serving_drain(ctx.h)
-                gm.gm_images_put(ctx.h, batch)
-        reqs.append((ctx.submit(p), time.perf_counter() - t_next, cold))   # the queued request protects both now
-        for i in held:
-            gm.gm_image_pin(ctx.h, i, False)
-    lat = {True: [], False: []}
-    for t, wait_s, cold in reqs:
-        _, us = ctx.poll(t, timeout_ms=60000)
-        lat[cold].append(wait_s * 1e3 + us / 1e3)
-    wall = time.perf_counter() - t0
+    with _GcPauses() as gcp:
+        t0 = time.perf_counter()
+        t_next = t0
+        for k in range(n):
+            t_next += gaps[k]
+            while time.perf_counter() < t_next:
+                pass
+            t, cold = _serve_one(gm, ctx, pairs[picks[k]], images)
+            reqs.append((t, time.perf_counter() - t_next, cold, t_next - t0))
+        lat = {True: [], False: []}
+        worst = []
+        for k, (t, wait_s, cold, at) in enumerate(reqs):
+            _, us = ctx.poll(t, timeout_ms=60000)
+            ms = wait_s * 1e3 + us / 1e3
+            lat[cold].append(ms)
+            worst.append((ms, k, cold, at * 1e3, wait_s * 1e3))
+        wall = time.perf_counter() - t0
     c = gm.gm_image_cache_stats(ctx.h)
     out = {"rate_req_s": rate, "requests": n, "seconds": wall, "throughput_req_s": n / wall,
-           "hits": len(lat[False]), "cold": len(lat[True]), "images_evicted": c["evicted"],
-           "resident_images_at_end": c["images"]}
+           "hits": len(lat[False]), "cold": len(lat[True]), "images_evicted": c["evicted"] - evicted0,
+           "resident_images_at_end": c["images"], "warmup_requests": warmup, **gcp.summary(),
+           "worst": [{"ms": round(w[0], 3), "request": w[1], "cold": w[2], "arrival_ms": round(w[3], 1),
+                      "late_at_submit_ms": round(w[4], 3)} for w in sorted(worst, reverse=True)[:5]]}
     for key, v in (("hit", lat[False]), ("cold", lat[True])):
         if v:
             out[f"{key}_p50_ms"] = float(np.percentile(v, 50))
             out[f"{key}_p99_ms"] = float(np.percentile(v, 99))
     return out
+
+
+def _serve_one(gm, ctx, p, images):
+    """One request of the budgeted serving leg: put its missing images, then submit.  Returns (ticket, cold)."""
+    missing = [i for i in {p.img_a, p.img_b} if gm.gm_image_info(ctx.h, i) is None]
+    held = [i for i in {p.img_a, p.img_b} if i not in missing]
+    for i in held:   # a resident image of the request stays while the other one is put
+        gm.gm_image_pin(ctx.h, i, True)
+    cold = bool(missing)
+    if missing:   # both images in one call, so that neither is evicted to make room for the other
+        batch = gm.make_images([images[i] for i in missing])
+        try:
+            gm.gm_images_put(ctx.h, batch)
+        except gm.GeomatchError as e:   # every resident image is still needed: let the queue drain
+            if e.status != gm.GM_ERR_BUDGET:
+                raise
+            gm.gm_serving_drain(ctx.h)
+            gm.gm_images_put(ctx.h, batch)
+    t = ctx.submit(p)   # the queued request protects both images now
+    for i in held:
+        gm.gm_image_pin(ctx.h, i, False)
+    return t, cold
 
 
 def _oracle_comparisons(sc, pairs, n_sample=200, seed=1512):
