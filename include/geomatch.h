@@ -213,7 +213,7 @@ GM_API gm_status gm_merge_tracks(gm_ctx *ctx, int64_t n_nodes, int64_t n_edges, 
  * FP64 (NaN if the system is singular; the FP64 sums run in a data-dependent order, so the last bits may differ
  * between calls).  Outputs (cap rows each): X double [cap][3], roots int64 [cap] (the track's smallest node),
  * n_views int32 [cap]; *n_tracks = number of tracks.  If it exceeds cap, nothing is written and the call returns
- * GM_ERR_NOMEM.  P, labels and the outputs may each be host or device memory (X, roots and n_views all alike).
+ * GM_ERR_NOMEM.  P, labels and the outputs may each be host or device memory (X, roots and n_views all alike, else GM_ERR_INVALID).
  * Errors: GM_ERR_INVALID, GM_ERR_NOT_FOUND (an image not put), GM_ERR_NOMEM, GM_ERR_CUDA. */
 GM_API gm_status gm_triangulate(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids, const double *P,
                                 int64_t n_nodes, const int64_t *labels, int64_t cap, double *X, int64_t *roots,
@@ -243,7 +243,7 @@ GM_API gm_status gm_coarse_prepare(gm_ctx *ctx, int32_t n_images, const int32_t 
                                    const gm_coarse_opts *opts);
 
 /* The selection of one image as ascending feature indices: q1 (first query batch), q2 (second query batch) and t
- * (targets), cap entries each (host or device, all alike); counts[3] (host) receives their sizes.  If a size
+ * (targets), cap entries each (host or device, all alike, else GM_ERR_INVALID); counts[3] (host) receives their sizes.  If a size
  * exceeds cap nothing is written and the call returns GM_ERR_NOMEM.  Builds the views if needed. */
 GM_API gm_status gm_coarse_selection(gm_ctx *ctx, int32_t image_id, const gm_coarse_opts *opts, int32_t *q1,
                                      int32_t *q2, int32_t *t, int32_t cap, int32_t *counts);

@@ -511,9 +511,15 @@ gm_status gm_create(const gm_config *cfg, gm_ctx **out)
         cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_desc, cudaEventDisableTiming) != cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        workspace_free(ctx, ctx->ws2);   // whatever was created: events and streams (no buffers yet)
+        workspace_free(ctx, ctx->ws);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        if (ctx->ev_stage) cudaEventDestroy(ctx->ev_stage);
+        if (ctx->ev_desc) cudaEventDestroy(ctx->ev_desc);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
-        return GM_ERR_CUDA;
+        return fail(GM_ERR_CUDA, "gm_create: stream or event creation failed: %s", cudaGetErrorString(e));
     }
     *out = ctx;
     return GM_OK;
@@ -816,12 +822,22 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     GM_CUDA(cudaSetDevice(ctx->device));
     std::vector<ImageLayout> L(count);
+    // page-locked inputs are read by the binning kernels in place (one pass over the link, no staging copy)
+    std::vector<const void *> in_xy(count, nullptr), in_desc(count, nullptr);
     size_t stage_bytes = 0, new_bytes = 0, replaced = 0;
     for (int32_t k = 0; k < count; ++k) {
         const gm_image &g = imgs[k];
         L[k] = image_layout(ctx, g.width, g.height, g.n);
         if (L[k].m + 2 > INT32_MAX / 4) return fail(GM_ERR_INVALID, "%s: grid too large (image %d)", fn, g.image_id);
-        if (!on_device) stage_bytes += align_up(8 * (size_t)g.n + 1, 256) + align_up(128 * (size_t)g.n + 1, 256);
+        if (!on_device && g.n > 0) {
+            const void *mxy = mapped_host_ptr(g.xy), *mds = mxy ? mapped_host_ptr(g.desc) : nullptr;
+            if (mxy && mds && (reinterpret_cast<uintptr_t>(mxy) & 7) == 0) {
+                in_xy[k] = mxy;
+                in_desc[k] = mds;
+            } else {
+                stage_bytes += align_up(8 * (size_t)g.n + 1, 256) + align_up(128 * (size_t)g.n + 1, 256);
+            }
+        }
         auto it = ctx->images.find(g.image_id);
         const bool reuse = it != ctx->images.end() && it->second->bytes >= L[k].tot;
         if (!reuse) {
@@ -841,10 +857,10 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
     // 1. stage host inputs and check every keypoint (nothing registered is touched yet)
     std::vector<const float2 *> raw_xy(count);
     std::vector<const uint8_t *> raw_desc(count);
-    if (!on_device && (st = ensure_dev(ctx, ctx->d_stage, stage_bytes + 256)) != GM_OK) return st;
+    if (stage_bytes && (st = ensure_dev(ctx, ctx->d_stage, stage_bytes + 256)) != GM_OK) return st;
     // coordinates go up on the stream (the keypoint check needs them); descriptors on the copy stream, so that their
     // upload overlaps the check and is waited for only before the descriptors are binned
-    const bool side = !on_device && ctx->copy_stream;
+    const bool side = stage_bytes && ctx->copy_stream;
     if (side) {
         // the staging area is free once earlier work on s and an earlier call's uploads (even one that failed before
         // its binning) are done
@@ -859,11 +875,9 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             raw_xy[k] = reinterpret_cast<const float2 *>(g.xy);
             raw_desc[k] = g.desc;
             if (on_device || g.n == 0) continue;
-            // page-locked inputs are read by the binning kernels in place (one pass over the link, no staging copy)
-            const void *mxy = mapped_host_ptr(g.xy), *mds = mxy ? mapped_host_ptr(g.desc) : nullptr;
-            if (mxy && mds && (reinterpret_cast<uintptr_t>(mxy) & 7) == 0) {
-                raw_xy[k] = static_cast<const float2 *>(mxy);
-                raw_desc[k] = static_cast<const uint8_t *>(mds);
+            if (in_xy[k]) {
+                raw_xy[k] = static_cast<const float2 *>(in_xy[k]);
+                raw_desc[k] = static_cast<const uint8_t *>(in_desc[k]);
                 continue;
             }
             const size_t N = (size_t)g.n, xy_al = align_up(8 * N + 1, 256);
@@ -942,6 +956,35 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             }
         }
     }
+    // 4. what can still fail comes before the install, so that a failed call leaves every registered image as it
+    // was: the slots of new images, the device tables grown to hold them (old entries kept) and the TMA descriptors
+    // of each image (tcgen05 path)
+    std::vector<int32_t> slot_of(count, -1);
+    size_t n_slots = ctx->slots.size();
+    {
+        size_t q = 0;
+        for (int32_t k = 0; k < count; ++k) {
+            if (ctx->images.count(imgs[k].image_id)) continue;
+            while (q < ctx->slots.size() && ctx->slots[q]) ++q;
+            slot_of[k] = (int32_t)(q < ctx->slots.size() ? q++ : n_slots++);
+        }
+    }
+    if (st == GM_OK && e == cudaSuccess)
+        st = grow_table(ctx, ctx->d_imgs, sizeof(ImageDev) * n_slots, 4096, s, "image");
+    if (st == GM_OK && e == cudaSuccess)
+        st = grow_table(ctx, ctx->d_maps, sizeof(TmaMaps) * n_slots, sizeof(TmaMaps) * 16, s, "TMA descriptor");
+    // the TMA descriptors depend only on the descriptor rows, the records and n: a re-put into the same block with
+    // as many keypoints keeps them
+    std::vector<TmaMaps> maps(count);
+    std::vector<char> same_maps(count, 0);
+    for (int32_t k = 0; k < count && st == GM_OK && e == cudaSuccess; ++k) {
+        auto it = ctx->images.find(imgs[k].image_id);
+        const ImageDev *old = it != ctx->images.end() ? &it->second->dev : nullptr;
+        same_maps[k] = imgs[k].n > 0 && old && old->n == dev[k].n && old->desc_h == dev[k].desc_h &&
+                       old->rec == dev[k].rec;
+        std::memset(&maps[k], 0, sizeof(TmaMaps));
+        if (!same_maps[k] && imgs[k].n > 0) st = encode_maps(dev[k], maps[k]);
+    }
     if (st != GM_OK || e != cudaSuccess) {
         cudaStreamSynchronize(s);
         if (slab) {   // no image holds it yet
@@ -950,7 +993,8 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
         }
         return st != GM_OK ? st : fail(GM_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     }
-    // 4. install: replace or take a free slot; TMA descriptors of each image (tcgen05 path)
+    // 5. install: replace, or take the slot chosen above
+    if (ctx->slots.size() < n_slots) ctx->slots.resize(n_slots, nullptr);
     for (int32_t k = 0; k < count; ++k) {
         const gm_image &g = imgs[k];
         auto it = ctx->images.find(g.image_id);
@@ -969,15 +1013,8 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
         } else {
             img = new ImageSlot();
             img->id = g.image_id;
-            int slot = -1;
-            for (size_t q = 0; q < ctx->slots.size(); ++q)
-                if (!ctx->slots[q]) { slot = (int)q; break; }
-            if (slot < 0) {
-                slot = (int)ctx->slots.size();
-                ctx->slots.push_back(nullptr);
-            }
-            img->slot = slot;
-            ctx->slots[slot] = img;
+            img->slot = slot_of[k];
+            ctx->slots[img->slot] = img;
             ctx->images[g.image_id] = img;
             img->block = block[k];
             img->slab = slab;
@@ -985,27 +1022,14 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
             img->bytes = L[k].tot;
             ctx->bytes_images += L[k].tot;
         }
-        // the TMA descriptors depend only on the descriptor rows, the records and n: a re-put into the same block
-        // with as many keypoints keeps them
-        const bool same_maps = g.n > 0 && img->dev.n == dev[k].n && img->dev.desc_h == dev[k].desc_h &&
-                               img->dev.rec == dev[k].rec;
         img->dev = dev[k];
         img->gen = ++ctx->image_gen;
         img->last_use = ++ctx->use_tick;
         img->scale = reinterpret_cast<const float *>(static_cast<char *>(img->block) + L[k].offs[10]);
         img->has_scale = g.n > 0 && g.scale != nullptr;
-        if (!same_maps) {
-            TmaMaps maps;
-            std::memset(&maps, 0, sizeof(maps));
-            if (g.n > 0 && (st = encode_maps(img->dev, maps)) != GM_OK) return st;
-            img->maps = maps;
-        }
+        if (!same_maps[k]) img->maps = maps[k];
     }
-    // 5. device tables (grow keeps old entries), one copy each of every slot's entry
-    if ((st = grow_table(ctx, ctx->d_imgs, sizeof(ImageDev) * ctx->slots.size(), 4096, s, "image")) != GM_OK) return st;
-    if ((st = grow_table(ctx, ctx->d_maps, sizeof(TmaMaps) * ctx->slots.size(), sizeof(TmaMaps) * 16, s, "TMA descriptor"))
-        != GM_OK)
-        return st;
+    // 6. the device tables' entries: one copy each of every slot's entry
     std::vector<ImageDev> tab_dev;
     std::vector<TmaMaps> tab_maps;
     if (count >= 8) {   // many images: both whole tables in two copies instead of two per image

@@ -423,6 +423,8 @@ gm_status gm_coarse_selection(gm_ctx *ctx, int32_t image_id, const gm_coarse_opt
     cudaStream_t s = ctx->ws.stream;
     int32_t *dst[3] = {q1, q2, t};
     const bool dev = cap > 0 && is_device_ptr(q1);
+    if (cap > 0 && (is_device_ptr(q2) != dev || is_device_ptr(t) != dev))
+        return fail(GM_ERR_INVALID, "gm_coarse_selection: q1, q2 and t must all be host or all device memory");
     for (int k = 0; k < 3; ++k) {
         if (v.n[k] == 0) continue;
         if (v.all) {

@@ -205,6 +205,8 @@ gm_status gm_triangulate(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids
     if (nt == 0) return GM_OK;
     // per-track accumulators and outputs (device; copied out when the caller's buffers are host memory)
     const bool dev_o = is_device_ptr(X);
+    if (is_device_ptr(roots) != dev_o || is_device_ptr(n_views) != dev_o)
+        return fail(GM_ERR_INVALID, "gm_triangulate: X, roots and n_views must all be host or all device memory");
     const size_t acc_b = align_up(sizeof(double) * 9 * nt, 256), x_b = align_up(sizeof(double) * 3 * nt, 256);
     const size_t r_b = align_up(sizeof(int64_t) * nt, 256), v_b = align_up(sizeof(int32_t) * nt, 256);
     if ((st = ensure_dev(ctx, ctx->d_tri_out, acc_b + (dev_o ? 0 : x_b + r_b + v_b))) != GM_OK) return st;

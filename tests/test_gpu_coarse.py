@@ -143,6 +143,11 @@ def test_device_outputs_cap_and_refresh(gm, small_facade):
         with pytest.raises(gm.GeomatchError) as e:
             gm.gm_match_coarse(ctx.h, pairs, np.empty(len(pairs) + 1, np.int64), small, total - 1)
         assert e.value.status == gm.GM_ERR_NOMEM and e.value.required == total and (small == -7).all()
+        # selection lists of mixed kinds (device q1, host q2 and t) are refused, nothing written
+        q1 = torch.full((8000,), -5, dtype=torch.int32, device="cuda:0")
+        with pytest.raises(gm.GeomatchError) as e:
+            gm.gm_coarse_selection(ctx.h, 0, q1, np.empty(8000, np.int32), np.empty(8000, np.int32), 8000)
+        assert e.value.status == gm.GM_ERR_INVALID and bool((q1 == -5).all())
         # putting an image again with other scales refreshes its views
         im = sc.images[0]
         rev = SimpleNamespace(width=im.width, height=im.height, xy=im.xy, desc=im.desc, scale=im.scale[::-1].copy())

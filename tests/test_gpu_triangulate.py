@@ -192,3 +192,9 @@ def test_cap_and_errors(gm):
         with pytest.raises(gm.GeomatchError) as e:
             gm.gm_triangulate(ctx.h, ids, P, lab2, np.empty((T, 3)), np.empty(T, np.int64), np.empty(T, np.int32), T)
         assert e.value.status == gm.GM_ERR_INVALID
+        # outputs of mixed kinds (device X, host roots and n_views) are refused before any kernel runs
+        import torch
+        Xd = torch.full((T, 3), 7.0, dtype=torch.float64, device="cuda:0")
+        with pytest.raises(gm.GeomatchError) as e:
+            gm.gm_triangulate(ctx.h, ids, P, labels, Xd, np.empty(T, np.int64), np.empty(T, np.int32), T)
+        assert e.value.status == gm.GM_ERR_INVALID and bool((Xd == 7.0).all())
