@@ -349,7 +349,9 @@ GM_API gm_status gm_submit(gm_ctx *ctx, const gm_pair *pair, uint64_t *ticket);
 /* Waits up to timeout_ms (0 = do not wait, < 0 = wait without limit) for request `ticket`, then writes its
  * matches (int32 [cap][2] rows (i_A, j_B), sorted by i) and *n.  Returns GM_ERR_TIMEOUT if the request is not
  * done yet (the ticket stays valid), GM_ERR_NOMEM if cap < *n (the ticket stays valid), GM_ERR_NOT_FOUND for an
- * unknown or already collected ticket, or the request's own error.  A collected ticket is released.
+ * unknown or already collected ticket, or the request's own error (a device-side wait that ran out inside its
+ * batch is GM_ERR_CUDA here, so that GM_ERR_TIMEOUT from gm_poll always means "not done yet").  A collected
+ * ticket is released.
  * If latency_us is not NULL it receives the request's submit-to-completion time in microseconds. */
 GM_API gm_status gm_poll(gm_ctx *ctx, uint64_t ticket, int32_t *matches, int64_t cap, int64_t *n, int32_t timeout_ms,
                   double *latency_us);

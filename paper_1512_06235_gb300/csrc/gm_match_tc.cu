@@ -11,12 +11,12 @@
 //       its candidate stream (positions computed beforehand by gm_stream.cu: the chord-bounded cell walk of the
 //       whole group) into shared memory; everything comes from the group's descriptor, loaded well before the slot
 //       frees.  Chunk loads: 64 stream positions at a time, the fp16 descriptor rows (two K halves) and a 16-byte
-//       record per candidate (x, y, |b'|^2 * 256, position) into a 4-stage ring: scattered rows by TMA gather4
+//       record per candidate (x, y, |b'|^2 * 256, position) into a 6-stage ring: scattered rows by TMA gather4
 //       (records by cp.async, completion through cp.async.mbarrier.arrive), the contiguous rows of whole-image
 //       groups by TMA tile loads (64-row boxes, 128-byte swizzle; rows past the image read as NaN records); slots
 //       past the end of a stream get the image's NaN sentinel record;
 //   MMA warp (one elected thread): eight tcgen05.mma.kind::f16 per chunk (M = 128, N = 64, K = 16 each), f32
-//       accumulation into one of two tensor-memory buffers.  Products are integers of magnitude <= 2^14 and partial
+//       accumulation into one of four tensor-memory buffers.  Products are integers of magnitude <= 2^14 and partial
 //       sums <= 2^21 < 2^24, so the accumulator holds the exact integer dot product a'.b';
 //   epilogue warps (8 = 4 lane quadrants x 2 column halves): each thread derives its query's FP32 line and
 //       exact-decision thresholds (gm_band.cuh), then per chunk tcgen05.ld of 32 accumulator columns and per element
@@ -44,10 +44,10 @@ namespace {
 
 constexpr int kM = 128;             // queries per group (tensor-memory lanes)
 constexpr int kN = 64;              // candidates per chunk
-constexpr int kStages = 4;          // candidate chunks in flight
-constexpr int kAcc = 2;             // accumulator buffers in tensor memory
+constexpr int kStages = 6;          // candidate chunks in flight
+constexpr int kAcc = 4;             // accumulator buffers in tensor memory
 constexpr int kSlots = 3;           // query groups in flight
-constexpr int kPosCap = 3840;       // candidate positions a slot stages in shared memory (multiple of kN)
+constexpr int kPosCap = 1024;       // candidate positions a slot stages in shared memory (multiple of kN)
 constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
 constexpr int kEpiWarps = 8;
 constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;   // worker warps: 8, 10, 11
