@@ -41,6 +41,25 @@ def _dist():
     return rank, world, local
 
 
+def _facade_seed(rank: int) -> int:
+    """Seed of the facade component a rank matches.  Pairs are independent (Sec. 6.2), so under torchrun every rank
+    matches a component of its own (the paper matches its components separately): rank 0 the standard facade, rank r
+    the facade seeded 1000 r further on.  Nothing is exchanged between ranks on the data path."""
+    import scenes
+    return scenes.SEED_BASE + 2 + 1000 * rank
+
+
+def _reduce(x: float, op: str, world: int, device) -> float:
+    """The maximum ("max") or the sum ("sum") of a per-rank scalar over all ranks; x itself at world size 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def _load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -900,7 +919,7 @@ def main():
         else:
             run_serving(args, gm, dev, local)
         return
-    sc = scenes.facade()
+    sc = scenes.facade(seed=_facade_seed(rank))
     if args.pairs:
         sc.pairs = sc.pairs[:args.pairs]
     pairs = sc.pairs
@@ -945,12 +964,10 @@ def main():
     ms = float(np.mean(step_ms))
     ms_match = float(np.mean([s["ms_match"] for s in st_list]))
     st = st_list[-1]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * len(pairs) / (ms / 1e3)
-    comps_per_s = world * st["n_candidates"] / (ms / 1e3)
+    ms = _reduce(ms, "max", world, dev)                       # the slowest rank's step
+    units = _reduce(len(pairs), "sum", world, dev)            # pairs matched by all ranks in one step
+    value = units / (ms / 1e3)
+    comps_per_s = _reduce(st["n_candidates"], "sum", world, dev) / (ms / 1e3)
 
     # ---- end-to-end through the public API with host buffers (pinned): upload + binning + match + download
     pinned = []
@@ -978,6 +995,9 @@ def main():
 
     e2e_step()
     torch.cuda.synchronize(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.e2e_steps)]
     n_out = 0
     for k in range(args.e2e_steps):
@@ -986,7 +1006,7 @@ def main():
         n_out = e2e_step()
         e_ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in e_ev]))
+    e2e_ms = _reduce(float(np.mean([a.elapsed_time(b) for a, b in e_ev])), "max", world, dev)
     d2h = (len(pairs) + 1) * 8 + n_out * 8
     e2e_ctx.close()
 
@@ -1020,11 +1040,13 @@ def main():
             "config": {"workload": WORKLOAD if not args.pairs else f"{WORKLOAD}_first{args.pairs}", "pairs": len(pairs), "images": len(sc.images), "keypoints_per_image": 8000,
                        "band_px": 4.0, "ratio": 0.8, "cell_px": args.cell or "auto (4)", "group": args.group, "l2": "flushed between steps (512 MB write)",
                        "path": st["path_used"], "schedule": "persistent batch" if not args.schedule else "one pair per launch",
-                       "graph": not args.no_graph and not args.schedule},
+                       "graph": not args.no_graph and not args.schedule,
+                       "sharding": "one facade component per rank (pairs are independent); no collective on the "
+                                   "data path"},
             "comparisons_per_s": comps_per_s, "candidates_per_step": st["n_candidates"],
             "examined_per_step": st["n_examined"], "redecided_per_step": st["n_redecided"], "matches_per_step": st["n_matches"],
             "ms_match_kernel": ms_match,
-            "e2e": {"value": world * len(pairs) / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(args.steps * st["kernel_launches"]),
             "roofline": roofline, "clocks": clocks}
@@ -1036,6 +1058,7 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
 
