@@ -139,7 +139,9 @@ GM_API gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value);
  *          0 <= y < height (otherwise GM_ERR_INVALID);
  *   scale: float32 [n] keypoint scales (stored, not used by the matching; may be NULL);
  *   desc:  uint8 [n][128] SIFT descriptors, row-major;
- *   on_device: 0 = the three pointers are host memory, 1 = device memory of the context's device.
+ *   on_device: 0 = the three pointers are host memory, 1 = device memory of the context's device (then xy must
+ *          be 8-byte and desc 16-byte aligned, otherwise GM_ERR_INVALID).  Page-locked host inputs with those
+ *          alignments are read in place by the kernels; other host inputs are staged.
  * n may be 0.  Errors: GM_ERR_INVALID, GM_ERR_BUDGET (the resident image would exceed the budget),
  * GM_ERR_NOMEM, GM_ERR_CUDA. */
 GM_API gm_status gm_image_put(gm_ctx *ctx, int32_t image_id, int32_t width, int32_t height, int32_t n,

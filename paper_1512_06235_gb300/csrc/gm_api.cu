@@ -829,9 +829,13 @@ gm_status put_images(gm_ctx *ctx, int32_t count, const gm_image *imgs, int32_t o
         const gm_image &g = imgs[k];
         L[k] = image_layout(ctx, g.width, g.height, g.n);
         if (L[k].m + 2 > INT32_MAX / 4) return fail(GM_ERR_INVALID, "%s: grid too large (image %d)", fn, g.image_id);
+        if (on_device && g.n > 0 &&
+            ((reinterpret_cast<uintptr_t>(g.xy) & 7) != 0 || (reinterpret_cast<uintptr_t>(g.desc) & 15) != 0))
+            return fail(GM_ERR_INVALID, "%s: image %d: device xy must be 8-byte and desc 16-byte aligned", fn,
+                        g.image_id);
         if (!on_device && g.n > 0) {
             const void *mxy = mapped_host_ptr(g.xy), *mds = mxy ? mapped_host_ptr(g.desc) : nullptr;
-            if (mxy && mds && (reinterpret_cast<uintptr_t>(mxy) & 7) == 0) {
+            if (mxy && mds && (reinterpret_cast<uintptr_t>(mxy) & 7) == 0 && (reinterpret_cast<uintptr_t>(mds) & 15) == 0) {
                 in_xy[k] = mxy;
                 in_desc[k] = mds;
             } else {

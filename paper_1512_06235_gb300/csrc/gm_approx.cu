@@ -415,12 +415,19 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
                 lo[t] = cidx >= 0 ? __ldg(cell_off + cidx) : 0;
                 hi[t] = cidx >= 0 ? __ldg(cell_off + cidx + 1) : 0;
             }
+            // the cells' members, one from each of the lane's samples at a time (independent loads in flight
+            // together; the bitmap OR does not depend on the order)
+            int span = 0;
 #pragma unroll
-            for (int t = 0; t < kSampleBatch; ++t)
-                for (int32_t m = lo[t]; m < hi[t]; ++m) {
-                    const int32_t pos = __ldg(members + m);
-                    atomicOr(&bm[pos >> 5], 1u << (pos & 31));
-                }
+            for (int t = 0; t < kSampleBatch; ++t) span = max(span, hi[t] - lo[t]);
+            for (int i = 0; i < span; ++i) {
+                int32_t pos[kSampleBatch];
+#pragma unroll
+                for (int t = 0; t < kSampleBatch; ++t) pos[t] = lo[t] + i < hi[t] ? __ldg(members + lo[t] + i) : -1;
+#pragma unroll
+                for (int t = 0; t < kSampleBatch; ++t)
+                    if (pos[t] >= 0) atomicOr(&bm[pos[t] >> 5], 1u << (pos[t] & 31));
+            }
         }
         if (lane == 0) atomicAdd(&ctr->cells, (unsigned long long)(K + 1));
     }
@@ -483,16 +490,24 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
                 w0 += 32;
             }
             __syncwarp();
-            for (int32_t n0 = 0; n0 < nl; n0 += 8) {   // one n-tile of 8 candidates
-                const int cj = n0 + gq < nl ? list[n0 + gq] : list[n0];   // padding columns repeat a real one
+            // B fragments of n-tile n0 (8 candidates; padding columns repeat a real one), loaded one tile ahead
+            auto load_b = [&](int32_t n0, int (&bf)[8]) {
+                const int cj = n0 + gq < nl ? list[n0 + gq] : list[n0];
                 const int8_t *brow = B.desc + (size_t)cj * kDim + 4 * t4;
-                int acc[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
-                    const int b0 = __ldg(reinterpret_cast<const int *>(brow + ks * 32));
-                    const int b1 = __ldg(reinterpret_cast<const int *>(brow + ks * 32 + 16));
-                    mma_s8(acc, afr[ks], b0, b1);
+                    bf[2 * ks] = __ldg(reinterpret_cast<const int *>(brow + ks * 32));
+                    bf[2 * ks + 1] = __ldg(reinterpret_cast<const int *>(brow + ks * 32 + 16));
                 }
+            };
+            int bcur[8];
+            if (nl > 0) load_b(0, bcur);
+            for (int32_t n0 = 0; n0 < nl; n0 += 8) {   // one n-tile of 8 candidates
+                int bnext[8];
+                if (n0 + 8 < nl) load_b(n0 + 8, bnext);
+                int acc[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) mma_s8(acc, afr[ks], bcur[2 * ks], bcur[2 * ks + 1]);
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int col = n0 + 2 * t4 + e;
@@ -505,6 +520,10 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
                         if (D < D1[hh] || (D == D1[hh] && j < J1[hh])) { D2[hh] = D1[hh]; D1[hh] = D; J1[hh] = j; }
                         else if (D < D2[hh]) D2[hh] = D;
                     }
+                }
+                if (n0 + 8 < nl) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) bcur[u] = bnext[u];
                 }
             }
             __syncwarp();

@@ -168,35 +168,48 @@ __global__ void batch_scatter_kernel(const BucketJob *__restrict__ jobs, const i
     }
 }
 
+// Descriptors in cell order: eight lanes per keypoint, 16 bytes each (a warp moves four rows per load, so that
+// more bytes are in flight when the rows are read from page-locked host memory), recentred int8, fp16 and the norms.
 __global__ void batch_desc_kernel(const BucketJob *__restrict__ jobs, const int64_t *__restrict__ kp_prefix, int K,
                                   int64_t n_total)
 {
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (g >= n_total) return;
-    const int k = find_job(kp_prefix, K, g);
-    const BucketJob &J = jobs[k];
-    const int row = (int)(g - J.kp_base);
-    const int src = J.perm[row];
-    const uint32_t w = reinterpret_cast<const uint32_t *>(J.desc_raw + (int64_t)src * kDim)[lane] ^ 0x80808080u;
-    reinterpret_cast<uint32_t *>(J.desc + (int64_t)row * kDim)[lane] = w;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int part = threadIdx.x & 7;
+    const bool live = g < n_total;   // every lane takes part in the shuffles below
     int sq = 0;
-    uint32_t h01 = 0, h23 = 0;
+    const BucketJob *J = nullptr;
+    int row = 0;
+    if (live) {
+        const int k = find_job(kp_prefix, K, g);
+        J = &jobs[k];
+        row = (int)(g - J->kp_base);
+        const int src = J->perm[row];
+        uint4 w = reinterpret_cast<const uint4 *>(J->desc_raw + (int64_t)src * kDim)[part];
+        w.x ^= 0x80808080u; w.y ^= 0x80808080u; w.z ^= 0x80808080u; w.w ^= 0x80808080u;
+        reinterpret_cast<uint4 *>(J->desc + (int64_t)row * kDim)[part] = w;
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+        uint32_t h[8];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const int v = (int)(int8_t)((w >> (8 * t)) & 0xffu);
-        sq += v * v;
-        const uint16_t hb = __half_as_ushort(__int2half_rn(v));
-        if (t < 2) h01 |= (uint32_t)hb << (16 * t);
-        else h23 |= (uint32_t)hb << (16 * (t - 2));
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int t = 0; t < 4; t += 2) {
+                const int v0 = (int)(int8_t)((ws[q] >> (8 * t)) & 0xffu);
+                const int v1 = (int)(int8_t)((ws[q] >> (8 * t + 8)) & 0xffu);
+                sq += v0 * v0 + v1 * v1;
+                h[2 * q + t / 2] = (uint32_t)__half_as_ushort(__int2half_rn(v0)) |
+                                   ((uint32_t)__half_as_ushort(__int2half_rn(v1)) << 16);
+            }
+        }
+        uint4 *dh = reinterpret_cast<uint4 *>(J->desc_h + (int64_t)row * kDim) + 2 * part;
+        dh[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        dh[1] = make_uint4(h[4], h[5], h[6], h[7]);
     }
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
-    if (lane == 0) {
-        J.norm[row] = sq;
-        J.norm256[row] = sq * 256;
+    for (int s = 4; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
+    if (live && part == 0) {
+        J->norm[row] = sq;
+        J->norm256[row] = sq * 256;
     }
-    reinterpret_cast<uint2 *>(J.desc_h + (int64_t)row * kDim)[lane] = make_uint2(h01, h23);
 }
 
 // records of every image plus one sentinel each: index g over sum (n + 1), image k owns [kp_base + k, ...]
@@ -252,7 +265,7 @@ cudaError_t launch_bucket_batch_build(const BucketJob *jobs, const int64_t *kp_p
     if (n_total > 0) {
         batch_scatter_kernel<<<blocks_for(n_total, 256), 256, 0, st>>>(jobs, kp_prefix, K, n_total, work, false);
         batch_scatter_kernel<<<blocks_for(n_total, 256), 256, 0, st>>>(jobs, kp_prefix, K, n_total, work, true);
-        batch_desc_kernel<<<blocks_for(n_total * 32, 256), 256, 0, st>>>(jobs, kp_prefix, K, n_total);
+        batch_desc_kernel<<<blocks_for(n_total * 8, 256), 256, 0, st>>>(jobs, kp_prefix, K, n_total);
     }
     // the record index space has one extra entry (the sentinel) per image: rec_prefix[k] = kp_prefix[k] + k
     batch_records_kernel<<<blocks_for(n_total + K, 256), 256, 0, st>>>(jobs, rec_prefix, K, n_total + K);

@@ -307,6 +307,31 @@ def test_images_put_batch_equals_single_puts(gm, facade_scene):
             got = gm.split_matches(off, m)
             for k in range(len(pairs)):
                 np.testing.assert_array_equal(got[k], ref[k], err_msg=f"after rejected batch, pair {k}")
+    # page-locked descriptors 8 bytes past a 16-byte boundary are staged instead of read in place (same result);
+    # device descriptors at such an offset are refused before any kernel reads them
+    def shifted(a, device):
+        buf = torch.zeros(a.size + 8, dtype=torch.uint8, device=device)
+        if device == "cpu":
+            buf = buf.pin_memory()
+        v = buf[8:].view(a.shape)
+        v.copy_(torch.from_numpy(a))
+        assert v.data_ptr() % 16 == 8
+        return v
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    with gm.Context(device=0) as ctx:
+        ctx.put_images({k: scenes.Image(sc.images[k].width, sc.images[k].height, pin(sc.images[k].xy),
+                                        pin(sc.images[k].scale), shifted(sc.images[k].desc, "cpu"), sc.images[k].pid)
+                        for k in used})
+        off, m = ctx.match_pairs(pairs)
+        got = gm.split_matches(off, m)
+        for k in range(len(pairs)):
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"unaligned page-locked, pair {k}")
+        im = sc.images[used[0]]
+        with pytest.raises(gm.GeomatchError) as e:
+            gm.gm_images_put(ctx.h, [(999, im.width, im.height, torch.from_numpy(im.xy).cuda(), None,
+                                      shifted(im.desc, "cuda:0"))])
+        assert e.value.status == gm.GM_ERR_INVALID
+        assert gm.gm_image_info(ctx.h, 999) is None
 
 
 def test_street_uneven_batch_sampled(gm):
