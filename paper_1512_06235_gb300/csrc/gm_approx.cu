@@ -357,7 +357,7 @@ __global__ void group_start_kernel(const int32_t *__restrict__ flag, const int32
 // ---------------------------------------------------------------- Steps 3-4: one warp per group
 
 constexpr int kQTile = 16;           // queries of a group scored together (the mma m dimension)
-constexpr int kSampleBatch = 4;      // chord samples a lane looks up at a time
+constexpr int kSampleBatch = 8;      // chord samples a lane looks up at a time
 constexpr int kListCap = 1024;       // compacted candidate positions per round (32 bitmap words)
 constexpr size_t kWarpExtra = kQTile * kDim + 4 * kListCap + 4 * kQTile;   // query rows, list, query norms
 
