@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kBins = 4096;
 constexpr int kOrderThreads = 1024;
+constexpr int kKeyCache = 16384;   // queries whose keys (then bins) a block keeps in shared memory between passes
 
 struct KeyParams {
     float cx, cy;      // image centre of B
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(const ImageDev *__
                                                               int32_t *__restrict__ qorder)
 {
     __shared__ int32_t hist[kBins];
+    extern __shared__ float skey[];   // [kKeyCache]: the key of query s, then its bin (each thread its own entries)
     __shared__ float rmin[32], rmax[32];
     __shared__ KeyParams skp;
     __shared__ float sF[9];
@@ -103,9 +105,12 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(const ImageDev *__
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = sF[k];
 
+    const bool cached = nA <= kKeyCache;   // otherwise every pass recomputes the keys
+    int32_t *sbin = reinterpret_cast<int32_t *>(skey);
     float kmin = INFINITY, kmax = -INFINITY;
     for (int s = threadIdx.x; s < nA; s += blockDim.x) {
         const float key = line_key(F, A.xy[s], kp);
+        if (cached) skey[s] = key;
         kmin = fminf(kmin, key);
         kmax = fmaxf(kmax, key);
     }
@@ -135,8 +140,9 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(const ImageDev *__
     const float scale = span > 0.0f && isfinite(span) ? (float)kBins / span : 0.0f;
 
     for (int s = threadIdx.x; s < nA; s += blockDim.x) {
-        const float key = line_key(F, A.xy[s], kp);
+        const float key = cached ? skey[s] : line_key(F, A.xy[s], kp);
         const int bin = min(kBins - 1, max(0, (int)((key - kmin) * scale)));
+        if (cached) sbin[s] = bin;
         atomicAdd(&hist[bin], 1);
     }
     __syncthreads();
@@ -172,8 +178,13 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(const ImageDev *__
     }
     __syncthreads();
     for (int s = threadIdx.x; s < nA; s += blockDim.x) {
-        const float key = line_key(F, A.xy[s], kp);
-        const int bin = min(kBins - 1, max(0, (int)((key - kmin) * scale)));
+        int bin;
+        if (cached) {
+            bin = sbin[s];
+        } else {
+            const float key = line_key(F, A.xy[s], kp);
+            bin = min(kBins - 1, max(0, (int)((key - kmin) * scale)));
+        }
         const int pos = atomicAdd(&hist[bin], 1);
         qorder[P.qoff + pos] = s;
     }
@@ -185,7 +196,10 @@ cudaError_t launch_order(const ImageDev *imgs, const PairDev *pairs, int32_t n_p
                          cudaStream_t st)
 {
     static_assert(kBins == 4 * kOrderThreads, "scan layout");
-    if (n_pairs > 0) order_kernel<<<n_pairs, kOrderThreads, 0, st>>>(imgs, pairs, qorder);
+    constexpr int smem = (int)sizeof(float) * kKeyCache;
+    static const cudaError_t attr = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    if (n_pairs > 0) order_kernel<<<n_pairs, kOrderThreads, smem, st>>>(imgs, pairs, qorder);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ namespace gm {
 namespace {
 
 constexpr int kWarps = 4;
+constexpr int kMinBlocks = 1;   // resident blocks per SM that __launch_bounds__ asks the register allocation for
 constexpr int kG = kTcQueriesPerItem;   // queries per group
 constexpr int kMaxLines = 1024;
 
@@ -33,7 +34,7 @@ __device__ __forceinline__ int pair_of_item(const int64_t *__restrict__ item_off
     return lo;
 }
 
-__global__ void __launch_bounds__(kWarps * 32) stream_kernel(
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
     const ImageDev *__restrict__ imgs, const PairDev *__restrict__ pairs, const int64_t *__restrict__ item_off,
     int32_t n_pairs, const int32_t *__restrict__ qorder, int64_t item_begin, int64_t item_end,
     GroupDesc *__restrict__ gdesc, int32_t *__restrict__ grows, int32_t *__restrict__ stream, int64_t capacity,
