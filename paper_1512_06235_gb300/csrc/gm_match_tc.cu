@@ -49,12 +49,10 @@ constexpr int kAcc = 4;             // accumulator buffers in tensor memory
 constexpr int kSlots = 3;           // query groups in flight
 constexpr int kPosCap = 1024;       // candidate positions a slot stages in shared memory (multiple of kN)
 constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
-constexpr int kEpiSets = 1;         // epilogue warp sets: set e scores the chunks with chunk counter ck = e (mod kEpiSets)
-constexpr int kEpiWarps = 8 * kEpiSets;   // per set: 4 lane quadrants x 2 column halves
-constexpr int kLoaderWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kSetupWarp0 = kEpiWarps + 2;   // workers: 3
-constexpr int kPartials = 2 * kEpiSets;   // per-row top-2 states merged at the end of a group
+constexpr int kEpiWarps = 8;
+constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;   // worker warps: 8, 10, 11
 constexpr int kWorkers = 3;
-constexpr int kThreads = (kEpiWarps + 4) * 32;
+constexpr int kThreads = 12 * 32;
 constexpr int kTmemCols = kAcc * kN;
 constexpr int kCounterShards = 64;
 constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
@@ -72,7 +70,7 @@ struct Ctl {
     float2 qxy[kSlots][kM];          // query coordinates
     int32_t rinfo[kSlots][kM][2];    // original A index (-1: no query), |a'|^2 * 256
     alignas(16) int32_t aidx[kSlots][kM];   // A rows to gather
-    int32_t merge[kSlots][kPartials - 1][kM][4];
+    int32_t merge[kSlots][kM][4];
     alignas(16) int32_t pos[kSlots][kPosCap];   // the group's candidate positions (staged by the setup warp)
     uint64_t stage_full[kStages], stage_empty[kStages], acc_full[kAcc], acc_empty[kAcc];
     uint64_t grp_full[kSlots], grp_empty[kSlots], merge_ready[kSlots], pos_full[kSlots];
@@ -311,17 +309,17 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         cl.stat[0] = cl.stat[1] = cl.stat[2] = 0ull;
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&cl.stage_full[s], 32 * kWorkers);   // every lane of every worker (+ tile bytes)
-            mbar_init(&cl.stage_empty[s], 1 + 8);  // the MMA commit, the 8 warps of the set scoring it (records read)
+            mbar_init(&cl.stage_empty[s], 1 + kEpiWarps);  // the MMA commit, the epilogue warps (records read)
         }
         for (int b = 0; b < kAcc; ++b) {
             mbar_init(&cl.acc_full[b], 1);
-            mbar_init(&cl.acc_empty[b], 8);   // the 8 warps of the set that reads it
+            mbar_init(&cl.acc_empty[b], kEpiWarps);
         }
         for (int g = 0; g < kSlots; ++g) {
             mbar_init(&cl.pos_full[g], 33);   // the setup warp's 32 cp.async arrivals + its release
             mbar_init(&cl.grp_full[g], kWorkers);   // each worker's arrival with its share of the A tile's bytes
             mbar_init(&cl.grp_empty[g], 1 + kEpiWarps + kWorkers);   // MMA commit, epilogue warps, workers
-            mbar_init(&cl.merge_ready[g], 4 * (kPartials - 1));   // every warp that hands over a partial state
+            mbar_init(&cl.merge_ready[g], kEpiWarps / 2);
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -454,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         __syncwarp();
     } else {
         // ---------------------------------------------------------------- epilogue warps
-        const int quadrant = warp & 3, h = (warp >> 2) & 1, eset = warp >> 3, part = 2 * eset + h;
+        const int quadrant = warp & 3, h = warp >> 2;
         const int row = 32 * quadrant + lane;
         const uint32_t tmem_lane = tmem + ((uint32_t)(32 * quadrant) << 16) + 32 * h;
         int ck = 0;
@@ -486,7 +484,6 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             int k1 = INT_MAX, k2 = INT_MAX, j1 = 0, cnt = 0;
             bool ok = true;
             for (int c = 0; c < nchunks; ++c, ++ck) {
-                if (kEpiSets > 1 && ck % kEpiSets != eset) continue;   // another set's chunk
                 const int s = ck % kStages, b = ck % kAcc;
                 if (!mbar_wait_warp(&cl.acc_full[b], (ck / kAcc) & 1)) { ok = false; break; }
                 tc_fence_after();
@@ -582,23 +579,20 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 if (lane == 0) mbar_arrive(&cl.stage_empty[s]);
             }
             if (!ok) { raise_abort(cl, ctr); break; }
-            // merge the partial states of every row (column halves, warp sets), then the ratio test
-            if (part != 0) {
-                int32_t *mg = cl.merge[g][part - 1][row];
+            // merge the two column halves of every row, then the ratio test
+            if (h == 1) {
+                int32_t *mg = cl.merge[g][row];
                 mg[0] = k1; mg[1] = k2; mg[2] = j1; mg[3] = cnt;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&cl.merge_ready[g]);
             } else {
                 if (!mbar_wait_warp(&cl.merge_ready[g], (gk / kSlots) & 1)) { raise_abort(cl, ctr); break; }
-#pragma unroll
-                for (int pp = 0; pp < kPartials - 1; ++pp) {
-                    const int32_t *mg = cl.merge[g][pp][row];
-                    const int ok1 = mg[0], ok2 = mg[1], oj1 = mg[2];
-                    const int nk2 = min(max(k1, ok1), min(k2, ok2));
-                    if (ok1 < k1) { k1 = ok1; j1 = oj1; }
-                    k2 = nk2;
-                    cnt += mg[3];
-                }
+                const int32_t *mg = cl.merge[g][row];
+                const int ok1 = mg[0], ok2 = mg[1], oj1 = mg[2];
+                const int nk2 = min(max(k1, ok1), min(k2, ok2));
+                if (ok1 < k1) { k1 = ok1; j1 = oj1; }
+                k2 = nk2;
+                cnt += mg[3];
                 if (out_i >= 0) {
                     const int64_t D1 = k1 >> 8, D2 = k2 >> 8;
                     const int64_t pp = gd.p, qq = gd.q;
