@@ -369,6 +369,7 @@ __device__ __forceinline__ void mma_s8(int (&d)[4], const int (&a)[4], int b0, i
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 constexpr int kMatchThreads = 128;
+constexpr int kWarpsPerBlock = 4;    // groups (one warp each) per block of the match kernel, at most kMatchThreads / 32
 
 __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const ApproxPair *__restrict__ P, const int64_t *__restrict__ qoff, int n_pairs,
                                     const ApproxJob *__restrict__ jobs, const ImageDev *__restrict__ imgs,
@@ -728,7 +729,7 @@ gm_status gm_match_pairs_approx(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pai
     // Steps 3-4
     const int32_t words = ((max_nb + 31) / 32 + 3) & ~3;   // a multiple of 4 words keeps the query rows 16-byte aligned
     const size_t per_warp = (size_t)words * 4 + kWarpExtra;
-    int wpb = 4;
+    int wpb = kWarpsPerBlock;
     while (wpb > 1 && per_warp * wpb > 200 * 1024) --wpb;
     if (per_warp * wpb > 200 * 1024) return fail(GM_ERR_INVALID, "%s: target image too large for the bitmap", fn);
     const size_t smem = per_warp * wpb;
