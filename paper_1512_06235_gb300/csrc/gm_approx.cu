@@ -359,7 +359,7 @@ __global__ void group_start_kernel(const int32_t *__restrict__ flag, const int32
 constexpr int kQTile = 16;           // queries of a group scored together (the mma m dimension)
 constexpr int kSampleBatch = 8;      // chord samples a lane looks up at a time
 constexpr int kListCap = 1024;       // compacted candidate positions per round (32 bitmap words)
-constexpr size_t kWarpExtra = kQTile * kDim + 4 * kListCap + 4 * kQTile;   // query rows, list, query norms
+constexpr size_t kWarpExtra = kQTile * kDim + 4 * kListCap + 4 * kQTile + 16;   // query rows, list, query norms, count
 
 __device__ __forceinline__ void mma_s8(int (&d)[4], const int (&a)[4], int b0, int b1)
 {
@@ -392,8 +392,14 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
     const int64_t q0 = pr.qoff;
     const int32_t lead = order[s0];
     // Step 3: C' of the leader's chord as a bitmap over B's column-major positions
+    // every newly set bit also appends its position to the candidate list (up to kListCap entries; the count goes
+    // on, and a longer C' is compacted from the bitmap round by round below)
     const int32_t nw = (pr.n_b + 31) >> 5;
+    int32_t *list = reinterpret_cast<int32_t *>(qd + kQTile * kDim);
+    int32_t *qn_s = list + kListCap;
+    int32_t *nl_s = qn_s + kQTile;
     for (int32_t w = lane; w < nw; w += 32) bm[w] = 0u;
+    if (lane == 0) *nl_s = 0;
     __syncwarp();
     if (has[q0 + lead]) {
         const float2 pt = A.xy[A.inv_perm[lead]];
@@ -427,24 +433,27 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
                 for (int t = 0; t < kSampleBatch; ++t) pos[t] = lo[t] + i < hi[t] ? __ldg(members + lo[t] + i) : -1;
 #pragma unroll
                 for (int t = 0; t < kSampleBatch; ++t)
-                    if (pos[t] >= 0) atomicOr(&bm[pos[t] >> 5], 1u << (pos[t] & 31));
+                    if (pos[t] >= 0) {
+                        const uint32_t bit = 1u << (pos[t] & 31);
+                        if (!(atomicOr(&bm[pos[t] >> 5], bit) & bit)) {
+                            const int32_t slot = atomicAdd(nl_s, 1);
+                            if (slot < kListCap) list[slot] = pos[t];
+                        }
+                    }
             }
         }
         if (lane == 0) atomicAdd(&ctr->cells, (unsigned long long)(K + 1));
     }
     __syncwarp();
-    int32_t cnt = 0;
-    for (int32_t w = lane; w < nw; w += 32) cnt += __popc(bm[w]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    const int32_t cnt = *reinterpret_cast<volatile int32_t *>(nl_s);   // |C'|
+    const bool direct = cnt <= kListCap;                                // the list already holds all of C'
     if (lane == 0) atomicAdd(&ctr->candidates, (unsigned long long)cnt * (unsigned long long)(s1 - s0));
     // Step 4: exact distances from each query of the group to C', top-2, ratio test.  The group's queries are
     // scored 16 at a time against 8 candidates at a time by mma.sync.m16n8k32.s8 (the int32 accumulator holds the
-    // exact dot product a'.b'); the bitmap is compacted into a list of at most kListCap positions per round.
+    // exact dot product a'.b') over the list built while sampling; a C' longer than kListCap is compacted from the
+    // bitmap instead, kListCap positions per round.
     // Fragments (lane = 4 g + t): A rows g and g + 8, bytes 4t .. 4t + 3 and 16 + 4t .. of each 32-byte K step;
     // B column g (a candidate), the same bytes; accumulator element 2 h + e = (row g + 8 h, column 2 t + e).
-    int32_t *list = reinterpret_cast<int32_t *>(qd + kQTile * kDim);
-    int32_t *qn_s = list + kListCap;
     const int gq = lane >> 2, t4 = lane & 3;
     for (int32_t c0 = s0; c0 < s1; c0 += kQTile) {
         const int nq = min(kQTile, s1 - c0);
@@ -470,6 +479,10 @@ __global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const Appro
         int D1[2] = {INT_MAX, INT_MAX}, D2[2] = {INT_MAX, INT_MAX}, J1[2] = {INT_MAX, INT_MAX};
         for (int32_t w0 = 0; w0 < nw;) {
             int32_t nl = 0;
+            if (direct) {
+                nl = cnt;
+                w0 = nw;
+            }
             while (w0 < nw) {   // 32 words per round hold at most kListCap bits, so every round fits an empty list
                 const int32_t w = w0 + lane;
                 uint32_t bits = w < nw ? bm[w] : 0u;
