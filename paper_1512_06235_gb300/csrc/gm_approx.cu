@@ -369,9 +369,10 @@ __device__ __forceinline__ void mma_s8(int (&d)[4], const int (&a)[4], int b0, i
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 constexpr int kMatchThreads = 128;
+constexpr int kMatchMinBlocks = 1;   // resident blocks per SM that __launch_bounds__ asks the register allocation for
 constexpr int kWarpsPerBlock = 4;    // groups (one warp each) per block of the match kernel, at most kMatchThreads / 32
 
-__global__ void __launch_bounds__(kMatchThreads) approx_match_kernel(const ApproxPair *__restrict__ P, const int64_t *__restrict__ qoff, int n_pairs,
+__global__ void __launch_bounds__(kMatchThreads, kMatchMinBlocks) approx_match_kernel(const ApproxPair *__restrict__ P, const int64_t *__restrict__ qoff, int n_pairs,
                                     const ApproxJob *__restrict__ jobs, const ImageDev *__restrict__ imgs,
                                     const int32_t *__restrict__ cell_off, const int32_t *__restrict__ members,
                                     const int32_t *__restrict__ order, const uint8_t *__restrict__ has,
