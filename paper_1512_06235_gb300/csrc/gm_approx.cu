@@ -358,7 +358,9 @@ __global__ void group_start_kernel(const int32_t *__restrict__ flag, const int32
 
 constexpr int kQTile = 16;           // queries of a group scored together (the mma m dimension)
 constexpr int kSampleBatch = 8;      // chord samples a lane looks up at a time
-constexpr int kListCap = 1024;       // compacted candidate positions per round (32 bitmap words)
+constexpr int kListCap = 512;        // candidate positions in the list: the sampled C', or one round of compaction
+constexpr int kRoundWords = kListCap / 32;   // bitmap words per compaction round: they hold at most kListCap bits
+static_assert(kListCap % 32 == 0 && kRoundWords >= 1 && kRoundWords <= 32, "a round must fit an empty list");
 constexpr size_t kWarpExtra = kQTile * kDim + 4 * kListCap + 4 * kQTile + 16;   // query rows, list, query norms, count
 
 __device__ __forceinline__ void mma_s8(int (&d)[4], const int (&a)[4], int b0, int b1)
@@ -369,7 +371,7 @@ __device__ __forceinline__ void mma_s8(int (&d)[4], const int (&a)[4], int b0, i
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 constexpr int kMatchThreads = 128;
-constexpr int kMatchMinBlocks = 1;   // resident blocks per SM that __launch_bounds__ asks the register allocation for
+constexpr int kMatchMinBlocks = 8;   // resident blocks per SM that __launch_bounds__ asks the register allocation for
 constexpr int kWarpsPerBlock = 4;    // groups (one warp each) per block of the match kernel, at most kMatchThreads / 32
 
 __global__ void __launch_bounds__(kMatchThreads, kMatchMinBlocks) approx_match_kernel(const ApproxPair *__restrict__ P, const int64_t *__restrict__ qoff, int n_pairs,
@@ -484,9 +486,9 @@ __global__ void __launch_bounds__(kMatchThreads, kMatchMinBlocks) approx_match_k
                 nl = cnt;
                 w0 = nw;
             }
-            while (w0 < nw) {   // 32 words per round hold at most kListCap bits, so every round fits an empty list
+            while (w0 < nw) {   // kRoundWords words per round hold at most kListCap bits: every round fits an empty list
                 const int32_t w = w0 + lane;
-                uint32_t bits = w < nw ? bm[w] : 0u;
+                uint32_t bits = lane < kRoundWords && w < nw ? bm[w] : 0u;
                 const int c = __popc(bits);
                 int inc = c;
 #pragma unroll
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(kMatchThreads, kMatchMinBlocks) approx_match_k
                     bits &= bits - 1u;
                 }
                 nl += tot;
-                w0 += 32;
+                w0 += kRoundWords;
             }
             __syncwarp();
             // B fragments of n-tile n0 (8 candidates; padding columns repeat a real one), loaded one tile ahead

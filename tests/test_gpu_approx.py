@@ -53,6 +53,18 @@ def test_two_view(gm, two_view_scene, cell_scale):
         assert off[1] > 500 and st["n_groups"] > 50
 
 
+def test_wide_band_compacts_in_rounds(gm, two_view_scene):
+    """A band so wide that C' of most groups exceeds the 512-entry list, so C' is compacted from the bitmap in rounds:
+    the same matches and counts as the oracle."""
+    sc = two_view_scene
+    pr = sc.pairs[0]
+    wide = [SimpleNamespace(a=pr.a, b=pr.b, F=pr.F, d=150.0, p=4, q=5)]
+    with gm.Context(device=0) as ctx:
+        ctx.put_images({k: im for k, im in enumerate(sc.images)})
+        off, m, st = _check(gm, ctx, sc.images, wide, 1.5)
+    assert st["n_candidates"] > 512 * sc.images[pr.a].n
+
+
 def test_facade_full_batch_sampled(gm, facade_scene):
     """The whole 1200-pair facade batch in one call (the benchmark's launch); eight sampled pairs against the
     oracle."""
