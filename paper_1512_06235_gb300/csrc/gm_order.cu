@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kBins = 4096;
 constexpr int kOrderThreads = 1024;
+constexpr int kOrderMinBlocks = 1;   // resident blocks per SM that __launch_bounds__ asks the register allocation for
 constexpr int kKeyCache = 16384;   // queries whose keys (then bins) a block keeps in shared memory between passes
 
 struct KeyParams {
@@ -82,7 +83,7 @@ __device__ KeyParams key_params(const float F[9], float W, float H)
     return kp;
 }
 
-__global__ void __launch_bounds__(kOrderThreads) order_kernel(const ImageDev *__restrict__ imgs,
+__global__ void __launch_bounds__(kOrderThreads, kOrderMinBlocks) order_kernel(const ImageDev *__restrict__ imgs,
                                                               const PairDev *__restrict__ pairs,
                                                               int32_t *__restrict__ qorder)
 {
