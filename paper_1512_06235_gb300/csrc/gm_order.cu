@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kBins = 4096;
 constexpr int kOrderThreads = 1024;
-constexpr int kOrderMinBlocks = 1;   // resident blocks per SM that __launch_bounds__ asks the register allocation for
+constexpr int kOrderMinBlocks = 2;   // resident blocks per SM that __launch_bounds__ asks the register allocation for
 constexpr int kKeyCache = 16384;   // queries whose keys (then bins) a block keeps in shared memory between passes
 
 struct KeyParams {
