@@ -850,10 +850,15 @@ def cpu_baseline(sc):
     t0 = time.perf_counter()
     _, ncs = oracle.match_batch(sc.images, sample, n_threads=cores)
     dt = time.perf_counter() - t0
+    one = sample[::8]   # the same oracle on one thread, on every 8th pair of the sample
+    t1 = time.perf_counter()
+    oracle.match_batch(sc.images, one, n_threads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": len(sample) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(sample)} of {len(sc.pairs)} pairs (every {len(sc.pairs) // 64}th), {cores} threads, "
                       f"{dt:.1f} s wall",
-            "comparisons_per_s": float(ncs.sum()) / dt}
+            "comparisons_per_s": float(ncs.sum()) / dt,
+            "single_thread": {"value": len(one) / dt1, "unit": UNIT, "sample": f"{len(one)} of those pairs, 1 thread"}}
 
 
 def main():
