@@ -114,9 +114,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 
 // Every lane waits (each one acquires the phase); the outcome is made uniform so that a warp never splits around
 // warp-collective instructions.
+// The same bounded wait without the suspend-time hint, for waits that a whole warp takes (epilogue, workers): their
+// phases complete within a chunk's time, and polling picks them up sooner than a suspended thread wakes.
+__device__ __forceinline__ bool mbar_wait_spin(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((it & 255) == 0) {
+            const uint64_t t = globaltimer();
+            if (it == 0) t0 = t;
+            else if (t - t0 > kWaitNs) return false;
+        }
+    }
+}
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity)
 {
-    return __all_sync(0xffffffffu, mbar_wait(bar, parity));
+    return __all_sync(0xffffffffu, mbar_wait_spin(bar, parity));
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
