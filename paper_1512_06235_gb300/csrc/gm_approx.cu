@@ -13,7 +13,7 @@
 //           sorted keys and marks a group leader wherever t1 or t2 leaves the 2 px window of the current leader;
 //   Step 3  one warp per group: the K + 1 equidistant points of the leader's chord (K = ceil(|AB| / h)), for each
 //           the cell with the nearest centre among its four cells, every point binned there into a shared-memory
-//           bitmap over B's points (C' as a set);
+//           bitmap over B's points (C' as a set), each newly set bit also appended to a list of C';
 //   Step 4  the same warp: exact squared distances from each query of the group to every point of C' (16 queries x
 //           8 candidates per mma.sync.m16n8k32 over the recentred int8 descriptors), top-2, ratio test
 //           q^2 D1 < p^2 D2 with |C'| >= 2.
