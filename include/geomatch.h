@@ -328,10 +328,14 @@ GM_API gm_status gm_band_candidates(gm_ctx *ctx, const gm_pair *pair, int32_t qu
 /* gm_band_candidates without any allocation (the paper has no counterpart: this is an interface for callers that
  * must not allocate, e.g. with device memory fully committed or in latency-critical loops where cudaMalloc,
  * cudaFree or cudaHostAlloc would stall).  Same sets, same layout, same errors as gm_band_candidates, except:
- *   cand_off, cand: DEVICE memory of the context's device (GM_ERR_INVALID otherwise), caller-owned;
+ *   cand_off, cand: DEVICE memory of the context's device, or managed memory (GM_ERR_INVALID otherwise),
+ *            caller-owned;
  *   scratch: one fixed 4 MiB device array per device, so query_count * ceil(|B| / 32) * 4 + 4 * query_count + 768
  *            bytes must fit in 4 MiB (GM_ERR_INVALID with the sizes otherwise; split the query range);
- *   the first call on a device sets up the scratch address and should come before any stream capture;
+ *   set-up: gm_create looks up the array's address, which loads it onto the device (4 MiB per device, held until
+ *            the process exits, charged to no context's budget); only if that lookup failed does the first call
+ *            here retry it (and may then load the array), so that call should come before any stream capture;
+ *            a context created after cudaDeviceReset refreshes the address;
  *   calls that overlap in time on one device (any thread or context) race on the scratch: serialise them.
  * The call returns when the outputs are complete. */
 GM_API gm_status gm_band_candidates_static(gm_ctx *ctx, const gm_pair *pair, int32_t query_begin,

@@ -129,6 +129,15 @@ void workspace_free(gm_ctx *ctx, Workspace &ws)
     ws.stream = nullptr;
 }
 
+size_t workspace_bytes(const Workspace &ws)
+{
+    size_t n = 0;
+    for (const DevBuf *b : {&ws.d_tab, &ws.d_qorder, &ws.d_matchj, &ws.d_counts, &ws.d_off, &ws.d_rows, &ws.d_ctr,
+                            &ws.d_next, &ws.d_grec, &ws.d_grows, &ws.d_stream})
+        n += b->bytes;
+    return n;
+}
+
 bool is_device_ptr(const void *p)
 {
     if (!p) return false;
@@ -138,6 +147,18 @@ bool is_device_ptr(const void *p)
         return false;
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device memory of the given device, or managed memory (which every device may access).
+bool is_device_ptr_on(const void *p, int device)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == device);
 }
 
 // The device address of page-locked host memory that the device may read directly (cudaMallocHost /
@@ -507,6 +528,7 @@ gm_status gm_create(const gm_config *cfg, gm_ctx **out)
         ctx->own_stream = true;
     }
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
+    noalloc_setup(cfg->device);   // gm_band_candidates_static's scratch array: loaded here, not in that call
     if (workspace_init(ctx->ws, ctx->stream) != GM_OK || workspace_init(ctx->ws2, ctx->ws.stream) != GM_OK ||
         cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess ||

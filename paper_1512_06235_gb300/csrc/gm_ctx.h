@@ -172,6 +172,8 @@ void free_dev(gm_ctx *ctx, DevBuf &b);
 void free_host(HostBuf &b);
 gm_status workspace_init(Workspace &ws, cudaStream_t stream);
 void workspace_free(gm_ctx *ctx, Workspace &ws);
+// Device bytes held by the workspace's buffers (counted in the context's bytes_work).
+size_t workspace_bytes(const Workspace &ws);
 
 // Validates one pair and fills its device record (without qoff).  Negative image ids (internal images) are
 // accepted only with `internal`.
@@ -189,6 +191,9 @@ void drop_image(gm_ctx *ctx, int32_t image_id);
 // Gives up an image's block: the slab is freed with its last image.
 void release_block(ImageSlot *img);
 bool is_device_ptr(const void *p);
+bool is_device_ptr_on(const void *p, int device);
+// gm_band_candidates_static's scratch: looks up (and so loads) the array on `device`, which must be current.
+void noalloc_setup(int device);
 // Enqueues the whole batch on ws.stream: table upload, order, match, count/scan, row writing into rows_dst
 // (device memory or mapped host memory with room for ws.Q rows; nullptr = ws.d_rows), then the D2H copy of the
 // offsets and counters into ws.h_off.  Nothing waits.  Caller holds ctx->mu.

@@ -9,8 +9,13 @@
 // array, and the caller provides the output buffers in device memory.  It computes exactly what gm_band_candidates
 // computes (same kernels: the band walk with the exact FP64 edge decision, bitmap, count, scan, fill).
 //
-// Set-up: the first call on a device (with that device current) looks up the array's device address with
-// cudaGetSymbolAddress, once per device; make that first call before any stream capture begins.
+// Set-up: gm_create looks up the array's device address with cudaGetSymbolAddress (with the context's device
+// current) and keeps it for that device.  The lookup is what loads the array onto the device: 4 MiB of device
+// memory per device, held until the process exits and charged to no context's budget (it is shared by every
+// context on the device).  Every gm_create refreshes the address, so a context created after a cudaDeviceReset
+// sees the new one.  If the lookup failed at gm_create (for instance because a stream capture was under way), the
+// first call of this entry point retries it, and that call may then load the array itself: make it before any
+// stream capture.
 // Concurrency: the scratch is shared by every context on a device, so calls that overlap in time on one device (from
 // any thread or context) race on it; the caller serialises them.
 #include <cuda_runtime.h>
@@ -26,8 +31,6 @@ static __device__ __align__(256) unsigned char gm_static_scratch[kStaticScratchB
 
 namespace gm {
 
-bool is_device_ptr(const void *p);
-
 namespace {
 
 constexpr int kMaxDevices = 64;
@@ -37,12 +40,25 @@ constexpr size_t kCountsOff = 512;    // int32 [query_count], then the bitmap
 static_assert(sizeof(PairDev) <= kCtrOff - kPairOff, "pair record slot");
 static_assert(sizeof(BatchCounters) <= kCountsOff - kCtrOff, "counter slot");
 
+// The array's device address per device; nullptr until a lookup succeeds (a failed lookup is retried).
 struct ScratchAddr {
-    std::once_flag once;
+    std::mutex mu;
     unsigned char *ptr = nullptr;
-    cudaError_t err = cudaSuccess;
 };
 ScratchAddr g_addr[kMaxDevices];
+
+// Looks the address up with `device` current and stores it; returns the CUDA error of the lookup.
+cudaError_t lookup_scratch(int device, unsigned char **out)
+{
+    ScratchAddr &sa = g_addr[device];
+    std::lock_guard<std::mutex> lk(sa.mu);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, gm_static_scratch);
+    if (e == cudaSuccess && p) sa.ptr = static_cast<unsigned char *>(p);
+    else cudaGetLastError();   // not sticky: clear it so that the caller's next CUDA call does not see it
+    *out = sa.ptr;
+    return e;
+}
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -53,6 +69,16 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
     } while (0)
 
 }  // namespace
+
+// Called by gm_create with the context's device current: loads the scratch array and records its address.  A
+// failure is not an error of gm_create (only this entry point needs the array); the entry point retries.
+void noalloc_setup(int device)
+{
+    if (device < 0 || device >= kMaxDevices) return;
+    unsigned char *p = nullptr;
+    lookup_scratch(device, &p);
+}
+
 }  // namespace gm
 
 extern "C" {
@@ -69,8 +95,9 @@ gm_status gm_band_candidates_static(gm_ctx *ctx, const gm_pair *pair, int32_t qu
         return fail(GM_ERR_INVALID, "gm_band_candidates_static: device %d beyond the %d supported", ctx->device,
                     kMaxDevices);
     GM_CUDA_S(cudaSetDevice(ctx->device));
-    if (!is_device_ptr(cand_off) || (cap > 0 && !is_device_ptr(cand)))
-        return fail(GM_ERR_INVALID, "gm_band_candidates_static: cand_off and cand must be device memory");
+    if (!is_device_ptr_on(cand_off, ctx->device) || (cap > 0 && !is_device_ptr_on(cand, ctx->device)))
+        return fail(GM_ERR_INVALID, "gm_band_candidates_static: cand_off and cand must be device memory of device %d",
+                    ctx->device);
     PairDev pd;
     gm_status st = prepare_pair(ctx, *pair, 0, pd);
     if (st != GM_OK) return st;
@@ -87,17 +114,18 @@ gm_status gm_band_candidates_static(gm_ctx *ctx, const gm_pair *pair, int32_t qu
                     "the fixed %zu; split the query range",
                     query_count, words, bm_off + bm_bytes, kStaticScratchBytes);
 
-    // once per device, with the device current: the scratch array's device address
-    ScratchAddr &sa = g_addr[ctx->device];
-    std::call_once(sa.once, [&] {
-        void *p = nullptr;
-        sa.err = cudaGetSymbolAddress(&p, gm_static_scratch);
-        sa.ptr = static_cast<unsigned char *>(p);
-    });
-    if (sa.err != cudaSuccess || !sa.ptr)
-        return fail(GM_ERR_CUDA, "gm_band_candidates_static: cudaGetSymbolAddress: %s", cudaGetErrorString(sa.err));
-
-    unsigned char *scr = sa.ptr;
+    // the address gm_create looked up; if that lookup failed, retry it now (with the device current)
+    unsigned char *scr = nullptr;
+    {
+        ScratchAddr &sa = g_addr[ctx->device];
+        std::lock_guard<std::mutex> lk(sa.mu);
+        scr = sa.ptr;
+    }
+    if (!scr) {
+        const cudaError_t e = lookup_scratch(ctx->device, &scr);
+        if (e != cudaSuccess || !scr)
+            return fail(GM_ERR_CUDA, "gm_band_candidates_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    }
     PairDev *d_pair = reinterpret_cast<PairDev *>(scr + kPairOff);
     BatchCounters *d_ctr = reinterpret_cast<BatchCounters *>(scr + kCtrOff);
     int32_t *d_counts = reinterpret_cast<int32_t *>(scr + kCountsOff);

@@ -7,12 +7,19 @@
 // batch and overlap with the running ones.  Completed batches are collected in any order.  Every wait is bounded:
 // the engine is polled (never blocked on), and poll() takes a timeout.
 //
+// Admission uses the smaller of the capacity given at construction (which also bounds what submit() accepts) and
+// the engine's current slot capacity, read before every round of admissions (the budget left for work buffers
+// changes as images are put and evicted).  When nothing is in flight, the first queued request is admitted even if
+// it exceeds the current capacity, so that the queue never stalls: the engine then runs it or fails it.
+//
 // Engine requirements (duck-typed):
 //   int64_t cost(const gm_pair&, gm_status* err);           // queries the request needs, or -1 (err set)
+//   int64_t slot_capacity();                                  // queries one batch may take now
 //   gm_status launch(int slot, std::vector<Request*>& batch); // enqueue; on error every request gets the status
 //   bool done(int slot);                                      // non-blocking completion test
 //   void collect(int slot, std::vector<Request*>& batch);     // fill rows / status of each request
 #pragma once
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -189,7 +196,14 @@ private:
             }
             if (progressed) cv_done_.notify_all();
             if (stop_ && inflight_ == 0) break;
-            // 2. admit queued requests into free slots (continuous batching)
+            // 2. admit queued requests into free slots (continuous batching), against the capacity of now
+            int64_t cap_now = capacity_;
+            if (!pending_.empty()) {
+                lk.unlock();
+                const int64_t c = eng_.slot_capacity();
+                lk.lock();
+                cap_now = std::min(capacity_, c);
+            }
             while (!stop_ && !pending_.empty()) {
                 int free_slot = -1;
                 for (size_t s = 0; s < slots_.size(); ++s)
@@ -198,11 +212,12 @@ private:
                 Slot &sl = slots_[free_slot];
                 int64_t used = 0;
                 while (!pending_.empty() && (int)sl.reqs.size() < max_batch_pairs_ &&
-                       used + pending_.front()->cost <= capacity_) {
+                       (used + pending_.front()->cost <= cap_now || (sl.reqs.empty() && inflight_ == 0))) {
                     used += pending_.front()->cost;
                     sl.reqs.push_back(pending_.front());
                     pending_.pop_front();
                 }
+                if (sl.reqs.empty()) break;   // the next request waits for a running batch to finish
                 for (auto &r : sl.reqs) sl.raw.push_back(r.get());
                 sl.busy = true;
                 ++inflight_;

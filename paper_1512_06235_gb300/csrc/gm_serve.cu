@@ -6,9 +6,11 @@
 // are written by the compaction kernel straight into mapped pinned host memory, and completion is detected with
 // cudaEventQuery (the scheduler never blocks on the device).
 //
-// Admission: a request costs |A| queries of device workspace.  The budget left after the resident images is split
-// evenly over the slots; a batch takes queued requests in arrival order while their total cost fits one slot, and
-// a request that could never fit a slot is refused with GM_ERR_BUDGET at submission.
+// Admission: a request costs |A| queries of device workspace.  The budget left after the resident images and the
+// context's other work buffers is split evenly over the slots, recomputed before every round of admissions (images
+// put or evicted since change it); a batch takes queued requests in arrival order while their total cost fits one
+// slot's share, and a request that could never fit a slot of the budget left at server start is refused with
+// GM_ERR_BUDGET at submission.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,6 +51,20 @@ struct GpuEngine {
             return -1;
         }
         return std::max<int64_t>(pd.n_a, 1);
+    }
+
+    // Queries one batch may take now: the budget minus the resident images and the work buffers other than the
+    // serving slots' own, split over the slots (the slots' buffers are what this share pays for).
+    int64_t slot_capacity()
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        if (!ctx->budget) return kMaxSlotQueries;
+        int64_t own = 0;
+        for (auto &S : slots) own += (int64_t)workspace_bytes(S.ws);
+        const int64_t left =
+            (int64_t)ctx->budget - (int64_t)ctx->bytes_images - ((int64_t)ctx->bytes_work - own);
+        return std::min<int64_t>(kMaxSlotQueries,
+                                 std::max<int64_t>(left, 0) / (int64_t)slots.size() / kBytesPerQuery);
     }
 
     gm_status launch(int s, std::vector<SchedRequest *> &batch)

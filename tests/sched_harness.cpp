@@ -19,6 +19,8 @@ namespace {
 struct StubEngine {
     std::atomic<bool> release{true};
     std::atomic<int> launches{0};
+    std::atomic<int64_t> capacity{1 << 30};   // what slot_capacity() reports (the budget share of the moment)
+    std::atomic<int64_t> max_multi_cost{0};   // largest total cost of a batch of two or more requests
     std::vector<std::vector<gm::SchedRequest *>> inflight;
     std::vector<int> polls_left;
     explicit StubEngine(int slots) : inflight(slots), polls_left(slots, 0) {}
@@ -31,9 +33,13 @@ struct StubEngine {
         }
         return 1 + (p.img_a % 7);
     }
+    int64_t slot_capacity() { return capacity.load(); }
     gm_status launch(int s, std::vector<gm::SchedRequest *> &batch)
     {
         ++launches;
+        int64_t c = 0;
+        for (auto *r : batch) c += r->cost;
+        if (batch.size() > 1 && c > max_multi_cost) max_multi_cost = c;
         for (auto *r : batch)
             if (r->pair.img_b == 99) return GM_ERR_CUDA;
         inflight[s] = batch;
@@ -169,6 +175,29 @@ int cancel()   // requests still queued when the scheduler stops end with GM_ERR
     return 0;
 }
 
+int shrink()   // the engine's capacity of the moment bounds every batch; a larger request runs alone when idle
+{
+    StubEngine E(2);
+    E.capacity = 4;   // below the construction capacity (10) and below the costliest requests (7)
+    gm::Scheduler<StubEngine> S(E, 2, 10, 64, 1 << 16);
+    const int n = 300;
+    std::vector<std::thread> th;
+    std::atomic<int> bad{0};
+    for (int w = 0; w < 2; ++w)
+        th.emplace_back([&, w] {
+            for (int k = 0; k < n / 2; ++k) {
+                const gm_pair p = make(w * 1000 + k, k % 50);
+                uint64_t t = 0;
+                if (S.submit(p, &t) != GM_OK || !check_rows(S, t, p)) ++bad;
+            }
+        });
+    for (auto &t : th) t.join();
+    const gm::SchedStats st = S.stats();
+    std::printf("{\"bad\": %d, \"completed\": %lld, \"max_multi_cost\": %lld}\n", bad.load(),
+                (long long)st.completed, (long long)E.max_multi_cost.load());
+    return 0;
+}
+
 }  // namespace
 
 int main(int argc, char **argv)
@@ -177,6 +206,7 @@ int main(int argc, char **argv)
     if (mode == "mix") return mix();
     if (mode == "faults") return faults();
     if (mode == "cancel") return cancel();
-    std::fprintf(stderr, "usage: sched_harness mix|faults|cancel\n");
+    if (mode == "shrink") return shrink();
+    std::fprintf(stderr, "usage: sched_harness mix|faults|cancel|shrink\n");
     return 2;
 }

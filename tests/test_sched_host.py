@@ -1,7 +1,8 @@
 """Host-side tests of the serving scheduler (the continuous-batching loop of gm_sched.h) with a stub engine, on the
 CPU: results in a mix equal results alone, batches respect the slot capacity, and the failure paths -- unknown
 image, over-budget request, failed launch, bounded poll timeout, full queue, cancellation at shutdown -- return
-their status without a GPU."""
+their status without a GPU; admission follows the engine's capacity of the moment (the budget share left after
+images put since the server started)."""
 import json
 import os
 import shutil
@@ -44,3 +45,9 @@ def test_cancellation_at_stop(harness):
     r = harness("cancel")
     assert r["cancelled"] == 5 and r["ok"] == 1 and r["other"] == 0
     assert r["after_stop"] == CANCELLED
+
+
+def test_admission_follows_current_capacity(harness):
+    r = harness("shrink")
+    assert r["bad"] == 0 and r["completed"] == 300
+    assert 0 < r["max_multi_cost"] <= 4   # batches of several requests fit the capacity of the moment
