@@ -1,5 +1,11 @@
-"""Triangulation of feature tracks (arXiv 1512.06235, Sec. 6.2 end: tracks are triangulated with a standard
+"""Triangulation of feature tracks (arXiv 1512.06235, Sec. 6.3: tracks are triangulated with a standard
 least-squares method) -- plain CPU oracle, FP64.
+
+Two track definitions are covered.  ``image_tracks`` follows Sec. 6.3's order: every query image's features form
+tracks from that image's matches in all its candidate images, and each such track is triangulated on its own,
+image by image (which duplicates points: a feature pair matched in both directions is triangulated once for each
+image).  ``triangulate_tracks`` triangulates the merged tracks (the connected components of all matches), the
+result after Sec. 6.3's merging step.
 
 TEST INFRASTRUCTURE ONLY: the tests and the CPU-baseline leg of ``bench.py`` may import this module; the product
 path never does.  It shares no code with the CUDA library.
@@ -50,6 +56,30 @@ def triangulate_tracks(P_per_image, xy_per_image, labels) -> tuple[np.ndarray, n
         out_X.append(triangulate(Ps, xys))
         out_n.append(n)
     return roots[keep].astype(np.int64), np.array(out_n, np.int32), np.array(out_X, np.float64).reshape(-1, 3)
+
+
+def image_tracks(P_per_image, xy_per_image, pairs, pair_matches):
+    """Per-image tracks (Sec. 6.3).  For every query image q and feature k: the observation (q, k) itself, then
+    (c, j) for every pair (q, c) -- in the order of ``pairs`` -- in which k matched j.  Every track with at least
+    two observations is triangulated with ``triangulate``.
+
+    P_per_image [n_images][3, 4]; xy_per_image[k] float [n_k, 2]; pairs: (a, b) image indices, a the query image;
+    pair_matches[p]: int [m_p, 2] rows (i, j) of pair p (feature i of a, feature j of b).  Nodes are numbered
+    image-major (node = features of the images before + feature index).  Returns (nodes int64 [T] -- the query
+    node of each track --, n_views int32 [T], X float64 [T, 3]), tracks in increasing order of their query node."""
+    counts = [len(xy) for xy in xy_per_image]
+    base = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    obs = {}
+    for (a, b), rows in zip(pairs, pair_matches):
+        for i, j in np.asarray(rows, np.int64).reshape(-1, 2):
+            v = int(base[a] + i)
+            if v not in obs:
+                obs[v] = [(int(a), int(i))]
+            obs[v].append((int(b), int(j)))
+    nodes = sorted(obs)
+    X = [triangulate([P_per_image[k] for k, _ in obs[v]], [xy_per_image[k][f] for k, f in obs[v]]) for v in nodes]
+    return (np.array(nodes, np.int64), np.array([len(obs[v]) for v in nodes], np.int32),
+            np.array(X, np.float64).reshape(-1, 3))
 
 
 def camera_matrix(cam) -> np.ndarray:
