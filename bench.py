@@ -1,15 +1,19 @@
 """Benchmark: batched geometry-aware pairwise matching on GB300 (arXiv 1512.06235, Sec. 6.2 / App. A).
 
-Workload (default): synthetic facade component -- 100 cameras on a 30 m arc around a 50k-point three-plane facade,
-8000 keypoints per image (70 % projections, 30 % distractors), the top 1200 pairs by co-visibility, band d = 4 px,
-ratio 0.8.  One step = one gm_match_pairs call over all 1200 pairs (lines, query order, band walk, exact
-distances, top-2, ratio test, match-list compaction).
+Workload (default): synthetic street component -- 1000 cameras every 0.5 m along a 500 m path between two facades
+(1M points), per-image keypoints log-uniform in [2000, 20000] (70 % projections, 30 % distractors), about 18600
+pairs chosen by co-visibility (>= 50 points), band d uniform in [2, 8] px per pair, ratio 0.8; the distance path,
+mma group and cell size chosen by the library's autotuner; CUDA graph replay.  One step = one gm_match_pairs call
+over all pairs (lines, query order, band walk, exact distances, top-2, ratio test, match-list compaction).
 
 Prints one JSON line: pairs/s (device-resident inputs), e2e pairs/s (host buffers: image upload + binning +
-matching + result download), candidate comparisons/s, the match kernel's roofline fraction, the oracle timed on
-the host cores (cpu_baseline), SM clocks sampled during the timed region.
+matching + result download), candidate comparisons/s, the match kernel's roofline fraction (per-pair and per-batch
+HBM bounds, tensor view), the same batch without graph replay and in the one-pair-per-launch form, parity of
+sampled pairs against the oracle, the oracle timed on the host cores (cpu_baseline), SM clocks sampled during the
+timed region.  `--workload facade` gives the same line for the 100-image facade component; the other workloads
+are the scope table's other configurations and next rows.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--path 0..3]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME] [--path 0..3]
 """
 from __future__ import annotations
 
@@ -138,10 +142,10 @@ def _kernel_source_hash(src_file):
     return h.hexdigest()
 
 
-def _profiled_traffic(kernel, src_file, workload):
+def _profiled_traffic(kernel, src_file, workload, root=ROOT):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed ncu summary of this
     kernel on this workload, or None when there is none or the kernel source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    path = os.path.join(root, "profiles", f"{kernel}_{workload}.txt")
     try:
         kv = {}
         with open(path) as fh:
@@ -184,11 +188,12 @@ class _GcPauses:
         return {"gc_collections": len(self.pauses), "gc_max_pause_ms": max(self.pauses, default=0.0) * 1e3}
 
 
-def _serving(gm, ctx, pairs, rate, seconds, seed=1512):
-    """Poisson arrivals of single-pair requests (drawn from the batch's pairs) at `rate` req/s for `seconds`,
-    through gm_submit / gm_poll on the resident images; per-request latency from submission to completion."""
+def _serving(gm, ctx, pairs, rate, seconds, seed=1512, min_requests=1):
+    """Poisson arrivals of single-pair requests (drawn from the batch's pairs) at `rate` req/s for `seconds` (or
+    longer, until `min_requests` have arrived), through gm_submit / gm_poll on the resident images; per-request
+    latency from submission to completion."""
     rng = np.random.default_rng(seed)
-    n = max(1, int(rate * seconds))
+    n = max(min_requests, int(rate * seconds))
     gaps = rng.exponential(1.0 / rate, n)
     picks = rng.integers(0, len(pairs), n)
     tickets = []
@@ -214,13 +219,14 @@ def _serving(gm, ctx, pairs, rate, seconds, seed=1512):
             "requests_from": "pairs of the batch workload, 1 pair per request, resident images"}
 
 
-def _serving_cache(gm, ctx, sc, pairs, images, rate, seconds, seed=1513, warmup=32):
+def _serving_cache(gm, ctx, sc, pairs, images, rate, seconds, seed=1513, warmup=32, min_requests=1):
     """Poisson single-pair requests under a memory budget that holds about a fifth of the images: a request whose
     images are resident is submitted at once (hit); otherwise its missing images are put first (cold: upload and
     binning, with least-recently-used eviction making room).  Latency from arrival to completion.  A warm-up of
-    `warmup` requests (first use of the context's work buffers) runs first and is not counted."""
+    `warmup` requests (first use of the context's work buffers) runs first and is not counted.  At least
+    `min_requests` requests arrive."""
     rng = np.random.default_rng(seed)
-    n = max(1, int(rate * seconds))
+    n = max(min_requests, int(rate * seconds))
     gaps = rng.exponential(1.0 / rate, n)
     picks = rng.integers(0, len(pairs), n)
     for k in rng.integers(0, len(pairs), warmup):
@@ -302,7 +308,9 @@ def _pair_array(gm, pairs, d=None):
                          [p.d for p in pairs] if d is None else d, [p.p for p in pairs], [p.q for p in pairs])
 
 
-def _time_batch(gm, ctx, gp, cap, steps, warmup, dev):
+def _time_batch(gm, ctx, gp, cap, steps, warmup, dev, out=None):
+    """Mean step time (CUDA events, L2 flushed between steps), mean match-kernel time and the last step's stats;
+    with `out` a list, the last step's (offsets as numpy, rows on the device) are appended to it."""
     import torch
     off = torch.empty(len(gp) + 1, dtype=torch.int64, device=dev)
     rows = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev)
@@ -321,50 +329,277 @@ def _time_batch(gm, ctx, gp, cap, steps, warmup, dev):
         torch.cuda.synchronize(dev)
         ms.append(a.elapsed_time(b))
         mm.append(ctx.stats()["ms_match"])
-    return float(np.mean(ms)), float(np.mean(mm)), ctx.stats()
+    st = ctx.stats()
+    if out is not None:
+        out.append((off.cpu().numpy(), rows[:st["n_matches"]]))
+    return float(np.mean(ms)), float(np.mean(mm)), st
 
 
-def run_street(args, gm, dev, local, peaks, peak_kind):
-    """Uneven batch: 1000-camera street component, per-image keypoints log-uniform in [2000, 20000], ~19k pairs
-    with d uniform in [2, 8] px; autotuned; CUDA graph replay against one pair per launch."""
+def _headline_scene(kind: str, rank: int):
+    """The headline workload of a rank: the street component (1000 images, 2k-20k keypoints, d in [2, 8] px per
+    pair) or the facade component (100 images, 8000 keypoints, d = 4 px).  Rank r > 0 matches a component of its
+    own, seeded 1000 r further on (pairs are independent, Sec. 6.2; the paper matches its components separately)."""
     import scenes
-    sc = scenes.street()
-    stream = __import__("torch").cuda.current_stream(dev)
-    ctx = gm.Context(device=local, stream=stream)
-    ctx.put_images({k: im for k, im in enumerate(sc.images)})
-    gp = _pair_array(gm, sc.pairs)
-    cap = sum(sc.images[p.a].n for p in sc.pairs)
-    tune = ctx.autotune(gp, repeats=1)
-    ctx.set_option(gm.GM_OPT_GRAPH, 1)
-    ms, ms_match, st = _time_batch(gm, ctx, gp, cap, args.steps, args.warmup, dev)
-    ctx.set_option(gm.GM_OPT_GRAPH, 0)
-    ctx.set_option(gm.GM_OPT_SCHEDULE, 1)
-    ms1, _, _ = _time_batch(gm, ctx, gp, cap, max(1, min(args.steps, 2)), 1, dev)
-    ctx.close()
+    if kind == "street":
+        return scenes.street(seed=scenes.SEED_BASE + 3 + 1000 * rank)
+    return scenes.facade(seed=_facade_seed(rank))
+
+
+def _workload_name(kind: str, sc) -> str:
+    if kind == "street":
+        return f"street_{len(sc.images)}img_2k-20kp_{len(sc.pairs)}pairs_d2-8"
+    return WORKLOAD
+
+
+def _parity_sample(sc, pairs, n_sample, seed):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(len(pairs), min(n_sample, len(pairs)), replace=False))
+
+
+def _oracle_sample(sc, pairs, idx):
+    """The oracle (as it stands, all host cores) on the sampled pairs: its match rows and sum |C_i| per pair, and
+    the wall time (the CPU baseline)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.build()
+    t0 = time.perf_counter()
+    mjs, ncs = oracle.match_batch(sc.images, [pairs[k] for k in idx], n_threads=cores)
+    dt = time.perf_counter() - t0
+    return [oracle.matches_from_match_j(mj) for mj in mjs], ncs, dt, cores
+
+
+def _parity(gm, ctx, sc, pairs, off_h, rows_d, idx, want, ncs):
+    """Sampled pairs of the last timed step against the oracle, element by element; and the sample run again as a
+    batch of its own, whose sum |C_i| must equal the oracle's."""
+    import torch
+    mismatches = []
+    for t, k in enumerate(idx):
+        got = rows_d[int(off_h[k]):int(off_h[k + 1])].cpu().numpy()
+        if not np.array_equal(got, want[t]):
+            mismatches.append(int(k))
+    sub = [pairs[k] for k in idx]
+    gp = _pair_array(gm, sub)
+    cap = sum(sc.images[p.a].n for p in sub)
+    off = torch.empty(len(sub) + 1, dtype=torch.int64, device=rows_d.device)
+    rows = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=rows_d.device)
+    gm.gm_match_pairs(ctx.h, gp, off, rows, cap)
+    cand = ctx.stats()["n_candidates"]
+    return {"pairs_checked": len(idx), "mismatches": len(mismatches), "mismatched_pairs": mismatches[:10],
+            "candidates_checked": int(ncs.sum()), "candidates_equal": bool(cand == int(ncs.sum())),
+            "rule": "match rows of sampled pairs of the last timed step equal the oracle's (bit-exact)"}
+
+
+def _batch_bound_bytes(sc, pairs, n_matches):
+    """Per-batch HBM lower bound: every image the batch uses read once (128-byte descriptor + 8-byte xy per
+    keypoint), every pair's F (36 bytes) and its match rows (8 bytes each)."""
+    used = {p.a for p in pairs} | {p.b for p in pairs}
+    return 136 * sum(sc.images[i].n for i in used) + 36 * len(pairs) + 8 * n_matches
+
+
+def run_headline(args, gm, dev, local, rank, world, peaks, peak_kind):
+    """One step = one gm_match_pairs call over the whole component (lines, query order, band walk, exact distances,
+    top-2, ratio test, match-list compaction), images resident.  The street component (default) runs with the
+    autotuned setting; both run through a captured CUDA graph unless --no-graph."""
+    import torch
+    kind = args.workload
+    sc = _headline_scene(kind, rank)
+    if args.pairs:
+        sc.pairs = sc.pairs[:args.pairs]
+    pairs = sc.pairs
+    used = sorted({p.a for p in pairs} | {p.b for p in pairs})
+    workload = _workload_name(kind, sc) if not args.pairs else f"{_workload_name(kind, sc)}_first{args.pairs}"
+    stream = torch.cuda.current_stream(dev)
+    ctx = gm.Context(device=local, stream=stream, path=args.path, cell_px=args.cell)
+    if args.schedule:
+        ctx.set_option(gm.GM_OPT_SCHEDULE, args.schedule)
+    if args.group != 16:
+        ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
+    ctx.put_images({k: sc.images[k] for k in used})
+    gp = _pair_array(gm, pairs)
+    tune = None
+    if kind == "street" and not args.path and not args.cell and not args.no_autotune:
+        tune = ctx.autotune(gp, repeats=1)
+    if not args.no_graph:
+        ctx.set_option(gm.GM_OPT_GRAPH, 1)
+    cap = sum(sc.images[p.a].n for p in pairs)
+    off_d = torch.empty(len(pairs) + 1, dtype=torch.int64, device=dev)
+    rows_d = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        return gm.gm_match_pairs(ctx.h, gp, off_d, rows_d, cap)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    st_list = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.fill_(k)                      # evict L2 between steps (outside the timed events)
+            ev[k][0].record(stream)
+            n_rows = step()
+            ev[k][1].record(stream)
+            st_list.append(ctx.stats())
+        torch.cuda.synchronize(dev)
+    clocks = clk.summary()
+    ms_local = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms_match = float(np.mean([s["ms_match"] for s in st_list]))
+    st = st_list[-1]
+    off_h = off_d.cpu().numpy()
+    ms = _reduce(ms_local, "max", world, dev)                 # the slowest rank's step
+    units = _reduce(len(pairs), "sum", world, dev)            # pairs matched by all ranks in one step
+    value = units / (ms / 1e3)
+    comps_per_s = _reduce(st["n_candidates"], "sum", world, dev) / (ms / 1e3)
+
+    # ---- the same batch launched directly (no graph replay), and the plain one-pair-per-launch form
+    direct = None
+    if not args.no_graph and not args.schedule:
+        ctx.set_option(gm.GM_OPT_GRAPH, 0)
+        ms_direct, _, _ = _time_batch(gm, ctx, gp, cap, max(3, args.steps // 4), 1, dev)
+        ctx.set_option(gm.GM_OPT_GRAPH, 1)
+        direct = {"ms_per_step": ms_direct, "graph_gain": ms_direct / ms_local}
+    one_pair = None
+    if not args.schedule and not args.no_one_pair:
+        ctx.set_option(gm.GM_OPT_GRAPH, 0)
+        ctx.set_option(gm.GM_OPT_SCHEDULE, 1)
+        ms1, _, _ = _time_batch(gm, ctx, gp, cap, 2, 1, dev)
+        ctx.set_option(gm.GM_OPT_SCHEDULE, 0)
+        ctx.set_option(gm.GM_OPT_GRAPH, 0 if args.no_graph else 1)
+        one_pair = {"value": len(pairs) / (ms1 / 1e3), "unit": UNIT, "ms_per_step": ms1,
+                    "batched_speedup": ms1 / ms_local,
+                    "form": "every pair its own order, stream and match launches (GM_OPT_SCHEDULE = 1)"}
+
+    # ---- end to end through the public API with host buffers (pinned): upload + binning of every image of the
+    # batch, the match, the download of the offsets and rows
+    pinned = {}
+    h2d = 0
+    for k in used:
+        im = sc.images[k]
+        xy = torch.from_numpy(im.xy).pin_memory()
+        scl = torch.from_numpy(im.scale).pin_memory()
+        ds = torch.from_numpy(im.desc).pin_memory()
+        pinned[k] = (im.width, im.height, xy, scl, ds)
+        h2d += xy.numel() * 4 + scl.numel() * 4 + ds.numel()
+    off_h2 = torch.empty(len(pairs) + 1, dtype=torch.int64).pin_memory()
+    rows_h = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
+    h2d += len(gp) * ctypes.sizeof(gm.GmPair)   # the gm_pair records handed to the library
+    e2e_ctx = gm.Context(device=local, stream=stream, path=args.path, cell_px=args.cell)
+    if tune is not None:   # the tuned setting, as a tuner cache would give it
+        e2e_ctx.set_option(gm.GM_OPT_PATH, tune["path"])
+        e2e_ctx.set_option(gm.GM_OPT_MMA_GROUP, tune["mma_group"])
+        e2e_ctx.set_option(gm.GM_OPT_CELL_PX, tune["cell_px"])
+    elif args.group != 16:
+        e2e_ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
+    if not args.no_graph:
+        e2e_ctx.set_option(gm.GM_OPT_GRAPH, 1)
+    batch = gm.make_images([(k, w, h, xy, scl, ds) for k, (w, h, xy, scl, ds) in pinned.items()])
+
+    def e2e_step():   # all images of the step in one gm_images_put call, then the batch
+        gm.gm_images_put(e2e_ctx.h, batch)
+        return gm.gm_match_pairs(e2e_ctx.h, gp, off_h2, rows_h, cap)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.e2e_steps)]
+    n_out = 0
+    for k in range(args.e2e_steps):
+        flush.fill_(k)
+        e_ev[k][0].record(stream)
+        n_out = e2e_step()
+        e_ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = _reduce(float(np.mean([a.elapsed_time(b) for a, b in e_ev])), "max", world, dev)
+    d2h = (len(pairs) + 1) * 8 + n_out * 8
+    e2e_ctx.close()
+
+    # ---- roofline of the dominant kernel (band walk + distances + top-2 + ratio test).  The binding bound is HBM:
+    # each pair's unique inputs once (136 B per keypoint of A and B, 36 B of F, 8 B per match row) take longer at
+    # the measured copy bandwidth than the candidate comparisons (256 ops each) take on the tensor pipe.
     kname, ksrc, kdtype = MATCH_KERNELS[st["path_used"]]
-    alg = _algorithmic_bytes(sc, sc.pairs, st["n_matches"])
-    ach = alg / (ms_match / 1e3) / 1e9
-    line = {"metric": METRIC, "value": len(gp) / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    alg_bytes = _algorithmic_bytes(sc, pairs, st["n_matches"])
+    achieved = alg_bytes / (ms_match / 1e3) / 1e9
+    traffic = _profiled_traffic(kname, ksrc, workload) if args.cell in (0, 4) else None
+    tensor_ops = 256.0 * st["n_candidates"]
+    bound = _batch_bound_bytes(sc, pairs, st["n_matches"])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
+                "peak_source": f"{peak_kind} (STREAM-style copy)", "algorithmic_bytes_per_launch": alg_bytes,
+                "ms_per_launch": ms_match, "kernel_share_of_step": ms_match / ms_local,
+                "examined_per_candidate": st["n_examined"] / max(1, st["n_candidates"]),
+                "hbm_batch_bound_bytes": bound,
+                "batch_bound_view": {"achieved": bound / (ms_match / 1e3) / 1e9,
+                                     "frac": bound / (ms_match / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                     "note": "every image of the batch read once, against the same kernel time"},
+                "tensor_view": {"ops_per_launch": tensor_ops,
+                                "achieved_tops": tensor_ops / (ms_match / 1e3) / 1e12,
+                                "peak_tops": peaks["bf16_tflops"],
+                                "frac": tensor_ops / (ms_match / 1e3) / 1e12 / peaks["bf16_tflops"],
+                                "note": "candidate comparisons x 128 MACs against the measured bf16 burst peak "
+                                        "(the fp16 dense rate equals bf16)"}}
+    band = "uniform [2, 8] per pair" if kind == "street" else 4.0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": kdtype, "data": "synthetic (seeded street scene)",
-            "config": {"workload": f"street_1000img_2k-20kp_{len(gp)}pairs_d2-8", "pairs": len(gp),
-                       "images": len(sc.images), "keypoints": int(sum(im.n for im in sc.images)),
-                       "l2": "flushed between steps (512 MB write)", "graph": True},
-            "comparisons_per_s": st["n_candidates"] / (ms / 1e3), "candidates_per_step": st["n_candidates"],
-            "autotune": tune, "ms_match_kernel": ms_match,
-            "one_pair_per_launch": {"value": len(gp) / (ms1 / 1e3), "unit": UNIT, "ms_per_step": ms1},
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": kname,
-                         "peak_source": f"{peak_kind} (STREAM-style copy)"}}
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = _oracle_comparisons(sc, sc.pairs)
-    print(json.dumps(line), flush=True)
+            "vs_baseline": None, "dtype": kdtype,
+            "data": f"synthetic (seeded {kind} scene; stands in for the paper's Rome16K-style components)",
+            "config": {"workload": workload, "pairs": len(pairs), "images": len(used),
+                       "keypoints": int(sum(sc.images[k].n for k in used)), "band_px": band, "ratio": 0.8,
+                       "cell_px": args.cell or (tune["cell_px"] if tune else "auto (4)"), "group": args.group,
+                       "l2": "flushed between steps (512 MB write)", "path": st["path_used"],
+                       "schedule": "persistent batch" if not args.schedule else "one pair per launch",
+                       "graph": not args.no_graph and not args.schedule,
+                       "sharding": "one component per rank (pairs are independent); no collective on the data path"},
+            "comparisons_per_s": comps_per_s, "candidates_per_step": st["n_candidates"],
+            "examined_per_step": st["n_examined"], "redecided_per_step": st["n_redecided"],
+            "matches_per_step": st["n_matches"], "ms_match_kernel": ms_match,
+            "cta_finish_spread": st["cta_finish_spread"], "unstaged_groups": st["n_unstaged_groups"],
+            "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(args.steps * st["kernel_launches"]),
+            "roofline": roofline, "clocks": clocks}
+    if tune is not None:
+        line["autotune"] = tune
+    if direct is not None:
+        line["direct_launch"] = direct
+    if one_pair is not None:
+        line["one_pair_per_launch"] = one_pair
+    if args.serve_seconds > 0:
+        line["serving"] = _serving(gm, ctx, gp, args.serve_rate, args.serve_seconds)
+    if rank == 0 and not args.no_cpu_baseline:
+        idx = _parity_sample(sc, pairs, args.sample, 1512)
+        want, ncs, dt, cores = _oracle_sample(sc, pairs, idx)
+        line["parity"] = _parity(gm, ctx, sc, pairs, off_h, rows_d[:n_rows], idx, want, ncs)
+        line["cpu_baseline"] = {"value": len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{len(idx)} seeded pairs of the {len(pairs)}, {cores} threads, "
+                                          f"{dt:.1f} s wall",
+                                "comparisons_per_s": float(ncs.sum()) / dt}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+
+def _dense_parity(sc, pairs, idx, off_h, rows_d):
+    """Sampled pairs of the timed batch against the oracle (all host cores), element by element."""
+    want, ncs, dt, cores = _oracle_sample(sc, pairs, idx)
+    bad = [int(k) for t, k in enumerate(idx)
+           if not np.array_equal(rows_d[int(off_h[k]):int(off_h[k + 1])].cpu().numpy(), want[t])]
+    return {"pairs_checked": len(idx), "mismatches": len(bad), "mismatched_pairs": bad[:10],
+            "oracle_s": round(dt, 2), "oracle_cores": cores}
 
 
 def run_dense(args, gm, dev, local, peaks, peak_kind):
-    """Dense stress: street geometry with 16000 keypoints per image, the top 30000 pairs, band d swept over 2, 4, 8
-    and 16 px (tc path) plus the paths compared at d = 4, and the whole-image band (exhaustive matching) on 300
-    pairs."""
+    """Dense stress: street geometry with 16000 keypoints per image, the top pairs by co-visibility (>= 50 points:
+    20671 of the 30000 asked for), band d swept over 2, 4, 8 and 16 px (tc path) plus the paths compared at d = 4,
+    and the whole-image band (exhaustive matching) on 300 pairs.  Every band's timed batch is checked against the
+    oracle on a seeded sample of pairs (200 at finite d, 16 whole pairs at d = inf)."""
     import scenes
     sc = scenes.street(n_kp=16000, n_pairs=30000)
     stream = __import__("torch").cuda.current_stream(dev)
@@ -372,12 +607,23 @@ def run_dense(args, gm, dev, local, peaks, peak_kind):
     ctx.put_images({k: im for k, im in enumerate(sc.images)})
     ctx.set_option(gm.GM_OPT_GRAPH, 1)
     cap = sum(sc.images[p.a].n for p in sc.pairs)
+    check = not args.no_cpu_baseline
+    idx = _parity_sample(sc, sc.pairs, args.sample, 1512)
     sweep = []
     for d in (2.0, 4.0, 8.0, 16.0):
         gp = _pair_array(gm, sc.pairs, d)
-        ms, msm, st = _time_batch(gm, ctx, gp, cap, max(1, min(args.steps, 3)), 2, dev)
-        sweep.append({"d": d, "path": "tc", "pairs_per_s": len(gp) / (ms / 1e3), "ms_per_step": ms, "ms_match": msm,
-                      "comparisons_per_s": st["n_candidates"] / (ms / 1e3), "candidates_per_step": st["n_candidates"]})
+        out = []
+        ms, msm, st = _time_batch(gm, ctx, gp, cap, max(1, min(args.steps, 3)), 2, dev, out)
+        row = {"d": d, "path": "tc", "pairs_per_s": len(gp) / (ms / 1e3), "ms_per_step": ms, "ms_match": msm,
+               "comparisons_per_s": st["n_candidates"] / (ms / 1e3), "candidates_per_step": st["n_candidates"],
+               "examined_per_candidate": st["n_examined"] / max(1, st["n_candidates"]),
+               "unstaged_groups": st["n_unstaged_groups"], "stream_reruns": st["n_stream_reruns"],
+               "cta_finish_spread": st["cta_finish_spread"]}
+        if check:
+            row["parity"] = _dense_parity(sc, [scenes.Pair(p.a, p.b, p.F, d, p.p, p.q) for p in sc.pairs], idx,
+                                          *out[0])
+        del out
+        sweep.append(row)
     gp4 = _pair_array(gm, sc.pairs, 4.0)
     for name, path, group in (("mma16", 2, 16), ("simt", 3, 16)):
         ctx.set_option(gm.GM_OPT_PATH, path)
@@ -388,22 +634,34 @@ def run_dense(args, gm, dev, local, peaks, peak_kind):
     sub = sc.pairs[:300]
     capi = sum(sc.images[p.a].n for p in sub)
     gpi = _pair_array(gm, sub, float("inf"))
+    idx_inf = _parity_sample(sc, sub, 16, 1513)
     for name, path in (("tc", 1), ("mma16", 2)):
         ctx.set_option(gm.GM_OPT_PATH, path)
         ctx.set_option(gm.GM_OPT_MMA_GROUP, 16)
-        ms, msm, st = _time_batch(gm, ctx, gpi, capi, 1, 1, dev)
+        out = []
+        ms, msm, st = _time_batch(gm, ctx, gpi, capi, 1, 1, dev, out)
         ops = 256.0 * st["n_candidates"]
-        sweep.append({"d": "inf", "path": name, "pairs": len(gpi), "pairs_per_s": len(gpi) / (ms / 1e3), "ms_per_step": ms,
-                      "comparisons_per_s": st["n_candidates"] / (ms / 1e3),
-                      "tensor_frac_of_bf16_peak": ops / (msm / 1e3) / 1e12 / peaks["bf16_tflops"]})
+        row = {"d": "inf", "path": name, "pairs": len(gpi), "pairs_per_s": len(gpi) / (ms / 1e3), "ms_per_step": ms,
+               "ms_match": msm, "comparisons_per_s": st["n_candidates"] / (ms / 1e3),
+               "tensor_frac_of_bf16_peak": ops / (msm / 1e3) / 1e12 / peaks["bf16_tflops"]}
+        if check and name == "tc":
+            row["parity"] = _dense_parity(sc, [scenes.Pair(p.a, p.b, p.F, float("inf"), p.p, p.q) for p in sub],
+                                          idx_inf, *out[0])
+        del out
+        sweep.append(row)
     ctx.close()
     head = sweep[1]
+    checked = [r["parity"] for r in sweep if "parity" in r]
     line = {"metric": "exact candidate comparisons/s", "value": head["comparisons_per_s"], "unit": "comparisons/s",
             "n_gpus": 1, "steps": max(1, min(args.steps, 3)), "warmup": 2, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f16 (integer-valued, f32 accumulate)", "data": "synthetic (seeded street scene, 16000 keypoints)",
             "config": {"workload": f"dense_1000img_16000kp_{len(sc.pairs)}pairs", "headline": "tc, d = 4 px",
                        "peak_source": peak_kind}, "sweep": sweep}
+    if checked:
+        line["parity"] = {"pairs_checked": sum(c["pairs_checked"] for c in checked),
+                          "mismatches": sum(c["mismatches"] for c in checked),
+                          "bands": "2, 4, 8, 16 px (200 pairs each) and inf (16 whole pairs)"}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _oracle_comparisons(sc, [scenes.Pair(p.a, p.b, p.F, 4.0, p.p, p.q) for p in sc.pairs])
     print(json.dumps(line), flush=True)
@@ -436,9 +694,27 @@ def run_two_view(args, gm, dev, local):
     print(json.dumps(line), flush=True)
 
 
+def _time_select(gm, ctx, stream, dev, n_cams, off, cams, T, k, warmup, steps):
+    import torch
+    d_off, d_cams = torch.from_numpy(off).to(dev), torch.from_numpy(cams).to(dev)
+    cap = max(1, n_cams * min(k, n_cams))
+    out = torch.empty((cap + 1, 3), dtype=torch.int32, device=dev)
+    for _ in range(warmup):
+        n = gm.gm_select_pairs(ctx.h, n_cams, d_off, d_cams, T, k, out, out.shape[0])
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        n = gm.gm_select_pairs(ctx.h, n_cams, d_off, d_cams, T, k, out, out.shape[0])
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    return float(np.mean([a.elapsed_time(b) for a, b in ev])), n
+
+
 def run_pairs(args, gm, dev, local, peaks, peak_kind):
     """Candidate pair selection (Sec. 6.1) on the street component's point-camera visibility: 1000 images,
-    T = 8 co-visible points, top 10 % of the images per query."""
+    T = 8 co-visible points, top 10 % of the images per query; then a 16000-image sequence (the size of the
+    paper's largest collections; 2M points seen by runs of 2-14 neighbouring cameras), T = 8, top 10 %."""
     import scenes
     import torch
     sc = scenes.street()
@@ -446,22 +722,15 @@ def run_pairs(args, gm, dev, local, peaks, peak_kind):
     T, k = 8, n_cams // 10
     stream = torch.cuda.current_stream(dev)
     ctx = gm.Context(device=local, stream=stream)
-    d_off, d_cams = torch.from_numpy(off).to(dev), torch.from_numpy(cams).to(dev)
-    out = torch.empty((n_cams * k + 1, 3), dtype=torch.int32, device=dev)
-    for _ in range(max(args.warmup, 3)):
-        n = gm.gm_select_pairs(ctx.h, n_cams, d_off, d_cams, T, k, out, out.shape[0])
-    torch.cuda.synchronize(dev)
     steps = max(args.steps, 5)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for a, b in ev:
-        a.record(stream)
-        n = gm.gm_select_pairs(ctx.h, n_cams, d_off, d_cams, T, k, out, out.shape[0])
-        b.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms, n = _time_select(gm, ctx, stream, dev, n_cams, off, cams, T, k, max(args.warmup, 3), steps)
+    off16, cams16, n16 = scenes.path_visibility(16000, 2_000_000)
+    ms16, n_16 = _time_select(gm, ctx, stream, dev, n16, off16, cams16, T, n16 // 10, max(args.warmup, 3), steps)
     ctx.close()
     npairs_obs = int(sum(int(d) * (int(d) - 1) // 2 for d in np.diff(off)))
-    alg = 8.0 * off.size + 4.0 * cams.size + 2 * 4.0 * n_cams * n_cams + 12.0 * n
+    # inputs once (offsets, observations), the output rows; the co-visible counts stay on chip
+    alg = 8.0 * off.size + 4.0 * cams.size + 12.0 * n
+    alg16 = 8.0 * off16.size + 4.0 * cams16.size + 12.0 * n_16
     line = {"metric": "candidate pair selections/s", "value": 1e3 / ms, "unit": "selections/s", "n_gpus": 1,
             "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded street scene)",
@@ -470,8 +739,12 @@ def run_pairs(args, gm, dev, local, peaks, peak_kind):
                        "top_k": k, "pairs_out": n},
             "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
-                         "kernel": "covis_count_kernel + select_kernel",
-                         "algorithmic_bytes": alg, "peak_source": f"{peak_kind} (STREAM-style copy)"}}
+                         "kernel": "row_kernel (three passes) + transpose",
+                         "algorithmic_bytes": alg, "peak_source": f"{peak_kind} (STREAM-style copy)"},
+            "sixteen_thousand": {"workload": "select_pairs_path_16000img_2000000pts", "ms_per_step": ms16,
+                                 "selections_per_s": 1e3 / ms16, "observations": int(cams16.size),
+                                 "pairs_out": n_16, "top_k": n16 // 10,
+                                 "hbm_frac": alg16 / (ms16 / 1e3) / 1e9 / peaks["hbm_gbs"]}}
     if not args.no_cpu_baseline:
         from oracle import pairs as op
         t0 = time.perf_counter()
@@ -534,8 +807,9 @@ def run_tracks(args, gm, dev, local, peaks, peak_kind):
 
 
 def run_triangulate(args, gm, dev, local, peaks, peak_kind):
-    """Triangulation of the facade batch's tracks (Sec. 6.2 end): the tracks of the 1200 pairs' matches over the
-    800000 features of the 100 images, one FP64 least-squares point per track, cameras P = K [R | t]."""
+    """Triangulation of the facade batch's tracks (Sec. 6.3): the merged tracks of the 1200 pairs' matches over the
+    800000 features of the 100 images, one FP64 least-squares point per track, cameras P = K [R | t]; and the
+    per-image tracks the paper triangulates before merging (every query image's features with their matches)."""
     import scenes
     import torch
     sc = scenes.facade()
@@ -568,9 +842,29 @@ def run_triangulate(args, gm, dev, local, peaks, peak_kind):
         y.record(stream)
     torch.cuda.synchronize(dev)
     ms = float(np.mean([x.elapsed_time(y) for x, y in ev]))
+    # per-image tracks (Sec. 6.3's order, before merging): every query image's features with their matches in all
+    # its candidate images, from the batch's own outputs
+    d_off, d_rows = torch.from_numpy(off).to(dev), torch.from_numpy(m).to(dev)
+    ab = np.array([[p.a, p.b] for p in sc.pairs], np.int32)
+    cap_i = int(m.shape[0])
+    Xi = torch.empty((cap_i, 3), dtype=torch.float64, device=dev)
+    nodes_i = torch.empty(cap_i, dtype=torch.int64, device=dev)
+    nv_i = torch.empty(cap_i, dtype=torch.int32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        nti = gm.gm_triangulate_image_tracks(ctx.h, ids, d_P, ab, d_off, d_rows, Xi, nodes_i, nv_i, cap_i)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for x, y in ev:
+        x.record(stream)
+        nti = gm.gm_triangulate_image_tracks(ctx.h, ids, d_P, ab, d_off, d_rows, Xi, nodes_i, nv_i, cap_i)
+        y.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_i = float(np.mean([x.elapsed_time(y) for x, y in ev]))
     ctx.close()
     # labels, coordinates and positions of every node; accumulators, point, root and view count of every track
     alg = 20.0 * n_nodes + (72.0 + 24.0 + 8.0 + 4.0) * nt
+    # per-image: every match row and node once (8 B + 4 B flag), the rows searched, and point, node, views per track
+    alg_i = 8.0 * m.shape[0] + 4.0 * n_nodes + 12.0 * n_nodes + (24.0 + 8.0 + 4.0) * nti
     n_obs = int(nv[:nt].sum().item())
     line = {"metric": "tracks triangulated/s", "value": nt / (ms / 1e3), "unit": "tracks/s", "n_gpus": 1,
             "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
@@ -580,7 +874,11 @@ def run_triangulate(args, gm, dev, local, peaks, peak_kind):
             "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
                          "kernel": "tri_accum_kernel + tri_solve_kernel", "algorithmic_bytes": alg,
-                         "peak_source": f"{peak_kind} (STREAM-style copy)"}}
+                         "peak_source": f"{peak_kind} (STREAM-style copy)"},
+            "per_image_tracks": {"tracks": nti, "ms_per_step": ms_i, "tracks_per_s": nti / (ms_i / 1e3),
+                                 "match_rows": int(m.shape[0]),
+                                 "hbm_frac": alg_i / (ms_i / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                 "kernel": "trk_node_kernel (count pass, scan, solve pass)"}}
     if not args.no_cpu_baseline:
         from oracle import triangulate as otri
         labels = lab.cpu().numpy()
@@ -765,7 +1063,9 @@ def run_approx(args, gm, dev, local, peaks, peak_kind):
 
 def run_serving(args, gm, dev, local):
     """Serving: Poisson single-pair requests over the facade geometry with per-image keypoints log-uniform in
-    [2000, 20000], at 500, 1000, 2000 and 5000 req/s, under a 40 GB device-memory budget."""
+    [2000, 20000], at 500, 1000, 2000 and 5000 req/s (at least --serve-requests requests per rate, so that each p99
+    rests on 200 or more requests above it), under a 40 GB device-memory budget; then a budget that holds a fifth of
+    the images, with least-recently-used eviction."""
     import scenes
     rng = np.random.default_rng(151206235 + 4)
     n_kp = np.exp(rng.uniform(np.log(2000), np.log(20000), 100)).astype(np.int64)
@@ -779,7 +1079,8 @@ def run_serving(args, gm, dev, local):
     ctx.put_images({k: im for k, im in enumerate(sc.images)})
     gp = _pair_array(gm, sc.pairs)
     for r in (500, 1000, 2000, 5000):
-        s = _serving(gm, ctx, gp, r, args.serve_seconds if args.serve_seconds > 0 else 3.0)
+        s = _serving(gm, ctx, gp, r, args.serve_seconds if args.serve_seconds > 0 else 3.0,
+                     min_requests=args.serve_requests)
         s["budget"] = "40 GB"
         out["rates"].append(s)
     cs = gm.gm_image_cache_stats(ctx.h)
@@ -793,7 +1094,8 @@ def run_serving(args, gm, dev, local):
     budget = cs["work_bytes"] + total_bytes // 5
     ctx = gm.Context(device=local, stream=stream, mem_budget_bytes=budget, max_inflight=2)
     ctx.set_option(gm.GM_OPT_EVICT_LRU, 1)
-    s = _serving_cache(gm, ctx, sc, gp, images, 500, args.serve_seconds if args.serve_seconds > 0 else 3.0)
+    s = _serving_cache(gm, ctx, sc, gp, images, 500, args.serve_seconds if args.serve_seconds > 0 else 3.0,
+                       min_requests=args.serve_requests)
     s["budget"] = f"{budget / 2**20:.0f} MiB (images {total_bytes / 2**20:.0f} MiB in all)"
     out["small_budget"] = s
     ctx.close()
@@ -809,12 +1111,15 @@ def _algorithmic_bytes(sc, pairs, n_matches):
 
 
 def run_reference(args, rank, world):
-    """The oracle (plain FP64 CPU) on the host cores, on a bounded sample of the same workload per step."""
+    """The oracle (plain FP64 CPU) on the host cores, on a bounded sample of the same workload per step: the
+    headline component (street by default, or facade), `per_step` pairs spread over the batch per step."""
     if rank != 0:
         return
     import oracle
-    import scenes
-    sc = scenes.facade()
+    kind = args.workload if args.workload in ("street", "facade") else "street"
+    sc = _headline_scene(kind, 0)
+    if args.pairs:
+        sc.pairs = sc.pairs[:args.pairs]
     cores = os.cpu_count() or 1
     per_step = max(cores, 16)
     stride = max(1, len(sc.pairs) // (per_step * max(1, args.steps + args.warmup)))
@@ -831,34 +1136,15 @@ def run_reference(args, rank, world):
         if it >= args.warmup:
             t_steps.append(dt)
     v = per_step / float(np.mean(t_steps))
+    workload = _workload_name(kind, sc) if not args.pairs else f"{_workload_name(kind, sc)}_first{args.pairs}"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(t_steps)), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs_per_step": per_step, "sample": "pairs spread over the batch"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32", "data": f"synthetic (seeded {kind} scene)",
+            "config": {"workload": workload, "pairs_per_step": per_step, "sample": "pairs spread over the batch"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} of the 1200 pairs per step, {cores} threads"},
+                             "sample": f"{per_step} of the {len(sc.pairs)} pairs per step, {cores} threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def cpu_baseline(sc):
-    """Oracle throughput on a bounded sample (64 pairs spread over the batch) on all host cores."""
-    import oracle
-    cores = os.cpu_count() or 1
-    sample = sc.pairs[::max(1, len(sc.pairs) // 64)][:64]
-    oracle.build()
-    t0 = time.perf_counter()
-    _, ncs = oracle.match_batch(sc.images, sample, n_threads=cores)
-    dt = time.perf_counter() - t0
-    one = sample[::8]   # the same oracle on one thread, on every 8th pair of the sample
-    t1 = time.perf_counter()
-    oracle.match_batch(sc.images, one, n_threads=1)
-    dt1 = time.perf_counter() - t1
-    return {"value": len(sample) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(sample)} of {len(sc.pairs)} pairs (every {len(sc.pairs) // 64}th), {cores} threads, "
-                      f"{dt:.1f} s wall",
-            "comparisons_per_s": float(ncs.sum()) / dt,
-            "single_thread": {"value": len(one) / dt1, "unit": UNIT, "sample": f"{len(one)} of those pairs, 1 thread"}}
 
 
 def main():
@@ -875,14 +1161,20 @@ def main():
     ap.add_argument("--pairs", type=int, default=0, help="use only the first N pairs (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch every step directly (no CUDA graph replay)")
-    ap.add_argument("--workload", default="facade", choices=["facade", "two_view", "street", "dense", "serving", "pairs", "tracks",
-                                                       "triangulate", "coarse", "approx"],
-                    help="facade: the headline batch; two_view: one pair; street: uneven autotuned batch; dense: "
-                         "16000-keypoint band sweep; "
-                         "serving: Poisson requests; pairs: candidate pair selection; tracks: track merging; triangulate: track triangulation; "
+    ap.add_argument("--workload", default="street",
+                    choices=["street", "facade", "two_view", "dense", "serving", "pairs", "tracks", "triangulate",
+                             "coarse", "approx"],
+                    help="street: the headline, a 1000-image uneven component (autotuned); facade: the 100-image "
+                         "component; two_view: one pair; dense: 16000-keypoint band sweep; serving: Poisson requests; "
+                         "pairs: candidate pair selection; tracks: track merging; triangulate: track triangulation; "
                          "coarse: coarse-stage matching; approx: the paper's approximate search")
+    ap.add_argument("--sample", type=int, default=200, help="pairs of the oracle's parity / CPU-baseline sample")
+    ap.add_argument("--no-autotune", action="store_true", help="street: keep the library's default setting")
+    ap.add_argument("--no-one-pair", action="store_true", help="skip the one-pair-per-launch comparison")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving leg: Poisson arrivals, req/s")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving leg duration (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=20000,
+                    help="serving workload: at least this many requests per rate")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = _dist()
@@ -904,170 +1196,29 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if args.workload != "facade":
-        peaks, peak_kind = _load_peaks()
-        if args.workload == "street":
-            run_street(args, gm, dev, local, peaks, peak_kind)
-        elif args.workload == "dense":
-            run_dense(args, gm, dev, local, peaks, peak_kind)
-        elif args.workload == "two_view":
-            run_two_view(args, gm, dev, local)
-        elif args.workload == "pairs":
-            run_pairs(args, gm, dev, local, peaks, peak_kind)
-        elif args.workload == "tracks":
-            run_tracks(args, gm, dev, local, peaks, peak_kind)
-        elif args.workload == "triangulate":
-            run_triangulate(args, gm, dev, local, peaks, peak_kind)
-        elif args.workload == "coarse":
-            run_coarse(args, gm, dev, local, peaks, peak_kind)
-        elif args.workload == "approx":
-            run_approx(args, gm, dev, local, peaks, peak_kind)
-        else:
-            run_serving(args, gm, dev, local)
-        return
-    sc = scenes.facade(seed=_facade_seed(rank))
-    if args.pairs:
-        sc.pairs = sc.pairs[:args.pairs]
-    pairs = sc.pairs
-    stream = torch.cuda.current_stream(dev)
-    ctx = gm.Context(device=local, stream=stream, path=args.path, cell_px=args.cell)
-    if args.schedule:
-        ctx.set_option(gm.GM_OPT_SCHEDULE, args.schedule)
-    if args.group != 16:
-        ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
-    if not args.no_graph:
-        ctx.set_option(gm.GM_OPT_GRAPH, 1)
-    # ---- device-resident measurement: images registered before the timed region
-    ctx.put_images({k: im for k, im in enumerate(sc.images)})
-    gp = _pair_array(gm, pairs)
-    cap = sum(sc.images[p.a].n for p in pairs)
-    off_d = torch.empty(len(pairs) + 1, dtype=torch.int64, device=dev)
-    rows_d = torch.empty((cap, 2), dtype=torch.int32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-
-    def step():
-        return gm.gm_match_pairs(ctx.h, gp, off_d, rows_d, cap)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    st_list = []
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize(dev)
-        for k in range(args.steps):
-            flush.fill_(k)                      # evict L2 between steps (outside the timed events)
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-            st_list.append(ctx.stats())
-        torch.cuda.synchronize(dev)
-    clocks = clk.summary()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = float(np.mean(step_ms))
-    ms_match = float(np.mean([s["ms_match"] for s in st_list]))
-    st = st_list[-1]
-    ms = _reduce(ms, "max", world, dev)                       # the slowest rank's step
-    units = _reduce(len(pairs), "sum", world, dev)            # pairs matched by all ranks in one step
-    value = units / (ms / 1e3)
-    comps_per_s = _reduce(st["n_candidates"], "sum", world, dev) / (ms / 1e3)
-
-    # ---- end-to-end through the public API with host buffers (pinned): upload + binning + match + download
-    pinned = []
-    h2d = 0
-    for im in sc.images:
-        xy = torch.from_numpy(im.xy).pin_memory()
-        scl = torch.from_numpy(im.scale).pin_memory()
-        ds = torch.from_numpy(im.desc).pin_memory()
-        pinned.append((im.width, im.height, xy, scl, ds))
-        h2d += xy.numel() * 4 + scl.numel() * 4 + ds.numel()
-    off_h = torch.empty(len(pairs) + 1, dtype=torch.int64).pin_memory()
-    rows_h = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
-    h2d += len(gp) * ctypes.sizeof(gm.GmPair)   # the gm_pair records handed to the library
-    e2e_ctx = gm.Context(device=local, stream=stream, path=args.path, cell_px=args.cell)
-    if args.group != 16:
-        e2e_ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
-    if not args.no_graph:
-        e2e_ctx.set_option(gm.GM_OPT_GRAPH, 1)
-
-    batch = gm.make_images([(k, w, h, xy, scl, ds) for k, (w, h, xy, scl, ds) in enumerate(pinned)])
-
-    def e2e_step():   # all images of the step in one gm_images_put call, then the batch
-        gm.gm_images_put(e2e_ctx.h, batch)
-        return gm.gm_match_pairs(e2e_ctx.h, gp, off_h, rows_h, cap)
-
-    e2e_step()
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.e2e_steps)]
-    n_out = 0
-    for k in range(args.e2e_steps):
-        flush.fill_(k)
-        e_ev[k][0].record(stream)
-        n_out = e2e_step()
-        e_ev[k][1].record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = _reduce(float(np.mean([a.elapsed_time(b) for a, b in e_ev])), "max", world, dev)
-    d2h = (len(pairs) + 1) * 8 + n_out * 8
-    e2e_ctx.close()
-
-    # ---- roofline of the dominant kernel (band walk + distances + top-2 + ratio test).  The binding bound is HBM:
-    # each pair's unique inputs once (136 B per keypoint of A and B, 36 B of F, 8 B per match row) take longer at
-    # the measured copy bandwidth than the candidate comparisons (256 ops each) take on the tensor pipe.
     peaks, peak_kind = _load_peaks()
-    kname, ksrc, kdtype = MATCH_KERNELS[st["path_used"]]
-    alg_bytes = _algorithmic_bytes(sc, pairs, st["n_matches"])
-    achieved = alg_bytes / (ms_match / 1e3) / 1e9
-    traffic = _profiled_traffic(kname, ksrc, WORKLOAD) if not args.pairs and args.cell in (0, 4) else None
-    tensor_ops = 256.0 * st["n_candidates"]
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
-                "peak_source": f"{peak_kind} (STREAM-style copy)", "algorithmic_bytes_per_launch": alg_bytes,
-                "ms_per_launch": ms_match,
-                "tensor_view": {"ops_per_launch": tensor_ops,
-                                "achieved_tops": tensor_ops / (ms_match / 1e3) / 1e12,
-                                "peak_tops": peaks["bf16_tflops"],
-                                "frac": tensor_ops / (ms_match / 1e3) / 1e12 / peaks["bf16_tflops"],
-                                "note": "candidate comparisons x 128 MACs against the measured bf16 burst peak "
-                                        "(the fp16 dense rate equals bf16)"}}
-    serving = None
-    if args.serve_seconds > 0:
-        serving = _serving(gm, ctx, gp, args.serve_rate, args.serve_seconds)
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": kdtype, "data": "synthetic (seeded facade scene; stands in for the paper's "
-                                                         "Rome16K-style components)",
-            "config": {"workload": WORKLOAD if not args.pairs else f"{WORKLOAD}_first{args.pairs}", "pairs": len(pairs), "images": len(sc.images), "keypoints_per_image": 8000,
-                       "band_px": 4.0, "ratio": 0.8, "cell_px": args.cell or "auto (4)", "group": args.group, "l2": "flushed between steps (512 MB write)",
-                       "path": st["path_used"], "schedule": "persistent batch" if not args.schedule else "one pair per launch",
-                       "graph": not args.no_graph and not args.schedule,
-                       "sharding": "one facade component per rank (pairs are independent); no collective on the "
-                                   "data path"},
-            "comparisons_per_s": comps_per_s, "candidates_per_step": st["n_candidates"],
-            "examined_per_step": st["n_examined"], "redecided_per_step": st["n_redecided"], "matches_per_step": st["n_matches"],
-            "ms_match_kernel": ms_match,
-            "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": int(args.steps * st["kernel_launches"]),
-            "roofline": roofline, "clocks": clocks}
-    if serving is not None:
-        line["serving"] = serving
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc)
-    ctx.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    if args.workload in ("street", "facade"):
+        run_headline(args, gm, dev, local, rank, world, peaks, peak_kind)
+    elif args.workload == "dense":
+        run_dense(args, gm, dev, local, peaks, peak_kind)
+    elif args.workload == "two_view":
+        run_two_view(args, gm, dev, local)
+    elif args.workload == "pairs":
+        run_pairs(args, gm, dev, local, peaks, peak_kind)
+    elif args.workload == "tracks":
+        run_tracks(args, gm, dev, local, peaks, peak_kind)
+    elif args.workload == "triangulate":
+        run_triangulate(args, gm, dev, local, peaks, peak_kind)
+    elif args.workload == "coarse":
+        run_coarse(args, gm, dev, local, peaks, peak_kind)
+    elif args.workload == "approx":
+        run_approx(args, gm, dev, local, peaks, peak_kind)
+    else:
+        run_serving(args, gm, dev, local)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
-
 
 if __name__ == "__main__":
     main()

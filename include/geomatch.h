@@ -111,6 +111,13 @@ typedef struct {
     int32_t path_used;           /* GM_PATH_* of the distance kernel that ran */
     int32_t kernel_launches;     /* kernels launched by the call */
     int64_t n_device_errors;     /* device-side bounded waits that ran out (the call then fails with TIMEOUT) */
+    int64_t n_stream_reruns;     /* times the batch ran again because its candidate streams overflowed the buffer
+                                    (the buffer then grows to what the batch needed) */
+    int64_t n_unstaged_groups;   /* tcgen05-path query groups whose candidate stream was too long to stage in shared
+                                    memory (their positions are read from global memory) */
+    float cta_finish_spread;     /* load balance of the persistent tcgen05 grid: (last CTA finish - first CTA
+                                    finish) / (last CTA finish - earliest CTA start); 0 on other paths */
+    int32_t reserved0;
 } gm_stats;
 
 /* Result of gm_autotune. */
@@ -184,7 +191,8 @@ GM_API gm_status gm_image_cache_stats(gm_ctx *ctx, int64_t *images, int64_t *byt
  * For each query image q the candidates are the images i != q that see more than `threshold` of the points q sees
  * (|Points(C_q) & Points(C_i)| > T); only the `top_k` of them with the most co-visible points are kept (ties: the
  * lower image index first), and the result is the set of unique unordered pairs over all queries.
- *   n_cams:     images 0 .. n_cams-1 (at most 16384; the co-visible counts are a dense n_cams^2 int32 matrix);
+ *   n_cams:     images 0 .. n_cams-1, at most 49152 (each image's co-visible counts are one row of n_cams uint32 in
+ *               shared memory; device memory holds only the inputs, their camera -> points transpose and O(n_cams));
  *   point_off:  int64 [n_points + 1], nondecreasing from 0; point p is seen by point_cams[point_off[p] ..
  *               point_off[p+1]-1] (distinct cameras; GM_ERR_INVALID otherwise);
  *   point_cams: int32 [point_off[n_points]];  both host or both device memory;
@@ -204,7 +212,7 @@ GM_API gm_status gm_select_pairs(gm_ctx *ctx, int32_t n_cams, int64_t n_points, 
 GM_API gm_status gm_merge_tracks(gm_ctx *ctx, int64_t n_nodes, int64_t n_edges, const int64_t *edges, int64_t *labels,
                                  int64_t *n_tracks);
 
-/* Track triangulation (the end of Sec. 6.2: every merged track becomes a 3D point by linear least squares).
+/* Track triangulation (Sec. 6.3: every merged track becomes a 3D point by linear least squares).
  * Nodes are numbered image-major over image_ids (int32 [n_images], host memory): node = (features of
  * image_ids[0 .. k-1]) + feature index in image image_ids[k] (the caller's keypoint order); n_nodes must equal the
  * total.  labels (int64 [n_nodes]) are those of
@@ -220,6 +228,28 @@ GM_API gm_status gm_merge_tracks(gm_ctx *ctx, int64_t n_nodes, int64_t n_edges, 
 GM_API gm_status gm_triangulate(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids, const double *P,
                                 int64_t n_nodes, const int64_t *labels, int64_t cap, double *X, int64_t *roots,
                                 int32_t *n_views, int64_t *n_tracks);
+
+/* Per-image track triangulation (Sec. 6.3, the step before merging): the paper forms, for every query image, the
+ * tracks of its features from the matches found in all its candidate images, and triangulates them image by image
+ * (so a feature pair matched in both directions gives the same point twice; merging removes such duplicates).
+ * The track of feature k of query image q is the observation (q, k), then (c, j) for every pair (q, c), in the
+ * order of the pair list, in which k matched j.  Every track with at least two observations becomes a point by
+ * the linear least squares of gm_triangulate, its sums taken in the track's observation order (deterministic).
+ * Images, cameras and node numbering as in gm_triangulate (image_ids host memory; node = features of
+ * image_ids[0 .. k-1] + feature index).  The pairs and their matches are those of a gm_match_pairs call:
+ *   pair_images: int32 [n_pairs][2] (img_a, img_b) image ids, each in image_ids, host memory; ordered pairs, each
+ *                listed once, img_a != img_b (GM_ERR_INVALID otherwise); img_a is the query image;
+ *   pair_off:    int64 [n_pairs + 1], pair_off[0] = 0, non-decreasing; host or device;
+ *   matches:     int32 [pair_off[n_pairs]][2] rows (i_A, j_B), i strictly increasing within each pair, both
+ *                inside their images (GM_ERR_INVALID otherwise); host or device (8-byte aligned).
+ * Outputs (cap rows each): X double [cap][3], nodes int64 [cap] (the query node of each track, increasing),
+ * n_views int32 [cap]; *n_tracks = number of tracks.  If it exceeds cap, nothing is written and the call returns
+ * GM_ERR_NOMEM.  X, nodes and n_views all host or all device memory (GM_ERR_INVALID otherwise).
+ * Errors: GM_ERR_INVALID, GM_ERR_NOT_FOUND (an image not put), GM_ERR_NOMEM, GM_ERR_BUDGET, GM_ERR_CUDA. */
+GM_API gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids,
+                                             const double *P, int32_t n_pairs, const int32_t *pair_images,
+                                             const int64_t *pair_off, const int32_t *matches, int64_t cap, double *X,
+                                             int64_t *nodes, int32_t *n_views, int64_t *n_tracks);
 
 /* Coarse stage (Sec. 4): matching of the high-scale features of image pairs without geometry.  Every image keeps
  * its floor(n * eta_pct / 100) features of the largest scale (equal scales: the lower feature index first); an

@@ -45,10 +45,9 @@ def select_pairs(n_cams: int, point_off, point_cams, threshold: int, top_k: int)
     C = covisibility(n_cams, point_off, point_cams)
     chosen = set()
     for q in range(n_cams):
-        cand = [(int(C[q, i]), i) for i in range(n_cams) if i != q and C[q, i] > threshold]
-        cand.sort(key=lambda t: (-t[0], t[1]))
-        for cnt, i in cand[:max(top_k, 0)]:
-            chosen.add((min(q, i), max(q, i)))
+        i = np.nonzero((C[q] > threshold) & (np.arange(n_cams) != q))[0]   # S_q
+        i = i[np.lexsort((i, -C[q, i]))][:max(top_k, 0)]                    # by count, descending; ties: lower index
+        chosen.update((min(q, int(t)), max(q, int(t))) for t in i)
     rows = sorted(chosen)
     out = np.zeros((len(rows), 3), np.int64)
     for r, (a, b) in enumerate(rows):

@@ -25,6 +25,9 @@ using namespace gm;
 namespace gm {
 namespace {
 thread_local std::string g_err = "";
+// After the 64 counter shards of a batch: the persistent kernels' work-queue counter (int32 in the first 8 bytes),
+// the candidate-stream entries used, and the tcgen05 grid's three timing words (launch_match_tc).
+constexpr size_t kCtrTail = 5 * sizeof(unsigned long long);
 }  // namespace
 
 gm_status fail(gm_status st, const char *fmt, ...)
@@ -304,7 +307,8 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
         return st;
     if ((st = ensure_dev(ctx, ws.d_ctr, sizeof(BatchCounters) * 64 + 256)) != GM_OK) return st;
     if ((st = ensure_host(ws.h_tab, tab_bytes)) != GM_OK) return st;
-    if ((st = ensure_host(ws.h_off, sizeof(int64_t) * (P + 1) + sizeof(BatchCounters) * 64 + 16)) != GM_OK) return st;
+    if ((st = ensure_host(ws.h_off, sizeof(int64_t) * (P + 1) + sizeof(BatchCounters) * 64 + kCtrTail)) != GM_OK)
+        return st;
 
     // distance path and work-item size
     int path = ctx->path == GM_PATH_AUTO ? GM_PATH_TC : ctx->path;
@@ -343,6 +347,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     BatchCounters *ctr = static_cast<BatchCounters *>(ws.d_ctr.p);
     int32_t *next = reinterpret_cast<int32_t *>(ctr + 64);
     unsigned long long *stream_used = reinterpret_cast<unsigned long long *>(ctr + 64) + 1;
+    unsigned long long *cta_time = reinterpret_cast<unsigned long long *>(ctr + 64) + 2;
     const ImageDev *imgs = static_cast<const ImageDev *>(ctx->d_imgs.p);
     int64_t *d_off = static_cast<int64_t *>(ws.d_off.p);
     int32_t *rows = rows_dst ? rows_dst : static_cast<int32_t *>(ws.d_rows.p);
@@ -368,7 +373,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
             return launch_match_tc(static_cast<const TmaMaps *>(ctx->d_maps.p),
                                    static_cast<const GroupDesc *>(ws.d_grec.p),
                                    static_cast<const int32_t *>(ws.d_grows.p), static_cast<const int32_t *>(ws.d_stream.p),
-                                   i0, i1, gsz > 0 ? gsz : ctx->num_sms, match_j, ctr, s);
+                                   i0, i1, gsz > 0 ? gsz : ctx->num_sms, match_j, ctr, cta_time, s);
         return launch_match_mma(mt, imgs, d_proc, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
     };
 
@@ -382,7 +387,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
         ws.launches = 0;
         GM_CUDA(record(ws.ev[0]));
         GM_CUDA(cudaMemcpyAsync(ds, hs, tab_bytes, cudaMemcpyHostToDevice, s));
-        GM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(BatchCounters) * 64 + 16, s));
+        GM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(BatchCounters) * 64 + kCtrTail, s));
         if (ctx->schedule == 1) {
             // plain form: every pair gets its own launches (one block per work item)
             GM_CUDA(record(ws.ev[1]));
@@ -420,7 +425,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
         int64_t *h_off = static_cast<int64_t *>(ws.h_off.p);
         BatchCounters *h_ctr = reinterpret_cast<BatchCounters *>(h_off + P + 1);
         GM_CUDA(cudaMemcpyAsync(h_off, d_off, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToHost, s));
-        GM_CUDA(cudaMemcpyAsync(h_ctr, ctr, sizeof(BatchCounters) * 64 + 16, cudaMemcpyDeviceToHost, s));
+        GM_CUDA(cudaMemcpyAsync(h_ctr, ctr, sizeof(BatchCounters) * 64 + kCtrTail, cudaMemcpyDeviceToHost, s));
         return GM_OK;
     };
     ws.path_used = path;
@@ -476,10 +481,18 @@ void engine_stats(gm_ctx *ctx, Workspace &ws, gm_stats &S)
         S.n_redecided += (int64_t)h_ctr[k].redecided;
     }
     S.n_matches = h_off[P];
-    for (int k = 0; k < 64; ++k) S.n_device_errors += (int64_t)h_ctr[k].errors;
+    for (int k = 0; k < 64; ++k) {
+        S.n_device_errors += (int64_t)h_ctr[k].errors;
+        S.n_unstaged_groups += (int64_t)h_ctr[k].unstaged;
+    }
     ws.overflow = 0;
     for (int k = 0; k < 64; ++k) ws.overflow += (int64_t)h_ctr[k].overflow;
-    ws.stream_used = (int64_t)reinterpret_cast<const unsigned long long *>(h_ctr + 64)[1];
+    const unsigned long long *tail = reinterpret_cast<const unsigned long long *>(h_ctr + 64);
+    ws.stream_used = (int64_t)tail[1];
+    if (ws.path_used == GM_PATH_TC && ctx->schedule != 1 && tail[4] > 0) {   // persistent tcgen05 grid
+        const unsigned long long t0 = ~tail[2], first = ~tail[3], last = tail[4];
+        if (last > t0) S.cta_finish_spread = (float)((double)(last - first) / (double)(last - t0));
+    }
     cudaEventElapsedTime(&S.ms_device, ws.ev[0], ws.ev[3]);
     cudaEventElapsedTime(&S.ms_match, ws.ev[1], ws.ev[2]);
     S.path_used = ws.path_used;
@@ -1147,6 +1160,7 @@ gm_status run_batch(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair *
         if ((st = engine_launch(ctx, ws, nullptr)) != GM_OK) return st;
         GM_CUDA(cudaStreamSynchronize(ws.stream));
         engine_stats(ctx, ws, ctx->stats);
+        ctx->stats.n_stream_reruns = attempt;
         if (!ws.overflow) break;
         if (attempt >= 2) return fail(GM_ERR_NOMEM, "%s: candidate stream buffer kept overflowing", fn);
         ws.stream_cap = ws.stream_used + ws.stream_used / 4 + 1024;   // grow to what the batch needed, then rerun

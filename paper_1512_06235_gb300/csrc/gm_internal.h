@@ -62,6 +62,7 @@ struct BatchCounters {
     unsigned long long redecided;   // FP64 re-decisions
     unsigned long long errors;      // device-side argument / bound violations (must stay 0)
     unsigned long long overflow;    // groups whose candidate stream did not fit the stream buffer
+    unsigned long long unstaged;    // tcgen05 groups whose stream is longer than kTcStagedPositions
 };
 
 // Self-contained description of one query group of the tensor-core path (written by the stream kernel, so the
@@ -86,6 +87,8 @@ struct alignas(16) GroupDesc {
     int64_t qoff;                   // the pair's offset in the per-query output
 };
 constexpr int kTcQueriesPerItem = 128;
+// Candidate positions a tcgen05 group stages in shared memory; a longer stream is read from global memory.
+constexpr int kTcStagedPositions = 1024;
 
 // ---- launchers (host functions defined in the .cu files) ---------------------------------------------------
 // Image registration, many images per launch, in two phases so that invalid input never touches a destination:
@@ -144,10 +147,11 @@ int match_mma_blocks_per_sm(int mt);
 // tcgen05 matching path (warp-specialised, TMA gather4 + tcgen05.mma): groups of kTcQueriesPerItem sorted
 // queries per work item, one persistent CTA per SM (grid CTAs take items item_begin + b, + grid, ...).
 // The group streams come from launch_stream; every image of the batch must have max(gx, gy) <=
-// match_tc_max_grid_lines().
+// match_tc_max_grid_lines().  cta_time[0..2] (zeroed by the caller) receive the complement of the earliest CTA
+// start, the complement of the first CTA finish and the last CTA finish (globaltimer, ns).
 cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const int32_t *grows, const int32_t *stream,
                             int64_t item_begin, int64_t item_end, int32_t grid, int32_t *match_j, BatchCounters *ctr,
-                            cudaStream_t st);
+                            unsigned long long *cta_time, cudaStream_t st);
 // Candidate streams of the tcgen05 groups [item_begin, item_end) of a batch (grec is indexed by item); *used
 // accumulates the stream entries written (zeroed by the caller).
 cudaError_t launch_stream(const ImageDev *imgs, const PairDev *pairs, const int64_t *item_off, int32_t n_pairs,

@@ -47,7 +47,7 @@ constexpr int kN = 64;              // candidates per chunk
 constexpr int kStages = 6;          // candidate chunks in flight
 constexpr int kAcc = 4;             // accumulator buffers in tensor memory
 constexpr int kSlots = 3;           // query groups in flight
-constexpr int kPosCap = 1024;       // candidate positions a slot stages in shared memory (multiple of kN)
+constexpr int kPosCap = kTcStagedPositions;   // candidate positions a slot stages in shared memory (multiple of kN)
 constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
 constexpr int kEpiWarps = 8;
 constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;   // worker warps: 8, 10, 11
@@ -80,6 +80,7 @@ struct Ctl {
 };
 constexpr int kSmemBytes = kOffCtl + (int)sizeof(Ctl) + 1024;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
+static_assert(kPosCap % kN == 0, "staged positions: whole chunks");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -312,8 +313,9 @@ __device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g,
 __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     const TmaMaps *__restrict__ maps, const GroupDesc *__restrict__ gdesc, const int32_t *__restrict__ grows,
     const int32_t *__restrict__ stream, int64_t item_begin, int64_t item_end, int32_t *__restrict__ match_j,
-    BatchCounters *__restrict__ ctr)
+    BatchCounters *__restrict__ ctr, unsigned long long *__restrict__ cta_time)
 {
+    const uint64_t t_start = globaltimer();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     Ctl &cl = *reinterpret_cast<Ctl *>(base + kOffCtl);
@@ -647,6 +649,12 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         BatchCounters *cc = ctr + (blockIdx.x % kCounterShards);
         atomicAdd(&cc->candidates, cl.stat[0]);
         atomicAdd(&cc->redecided, cl.stat[2]);
+        // load balance of the persistent grid: earliest start and first finish (stored complemented, so that
+        // atomicMax over a zeroed word gives the minimum) and last finish
+        const uint64_t t_end = globaltimer();
+        atomicMax(cta_time + 0, ~(unsigned long long)t_start);
+        atomicMax(cta_time + 1, ~(unsigned long long)t_end);
+        atomicMax(cta_time + 2, (unsigned long long)t_end);
     }
 }
 
@@ -670,7 +678,7 @@ int match_tc_max_grid_lines() { return kMaxGridLines; }
 
 cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const int32_t *grows, const int32_t *stream,
                             int64_t item_begin, int64_t item_end, int32_t grid, int32_t *match_j, BatchCounters *ctr,
-                            cudaStream_t st)
+                            unsigned long long *cta_time, cudaStream_t st)
 {
     const int64_t n = item_end - item_begin;
     if (n <= 0) return cudaSuccess;
@@ -678,7 +686,7 @@ cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const i
     if (e != cudaSuccess) return e;
     const int64_t g = std::max<int64_t>(1, grid > 0 ? std::min<int64_t>(grid, n) : n);
     match_tc_kernel<<<(unsigned)g, kThreads, kSmemBytes, st>>>(maps, gdesc, grows, stream, item_begin, item_end, match_j,
-                                                             ctr);
+                                                             ctr, cta_time);
     return cudaGetLastError();
 }
 

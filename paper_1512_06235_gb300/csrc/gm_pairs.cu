@@ -4,12 +4,16 @@
 // top k by co-visible count are kept (ties: the lower image index); the pairs to match are the unique unordered
 // pairs {q, i} over all queries, written as rows (a, b, count), a < b, sorted by (a, b).
 //
-// Three steps on the device:
-//   count:  one warp per 3D point adds 1 to the count of every pair of cameras that see it (atomics into the upper
-//           triangle of a dense n_cams x n_cams int32 matrix; bit 31 is kept for the selection flag);
-//   select: one block per query image finds its top k (a bisection on the count threshold, then the lowest indices
-//           among the ties at the threshold) and flags the chosen pairs (atomicOr of bit 31);
-//   emit:   per-row counts of flagged pairs, a scan, and one warp per row writing its rows in column order.
+// No n_cams x n_cams matrix: the co-visible counts of one query camera form one row, accumulated in shared memory
+// (shared-memory atomics) from the camera's own points, and every pass recounts the row it needs.
+//   transpose: the point -> cameras lists become camera -> points lists (counts, scan, fill);
+//   select:    one block per query q counts its row, then finds its top k (a bisection on the count threshold,
+//              then the lowest indices among the ties at the threshold) and keeps only the rule: the k-th count
+//              c*_q and the last index taken at c*_q;
+//   count:     one block per query a counts its row again; pair {a, b} (b > a) is taken iff a chose b or b chose
+//              a, which both rules decide from the one symmetric count C[a][b];
+//   emit:      the same, writing the taken rows in increasing b at the row's offset (a scan of the counts).
+// Work per pass: sum over points of |cameras(p)|^2 shared-memory adds, reading every camera's point list once.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,43 +28,43 @@ bool is_device_ptr(const void *p);
 
 namespace {
 
-constexpr int32_t kMaxCams = 16384;
-constexpr uint32_t kFlag = 0x80000000u;
-constexpr int kSelThreads = 512;
+constexpr int32_t kMaxCams = 49152;     // one uint32 row per block: 192 KB of shared memory
+constexpr int kRowThreads = 512;
 
-__global__ void covis_count_kernel(const int64_t *__restrict__ point_off, const int32_t *__restrict__ point_cams,
-                                   int64_t n_points, int64_t nnz, int32_t n_cams, uint32_t *__restrict__ counts,
-                                   unsigned long long *__restrict__ bad)
+struct SelRule {
+    uint32_t cstar;    // counts above cstar are taken (0xffffffff: none)
+    int32_t tie_last;  // counts equal to cstar are taken for indices <= tie_last (-1: none)
+};
+
+// ---- transpose
+__global__ void obs_count_kernel(const int64_t *__restrict__ point_off, const int32_t *__restrict__ point_cams,
+                                 int64_t n_points, int64_t nnz, int32_t n_cams, int32_t *__restrict__ cam_cnt,
+                                 unsigned long long *__restrict__ bad)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_points; p += warps) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_points; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = point_off[p], o1 = point_off[p + 1];
-        if (o < 0 || o1 < o || o1 > nnz || o1 - o > INT32_MAX) {   // malformed offsets: counted, never read past
-            if (lane == 0) atomicAdd(bad, 1ull);
+        if (o < 0 || o1 < o || o1 > nnz) {   // malformed offsets: counted, never read past
+            atomicAdd(bad, 1ull);
             continue;
         }
-        const int d = (int)(o1 - o);
-        for (int i = 0; i < d - 1; ++i) {
-            const int ci = point_cams[o + i];
-            for (int j = i + 1 + lane; j < d; j += 32) {
-                const int cj = point_cams[o + j];
-                if (ci == cj || (unsigned)ci >= (unsigned)n_cams || (unsigned)cj >= (unsigned)n_cams) {
-                    atomicAdd(bad, 1ull);
-                    continue;
-                }
-                const int a = min(ci, cj), b = max(ci, cj);
-                atomicAdd(&counts[(int64_t)a * n_cams + b], 1u);
-            }
+        for (int64_t j = o; j < o1; ++j) {
+            const int c = point_cams[j];
+            if ((unsigned)c >= (unsigned)n_cams) atomicAdd(bad, 1ull);
+            else atomicAdd(&cam_cnt[c], 1);
         }
-        if (d == 1 && lane == 0 && (unsigned)point_cams[o] >= (unsigned)n_cams) atomicAdd(bad, 1ull);
     }
 }
 
-__device__ __forceinline__ uint32_t covis(const uint32_t *counts, int32_t n_cams, int q, int i)
+__global__ void obs_fill_kernel(const int64_t *__restrict__ point_off, const int32_t *__restrict__ point_cams,
+                                int64_t n_points, const int32_t *__restrict__ cam_off, int32_t *__restrict__ cursor,
+                                int32_t *__restrict__ cam_pts)
 {
-    const int a = min(q, i), b = max(q, i);
-    return counts[(int64_t)a * n_cams + b] & ~kFlag;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_points; p += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t j = point_off[p]; j < point_off[p + 1]; ++j) {
+            const int c = point_cams[j];
+            cam_pts[cam_off[c] + atomicAdd(&cursor[c], 1)] = (int32_t)p;
+        }
+    }
 }
 
 __device__ __forceinline__ int block_sum(int v, int *red)
@@ -75,95 +79,149 @@ __device__ __forceinline__ int block_sum(int v, int *red)
     return t;
 }
 
-// One block per query q: the top k of S_q (count > T) by count, ties to the lower index, flagged in the matrix.
-__global__ void __launch_bounds__(kSelThreads) select_kernel(uint32_t *__restrict__ counts, int32_t n_cams,
-                                                             int32_t threshold, int32_t top_k)
+__device__ __forceinline__ bool taken(const SelRule &r, uint32_t c, int i)
 {
-    __shared__ int red[kSelThreads / 32];
+    return c > r.cstar || (c == r.cstar && i <= r.tie_last);
+}
+
+// The co-visible counts of camera q with every camera, in shared memory (row[q] = 0).  Every point of q must list q
+// exactly once (else *bad); a camera listed twice by one point is caught by that camera's own row.
+__device__ void count_row(uint32_t *row, int q, int32_t n_cams, const int32_t *__restrict__ cam_off,
+                          const int32_t *__restrict__ cam_pts, const int64_t *__restrict__ point_off,
+                          const int32_t *__restrict__ point_cams, unsigned long long *bad)
+{
+    for (int i = threadIdx.x; i < n_cams; i += blockDim.x) row[i] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = cam_off[q] + warp; k < cam_off[q + 1]; k += nw) {
+        const int32_t p = cam_pts[k];
+        const int64_t o = point_off[p], o1 = point_off[p + 1];
+        int own = 0;
+        for (int64_t j = o + lane; j < o1; j += 32) {
+            const int c = point_cams[j];
+            if (c == q) ++own;
+            else atomicAdd(&row[c], 1u);
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) own += __shfl_xor_sync(0xffffffffu, own, s);
+        if (lane == 0 && own != 1) atomicAdd(bad, 1ull);
+    }
+    __syncthreads();
+}
+
+// kPhase 0: the selection rule of query q.  1: rows[q] = pairs {q, b > q} taken by either side.  2: write them.
+template <int kPhase>
+__global__ void __launch_bounds__(kRowThreads) row_kernel(
+    int32_t n_cams, const int32_t *__restrict__ cam_off, const int32_t *__restrict__ cam_pts,
+    const int64_t *__restrict__ point_off, const int32_t *__restrict__ point_cams, int32_t threshold, int32_t top_k,
+    SelRule *__restrict__ rules, int32_t *__restrict__ rows, const int64_t *__restrict__ off, int32_t *__restrict__ out,
+    unsigned long long *__restrict__ bad)
+{
+    extern __shared__ uint32_t row[];
+    __shared__ int red[kRowThreads / 32];
     __shared__ int scan_base;
     const int q = blockIdx.x;
-    // number of candidates with count >= c (c > threshold), and the largest count
-    auto count_ge = [&](uint32_t c) {
-        int n = 0;
-        for (int i = threadIdx.x; i < n_cams; i += blockDim.x)
-            n += (i != q && covis(counts, n_cams, q, i) >= c) ? 1 : 0;
-        return block_sum(n, red);
-    };
-    const uint32_t lo_c = (uint32_t)max(threshold, -1) + 1u;   // counts > T are >= T + 1 (T >= -1)
-    const int n_cand = count_ge(lo_c);
-    if (n_cand == 0 || top_k <= 0) return;
-    uint32_t cstar = lo_c;   // the k-th largest count (all candidates when there are at most k)
-    if (n_cand > top_k) {
-        uint32_t lo = lo_c, hi = 0x7fffffffu;   // invariant: count_ge(lo) >= top_k, count_ge(hi + 1) < top_k
-        int mx = 0;
-        for (int i = threadIdx.x; i < n_cams; i += blockDim.x)
-            if (i != q) mx = max(mx, (int)covis(counts, n_cams, q, i));
+    count_row(row, q, n_cams, cam_off, cam_pts, point_off, point_cams, bad);
+    const uint32_t lo_c = (uint32_t)(threshold + 1);   // counts > T are >= T + 1 (T >= -1)
+    if (kPhase == 0) {
+        auto count_ge = [&](uint32_t c) {
+            int n = 0;
+            for (int i = threadIdx.x; i < n_cams; i += blockDim.x) n += (i != q && row[i] >= c) ? 1 : 0;
+            return block_sum(n, red);
+        };
+        const int n_cand = count_ge(lo_c);
+        SelRule r{0xffffffffu, -1};
+        if (n_cand > 0 && top_k > 0) {
+            if (n_cand <= top_k) {
+                r.cstar = lo_c - 1u;   // every candidate: counts above T (T = -1: all, cstar wraps to 0xffffffff)
+                if (threshold < 0) { r.cstar = 0u; r.tie_last = n_cams; }
+            } else {
+                uint32_t lo = lo_c, hi = 0;   // invariant: count_ge(lo) >= top_k, count_ge(hi + 1) < top_k
+                int mx = 0;
+                for (int i = threadIdx.x; i < n_cams; i += blockDim.x)
+                    if (i != q) mx = max(mx, (int)row[i]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-        __syncthreads();
-        mx = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
-        hi = (uint32_t)mx;
-        while (lo < hi) {
-            const uint32_t mid = lo + (hi - lo + 1) / 2;
-            if (count_ge(mid) >= top_k) lo = mid;
-            else hi = mid - 1;
+                for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                __syncthreads();
+                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+                __syncthreads();
+                mx = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
+                hi = (uint32_t)mx;
+                while (lo < hi) {
+                    const uint32_t mid = lo + (hi - lo + 1) / 2;
+                    if (count_ge(mid) >= top_k) lo = mid;
+                    else hi = mid - 1;
+                }
+                const uint32_t cstar = lo;
+                const int need_tie = top_k - count_ge(cstar + 1);   // >= 1
+                // the need_tie-th camera (in index order) whose count equals cstar
+                __syncthreads();
+                if (threadIdx.x == 0) scan_base = 0;
+                __shared__ int tie_last;
+                if (threadIdx.x == 0) tie_last = -1;
+                __syncthreads();
+                for (int base = 0; base < n_cams; base += blockDim.x) {
+                    const int i = base + threadIdx.x;
+                    const bool tie = i < n_cams && i != q && row[i] == cstar;
+                    const unsigned bal = __ballot_sync(0xffffffffu, tie);
+                    const int wrank = __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+                    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = __popc(bal);
+                    __syncthreads();
+                    int before = scan_base;
+                    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) before += red[w];
+                    if (tie && before + wrank == need_tie - 1) tie_last = i;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        int t = 0;
+                        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+                        scan_base += t;
+                    }
+                    __syncthreads();
+                }
+                r.cstar = cstar;
+                r.tie_last = tie_last;
+            }
         }
-        cstar = lo;
+        if (threadIdx.x == 0) rules[q] = r;
+        return;
     }
-    // take every candidate above cstar, and the lowest-index ones at cstar up to k in total
-    const int above = n_cand > top_k ? count_ge(cstar + 1) : n_cand;
-    const int need_tie = n_cand > top_k ? top_k - above : 0;
+    // kPhase 1 / 2: pairs {q, b}, b > q, taken by q's rule or by b's (the count is symmetric)
+    const SelRule rq = rules[q];
     if (threadIdx.x == 0) scan_base = 0;
     __syncthreads();
-    for (int base = 0; base < n_cams; base += blockDim.x) {
-        const int i = base + threadIdx.x;
+    const int64_t w0 = kPhase == 2 ? off[q] : 0;
+    for (int base = q + 1; base < n_cams; base += blockDim.x) {
+        const int b = base + threadIdx.x;
+        bool t = false;
         uint32_t c = 0;
-        bool take = false, tie = false;
-        if (i < n_cams && i != q) {
-            c = covis(counts, n_cams, q, i);
-            if (n_cand <= top_k) take = c >= lo_c;
-            else if (c > cstar) take = true;
-            else tie = c == cstar;
+        if (b < n_cams) {
+            c = row[b];
+            t = c >= lo_c && (taken(rq, c, b) || taken(rules[b], c, q));
         }
-        // rank of this tie among the block's ties in index order
-        const unsigned bal = __ballot_sync(0xffffffffu, tie);
-        const int wrank = __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
-        __syncthreads();
+        const unsigned bal = __ballot_sync(0xffffffffu, t);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = __popc(bal);
         __syncthreads();
-        int before = scan_base;
-        for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) before += red[w];
-        if (tie && before + wrank < need_tie) take = true;
-        if (take) {
-            const int a = min(q, i), b = max(q, i);
-            atomicOr(&counts[(int64_t)a * n_cams + b], kFlag);
+        if (kPhase == 2 && t) {
+            int before = scan_base;
+            for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) before += red[w];
+            int32_t *o = out + 3 * (w0 + before + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u)));
+            o[0] = q;
+            o[1] = b;
+            o[2] = (int32_t)c;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            int t = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-            scan_base += t;
+            int s = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+            scan_base += s;
         }
         __syncthreads();
     }
+    if (kPhase == 1 && threadIdx.x == 0) rows[q] = scan_base;
 }
 
-// flagged pairs per row a (columns b > a), one warp per row
-__global__ void row_count_kernel(const uint32_t *__restrict__ counts, int32_t n_cams, int32_t *__restrict__ rows)
-{
-    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (a >= n_cams) return;
-    int n = 0;
-    for (int b = a + 1 + lane; b < n_cams; b += 32) n += (counts[(int64_t)a * n_cams + b] & kFlag) ? 1 : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if (lane == 0) rows[a] = n;
-}
-
-// exclusive scan of the row counts (one block; n_cams <= kMaxCams), off[n_cams] = total
+// exclusive scan of the row counts (one block), off[n_cams] = total
 __global__ void __launch_bounds__(1024) row_scan_kernel(const int32_t *__restrict__ rows, int32_t n_cams,
                                                         int64_t *__restrict__ off)
 {
@@ -186,27 +244,6 @@ __global__ void __launch_bounds__(1024) row_scan_kernel(const int32_t *__restric
         run += rows[i];
     }
     if (threadIdx.x == 1023) off[n_cams] = part[1023];
-}
-
-__global__ void emit_kernel(const uint32_t *__restrict__ counts, int32_t n_cams, const int64_t *__restrict__ off,
-                            int32_t *__restrict__ out)
-{
-    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (a >= n_cams) return;
-    int64_t w = off[a];
-    for (int b0 = a + 1; b0 < n_cams; b0 += 32) {
-        const int b = b0 + lane;
-        const uint32_t v = b < n_cams ? counts[(int64_t)a * n_cams + b] : 0u;
-        const bool f = (v & kFlag) != 0u;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (f) {
-            int32_t *r = out + 3 * (w + __popc(bal & ((1u << lane) - 1u)));
-            r[0] = a;
-            r[1] = b;
-            r[2] = (int32_t)(v & ~kFlag);
-        }
-        w += __popc(bal);
-    }
 }
 
 #define GM_CUDA_P(call)                                                                                \
@@ -248,48 +285,73 @@ gm_status gm_select_pairs(gm_ctx *ctx, int32_t n_cams, int64_t n_points, const i
             nnz = point_off[n_points];
         }
     }
-    if (nnz < 0) return fail(GM_ERR_INVALID, "gm_select_pairs: negative point offsets");
-    const size_t mat_b = align_up(sizeof(uint32_t) * (size_t)n_cams * n_cams, 256);
-    const size_t rows_b = align_up(sizeof(int32_t) * n_cams, 256), off_b = align_up(sizeof(int64_t) * (n_cams + 1), 256);
+    if (nnz < 0 || nnz > INT32_MAX - 1 || n_points > INT32_MAX - 1)
+        return fail(GM_ERR_INVALID, "gm_select_pairs: negative point offsets or more than 2^31 observations");
+    const size_t cnt_b = align_up(sizeof(int32_t) * (n_cams + 1), 256);   // counts, then offsets (scan), cursors
+    const size_t bs_b = align_up(sizeof(int32_t) * (n_cams / 1024 + 2), 256);
+    const size_t pts_b = align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1), 256);
+    const size_t rule_b = align_up(sizeof(SelRule) * n_cams, 256), rows_b = align_up(sizeof(int32_t) * n_cams, 256);
+    const size_t off_b = align_up(sizeof(int64_t) * (n_cams + 1), 256);
     const size_t in_b = dev_in ? 0 : align_up(sizeof(int64_t) * (n_points + 1), 256) + align_up(4 * (size_t)nnz + 4, 256);
-    gm_status st = ensure_dev(ctx, ctx->d_pairs, mat_b + rows_b + off_b + 256 + in_b);
+    gm_status st = ensure_dev(ctx, ctx->d_pairs, 3 * cnt_b + bs_b + pts_b + rule_b + rows_b + off_b + 256 + in_b);
     if (st != GM_OK) return st;
     char *w = static_cast<char *>(ctx->d_pairs.p);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(w);
-    int32_t *rows = reinterpret_cast<int32_t *>(w + mat_b);
-    int64_t *off = reinterpret_cast<int64_t *>(w + mat_b + rows_b);
-    unsigned long long *bad = reinterpret_cast<unsigned long long *>(w + mat_b + rows_b + off_b);
+    int32_t *cam_cnt = reinterpret_cast<int32_t *>(w);
+    int32_t *cam_off = reinterpret_cast<int32_t *>(w + cnt_b);
+    int32_t *cursor = reinterpret_cast<int32_t *>(w + 2 * cnt_b);
+    int32_t *bsum = reinterpret_cast<int32_t *>(w + 3 * cnt_b);
+    int32_t *cam_pts = reinterpret_cast<int32_t *>(w + 3 * cnt_b + bs_b);
+    SelRule *rules = reinterpret_cast<SelRule *>(w + 3 * cnt_b + bs_b + pts_b);
+    int32_t *rows = reinterpret_cast<int32_t *>(w + 3 * cnt_b + bs_b + pts_b + rule_b);
+    int64_t *off = reinterpret_cast<int64_t *>(w + 3 * cnt_b + bs_b + pts_b + rule_b + rows_b);
+    unsigned long long *bad = reinterpret_cast<unsigned long long *>(w + 3 * cnt_b + bs_b + pts_b + rule_b + rows_b + off_b);
     const int64_t *d_off = point_off;
     const int32_t *d_cams = point_cams;
     if (!dev_in && n_points > 0) {
-        char *in = w + mat_b + rows_b + off_b + 256;
+        char *in = reinterpret_cast<char *>(bad) + 256;
         GM_CUDA_P(cudaMemcpyAsync(in, point_off, sizeof(int64_t) * (n_points + 1), cudaMemcpyHostToDevice, s));
         char *cin = in + align_up(sizeof(int64_t) * (n_points + 1), 256);
         GM_CUDA_P(cudaMemcpyAsync(cin, point_cams, 4 * (size_t)nnz, cudaMemcpyHostToDevice, s));
         d_off = reinterpret_cast<const int64_t *>(in);
         d_cams = reinterpret_cast<const int32_t *>(cin);
     }
-    GM_CUDA_P(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)n_cams * n_cams, s));
+    GM_CUDA_P(cudaMemsetAsync(cam_cnt, 0, sizeof(int32_t) * (n_cams + 1), s));
+    GM_CUDA_P(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (n_cams + 1), s));
     GM_CUDA_P(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
+    const int grid = std::max(1, ctx->num_sms * 8);
     if (n_points > 0) {
-        const int blocks = std::max(1, std::min<int>((int)((n_points + 7) / 8), ctx->num_sms * 16));
-        covis_count_kernel<<<blocks, 256, 0, s>>>(d_off, d_cams, n_points, nnz, n_cams, counts, bad);
+        obs_count_kernel<<<grid, 256, 0, s>>>(d_off, d_cams, n_points, nnz, n_cams, cam_cnt, bad);
         GM_CUDA_P(cudaGetLastError());
     }
     unsigned long long h_bad = 0;
     GM_CUDA_P(cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, s));
     GM_CUDA_P(cudaStreamSynchronize(s));
     if (h_bad)
-        return fail(GM_ERR_INVALID,
-                    "gm_select_pairs: %llu entries repeat a camera within a point, exceed n_cams or have bad offsets",
-                    h_bad);
-    select_kernel<<<n_cams, kSelThreads, 0, s>>>(counts, n_cams, threshold, top_k);
-    GM_CUDA_P(cudaGetLastError());
-    row_count_kernel<<<(n_cams * 32 + 255) / 256, 256, 0, s>>>(counts, n_cams, rows);
+        return fail(GM_ERR_INVALID, "gm_select_pairs: %llu entries exceed n_cams or have bad offsets", h_bad);
+    GM_CUDA_P(launch_exclusive_scan(cam_cnt, n_cams, cam_off, bsum, s));
+    if (n_points > 0) obs_fill_kernel<<<grid, 256, 0, s>>>(d_off, d_cams, n_points, cam_off, cursor, cam_pts);
+    const size_t smem = sizeof(uint32_t) * (size_t)n_cams;
+    static const cudaError_t attr = [] {
+        cudaError_t e = cudaSuccess;
+        for (const void *f : {(const void *)row_kernel<0>, (const void *)row_kernel<1>, (const void *)row_kernel<2>})
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(uint32_t) * kMaxCams));
+        return e;
+    }();
+    GM_CUDA_P(attr);
+    row_kernel<0><<<n_cams, kRowThreads, smem, s>>>(n_cams, cam_off, cam_pts, d_off, d_cams, threshold, top_k, rules,
+                                                    rows, off, nullptr, bad);
+    row_kernel<1><<<n_cams, kRowThreads, smem, s>>>(n_cams, cam_off, cam_pts, d_off, d_cams, threshold, top_k, rules,
+                                                    rows, off, nullptr, bad);
     row_scan_kernel<<<1, 1024, 0, s>>>(rows, n_cams, off);
+    GM_CUDA_P(cudaGetLastError());
     int64_t total = 0;
     GM_CUDA_P(cudaMemcpyAsync(&total, off + n_cams, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_P(cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, s));
     GM_CUDA_P(cudaStreamSynchronize(s));
+    if (h_bad)
+        return fail(GM_ERR_INVALID, "gm_select_pairs: %llu points list one camera more than once", h_bad);
     *n_written = total;
     if (total > cap)
         return fail(GM_ERR_NOMEM, "gm_select_pairs: %lld pairs exceed cap %lld", (long long)total, (long long)cap);
@@ -300,7 +362,8 @@ gm_status gm_select_pairs(gm_ctx *ctx, int32_t n_cams, int64_t n_points, const i
             if ((st = ensure_dev(ctx, ctx->d_pairs_out, sizeof(int32_t) * 3 * (size_t)total)) != GM_OK) return st;
             dst = static_cast<int32_t *>(ctx->d_pairs_out.p);
         }
-        emit_kernel<<<(n_cams * 32 + 255) / 256, 256, 0, s>>>(counts, n_cams, off, dst);
+        row_kernel<2><<<n_cams, kRowThreads, smem, s>>>(n_cams, cam_off, cam_pts, d_off, d_cams, threshold, top_k,
+                                                        rules, rows, off, dst, bad);
         GM_CUDA_P(cudaGetLastError());
         if (!dev_out) GM_CUDA_P(cudaMemcpyAsync(pairs, dst, sizeof(int32_t) * 3 * (size_t)total, cudaMemcpyDeviceToHost, s));
     }

@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
         r.qoff = P.qoff;
         gdesc[item] = r;
         if (overflow) atomicAdd(&ctr->overflow, 1ull);
+        else if (!full && total > kTcStagedPositions) atomicAdd(&ctr->unstaged, 1ull);
         atomicAdd(&ctr->examined, (unsigned long long)total * kG);
     }
     if (full || overflow || total == 0) return;

@@ -1,4 +1,8 @@
-// gm_triangulate.cu -- gm_triangulate: linear least-squares triangulation of feature tracks (Sec. 6.2, end).
+// gm_triangulate.cu -- linear least-squares triangulation of feature tracks (Sec. 6.3).
+//
+// gm_triangulate: the merged tracks (connected components of all matches, gm_merge_tracks).
+// gm_triangulate_image_tracks: the per-image tracks that Sec. 6.3 triangulates before merging -- every query
+// image's features with their matches in all its candidate images.
 //
 // Nodes are numbered image-major over the caller's image list (node = first node of image k + feature index) and
 // labelled by their component (gm_merge_tracks).  Every component with at least two nodes is a track; tracks are
@@ -15,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <unordered_map>
 #include <vector>
 
 #include "gm_ctx.h"
@@ -99,24 +104,139 @@ __global__ void tri_accum_kernel(const int64_t *__restrict__ labels, const int32
     }
 }
 
+// Cramer's rule on the normal equations a = (M00 M01 M02 M11 M12 M22, b0 b1 b2); NaN if singular.
+__device__ __forceinline__ void tri_solve(const double *a, double *o)
+{
+    const double m00 = a[0], m01 = a[1], m02 = a[2], m11 = a[3], m12 = a[4], m22 = a[5];
+    const double b0 = a[6], b1 = a[7], b2 = a[8];
+    const double c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
+    const double det = m00 * c00 + m01 * c01 + m02 * c02;
+    if (det == 0.0 || !isfinite(det)) {
+        o[0] = o[1] = o[2] = nan("");
+        return;
+    }
+    const double c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
+    const double id = 1.0 / det;
+    o[0] = (c00 * b0 + c01 * b1 + c02 * b2) * id;
+    o[1] = (c01 * b0 + c11 * b1 + c12 * b2) * id;
+    o[2] = (c02 * b0 + c12 * b1 + c22 * b2) * id;
+}
+
 __global__ void tri_solve_kernel(const double *__restrict__ acc, int64_t n_tracks, double *__restrict__ X)
 {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tracks; t += (int64_t)gridDim.x * blockDim.x) {
-        const double *a = acc + 9 * t;
-        const double m00 = a[0], m01 = a[1], m02 = a[2], m11 = a[3], m12 = a[4], m22 = a[5];
-        const double b0 = a[6], b1 = a[7], b2 = a[8];
-        const double c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
-        const double det = m00 * c00 + m01 * c01 + m02 * c02;
-        double *o = X + 3 * t;
-        if (det == 0.0 || !isfinite(det)) {
-            o[0] = o[1] = o[2] = nan("");
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tracks; t += (int64_t)gridDim.x * blockDim.x)
+        tri_solve(acc + 9 * t, X + 3 * t);
+}
+
+// Adds the observation (x, y) of camera Pk (3 x 4, row-major) to the normal equations a: the rows x P3 - P1 and
+// y P3 - P2 of A = [A3 | a4] into A3^T A3 (six distinct entries) and -A3^T a4.
+__device__ __forceinline__ void tri_add(double *a, const double *__restrict__ Pk, double x, double y)
+{
+    double r1[4], r2[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        r1[c] = x * Pk[8 + c] - Pk[c];
+        r2[c] = y * Pk[8 + c] - Pk[4 + c];
+    }
+    a[0] += r1[0] * r1[0] + r2[0] * r2[0];
+    a[1] += r1[0] * r1[1] + r2[0] * r2[1];
+    a[2] += r1[0] * r1[2] + r2[0] * r2[2];
+    a[3] += r1[1] * r1[1] + r2[1] * r2[1];
+    a[4] += r1[1] * r1[2] + r2[1] * r2[2];
+    a[5] += r1[2] * r1[2] + r2[2] * r2[2];
+    a[6] -= r1[0] * r1[3] + r2[0] * r2[3];
+    a[7] -= r1[1] * r1[3] + r2[1] * r2[3];
+    a[8] -= r1[2] * r1[3] + r2[2] * r2[3];
+}
+
+// ---- per-image tracks
+// Pairs of the caller's list: pair p's rows are matches[off[p] .. off[p+1]), image indices ka (query), kb.
+struct TrkPair {
+    int32_t ka, kb;
+};
+
+// Row m of the match list belongs to pair p with off[p] <= m < off[p+1] (largest such p).
+__device__ __forceinline__ int pair_of_row(const int64_t *__restrict__ off, int n_pairs, int64_t m)
+{
+    int lo = 0, hi = n_pairs;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= m) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Every row names features inside its images, and i increases strictly within a pair (one match per query).
+__global__ void trk_check_kernel(const int2 *__restrict__ rows, int64_t n_rows, const int64_t *__restrict__ off,
+                                 int n_pairs, const TrkPair *__restrict__ pairs, const TriImage *__restrict__ imgs,
+                                 unsigned long long *bad)
+{
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n_rows; m += (int64_t)gridDim.x * blockDim.x) {
+        const int p = pair_of_row(off, n_pairs, m);
+        const int2 r = rows[m];
+        bool ok = r.x >= 0 && r.x < imgs[pairs[p].ka].n && r.y >= 0 && r.y < imgs[pairs[p].kb].n;
+        if (m + 1 < off[p + 1]) ok = ok && rows[m + 1].x > r.x;
+        if (!ok) atomicAdd(bad, 1ull);
+    }
+}
+
+// The row of pair p whose query is f, or -1 (binary search over the pair's rows, sorted by query).
+__device__ __forceinline__ int64_t find_row(const int2 *__restrict__ rows, int64_t lo, int64_t hi, int f)
+{
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int x = __ldg(&rows[mid].x);
+        if (x == f) return mid;
+        if (x < f) lo = mid + 1;
+        else hi = mid;
+    }
+    return -1;
+}
+
+// Pass 1 (count = false): flag[v] = 1 if node v matched in any pair of its image.  Pass 2 (count = true): for every
+// flagged node, the normal equations of its track -- its own observation, then one per pair of its image (in the
+// caller's order) in which it matched -- solved into the track's slot track_of[v].
+template <bool kSolve>
+__global__ void trk_node_kernel(int64_t n_nodes, const TriImage *__restrict__ imgs, int n_images,
+                                const int32_t *__restrict__ img_poff, const int32_t *__restrict__ img_pairs,
+                                const TrkPair *__restrict__ pairs, const int64_t *__restrict__ off,
+                                const int2 *__restrict__ rows, const double *__restrict__ P, int32_t *__restrict__ flag,
+                                const int32_t *__restrict__ track_of, double *__restrict__ X,
+                                int64_t *__restrict__ nodes, int32_t *__restrict__ n_views)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_nodes; v += (int64_t)gridDim.x * blockDim.x) {
+        const int k = find_image(imgs, n_images, v);
+        const int f = (int)(v - imgs[k].base);
+        if (!kSolve) {
+            int found = 0;
+            for (int t = img_poff[k]; t < img_poff[k + 1] && !found; ++t) {
+                const int p = img_pairs[t];
+                found = find_row(rows, off[p], off[p + 1], f) >= 0;
+            }
+            flag[v] = found;
             continue;
         }
-        const double c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
-        const double id = 1.0 / det;
-        o[0] = (c00 * b0 + c01 * b1 + c02 * b2) * id;
-        o[1] = (c01 * b0 + c11 * b1 + c12 * b2) * id;
-        o[2] = (c02 * b0 + c12 * b1 + c22 * b2) * id;
+        if (track_of[v + 1] == track_of[v]) continue;   // no match: no track
+        double a[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        const TriImage &Q = imgs[k];
+        const float2 q = Q.xy[Q.inv_perm[f]];
+        tri_add(a, P + 12 * (int64_t)k, (double)q.x, (double)q.y);
+        int nv = 1;
+        for (int t = img_poff[k]; t < img_poff[k + 1]; ++t) {
+            const int p = img_pairs[t];
+            const int64_t m = find_row(rows, off[p], off[p + 1], f);
+            if (m < 0) continue;
+            const int kb = pairs[p].kb;
+            const TriImage &B = imgs[kb];
+            const float2 b = B.xy[B.inv_perm[__ldg(&rows[m].y)]];
+            tri_add(a, P + 12 * (int64_t)kb, (double)b.x, (double)b.y);
+            ++nv;
+        }
+        const int32_t tr = track_of[v];
+        tri_solve(a, X + 3 * (int64_t)tr);
+        nodes[tr] = v;
+        n_views[tr] = nv;
     }
 }
 
@@ -222,6 +342,156 @@ gm_status gm_triangulate(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids
     if (!dev_o) {
         GM_CUDA_R(cudaMemcpyAsync(X, dX, sizeof(double) * 3 * nt, cudaMemcpyDeviceToHost, s));
         GM_CUDA_R(cudaMemcpyAsync(roots, dR, sizeof(int64_t) * nt, cudaMemcpyDeviceToHost, s));
+        GM_CUDA_R(cudaMemcpyAsync(n_views, dV, sizeof(int32_t) * nt, cudaMemcpyDeviceToHost, s));
+    }
+    GM_CUDA_R(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids, const double *P,
+                                      int32_t n_pairs, const int32_t *pair_images, const int64_t *pair_off,
+                                      const int32_t *matches, int64_t cap, double *X, int64_t *nodes,
+                                      int32_t *n_views, int64_t *n_tracks)
+{
+    gm::NvtxRange nvtx_("gm_triangulate_image_tracks");
+    using namespace gm;
+    if (!ctx || n_images < 0 || (n_images > 0 && (!image_ids || !P)) || n_pairs < 0 ||
+        (n_pairs > 0 && (!pair_images || !pair_off)) || cap < 0 || (cap > 0 && (!X || !nodes || !n_views)) ||
+        !n_tracks)
+        return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    GM_CUDA_R(cudaSetDevice(ctx->device));
+    *n_tracks = 0;
+    std::vector<TriImage> imgs(n_images);
+    std::unordered_map<int32_t, int32_t> index;
+    int64_t total = 0;
+    for (int32_t k = 0; k < n_images; ++k) {
+        auto it = ctx->images.find(image_ids[k]);
+        if (image_ids[k] < 0 || it == ctx->images.end())
+            return fail(GM_ERR_NOT_FOUND, "gm_triangulate_image_tracks: image %d not registered", image_ids[k]);
+        if (!index.emplace(image_ids[k], k).second)
+            return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: image %d listed twice", image_ids[k]);
+        const ImageDev &d = it->second->dev;
+        imgs[k] = TriImage{d.xy, d.inv_perm, total, d.n, 0};
+        total += d.n;
+    }
+    if (total > INT32_MAX - 1) return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: too many nodes");
+    // the pairs: image indices, offsets on the host (validated), and every image's pairs as the query side
+    std::vector<int64_t> off(n_pairs + 1, 0);
+    cudaStream_t s = ctx->ws.stream;
+    if (n_pairs > 0) {
+        GM_CUDA_R(cudaMemcpyAsync(off.data(), pair_off, sizeof(int64_t) * (n_pairs + 1), cudaMemcpyDefault, s));
+        GM_CUDA_R(cudaStreamSynchronize(s));
+    }
+    if (off[0] != 0) return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: pair_off[0] must be 0");
+    std::vector<TrkPair> pairs(n_pairs);
+    std::vector<int64_t> keys(n_pairs);
+    std::vector<int32_t> img_poff(n_images + 1, 0), img_pairs(n_pairs);
+    for (int32_t p = 0; p < n_pairs; ++p) {
+        auto ia = index.find(pair_images[2 * p]), ib = index.find(pair_images[2 * p + 1]);
+        if (ia == index.end() || ib == index.end())
+            return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: pair %d names an image outside image_ids", p);
+        if (ia->second == ib->second)
+            return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: pair %d matches an image with itself", p);
+        if (off[p + 1] < off[p])
+            return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: pair_off decreases at pair %d", p);
+        pairs[p] = TrkPair{ia->second, ib->second};
+        keys[p] = (int64_t)ia->second * n_images + ib->second;
+        ++img_poff[ia->second + 1];
+    }
+    std::vector<int64_t> sorted_keys(keys);
+    std::sort(sorted_keys.begin(), sorted_keys.end());
+    if (std::adjacent_find(sorted_keys.begin(), sorted_keys.end()) != sorted_keys.end())
+        return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: an ordered pair is listed twice");
+    for (int32_t k = 0; k < n_images; ++k) img_poff[k + 1] += img_poff[k];
+    {
+        std::vector<int32_t> fill(img_poff.begin(), img_poff.end() - 1);
+        for (int32_t p = 0; p < n_pairs; ++p) img_pairs[fill[pairs[p].ka]++] = p;   // the caller's order
+    }
+    const int64_t M = off[n_pairs];
+    if (M > 0 && !matches) return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: null matches");
+    if (total == 0 || M == 0) return GM_OK;
+    const bool dev_m = is_device_ptr(matches), dev_p = is_device_ptr(P);
+    const size_t N = (size_t)total;
+    const size_t img_b = align_up(sizeof(TriImage) * std::max(n_images, 1), 256);
+    const size_t p_b = align_up(sizeof(double) * 12 * std::max(n_images, 1), 256);
+    const size_t off_b = align_up(sizeof(int64_t) * (n_pairs + 1), 256);
+    const size_t pr_b = align_up(sizeof(TrkPair) * std::max(n_pairs, 1), 256);
+    const size_t ip_b = align_up(sizeof(int32_t) * (n_images + 1), 256);
+    const size_t il_b = align_up(sizeof(int32_t) * std::max(n_pairs, 1), 256);
+    const size_t m_b = dev_m ? 0 : align_up(sizeof(int32_t) * 2 * (size_t)M, 256);
+    const size_t fl_b = align_up(4 * N, 256), tr_b = align_up(4 * (N + 1), 256);
+    const size_t bs_b = align_up(4 * (N / 1024 + 2), 256);
+    gm_status st = ensure_dev(ctx, ctx->d_tri,
+                              img_b + p_b + off_b + pr_b + ip_b + il_b + m_b + fl_b + tr_b + bs_b + 256);
+    if (st != GM_OK) return st;
+    char *w = static_cast<char *>(ctx->d_tri.p);
+    TriImage *d_imgs = reinterpret_cast<TriImage *>(w);
+    w += img_b;
+    double *d_P = reinterpret_cast<double *>(w);
+    w += p_b;
+    int64_t *d_off = reinterpret_cast<int64_t *>(w);
+    w += off_b;
+    TrkPair *d_pairs = reinterpret_cast<TrkPair *>(w);
+    w += pr_b;
+    int32_t *d_ipoff = reinterpret_cast<int32_t *>(w);
+    w += ip_b;
+    int32_t *d_ipairs = reinterpret_cast<int32_t *>(w);
+    w += il_b;
+    const int2 *d_rows = reinterpret_cast<const int2 *>(matches);
+    if (!dev_m) {
+        GM_CUDA_R(cudaMemcpyAsync(w, matches, sizeof(int32_t) * 2 * (size_t)M, cudaMemcpyHostToDevice, s));
+        d_rows = reinterpret_cast<const int2 *>(w);
+        w += m_b;
+    } else if (reinterpret_cast<uintptr_t>(matches) % 8 != 0) {
+        return fail(GM_ERR_INVALID, "gm_triangulate_image_tracks: device matches must be 8-byte aligned");
+    }
+    int32_t *flag = reinterpret_cast<int32_t *>(w);
+    int32_t *track_of = reinterpret_cast<int32_t *>(w + fl_b);
+    int32_t *bsum = reinterpret_cast<int32_t *>(w + fl_b + tr_b);
+    unsigned long long *bad = reinterpret_cast<unsigned long long *>(w + fl_b + tr_b + bs_b);
+    GM_CUDA_R(cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(TriImage) * n_images, cudaMemcpyHostToDevice, s));
+    GM_CUDA_R(cudaMemcpyAsync(d_P, P, sizeof(double) * 12 * n_images,
+                              dev_p ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    GM_CUDA_R(cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * (n_pairs + 1), cudaMemcpyHostToDevice, s));
+    GM_CUDA_R(cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(TrkPair) * n_pairs, cudaMemcpyHostToDevice, s));
+    GM_CUDA_R(cudaMemcpyAsync(d_ipoff, img_poff.data(), sizeof(int32_t) * (n_images + 1), cudaMemcpyHostToDevice, s));
+    GM_CUDA_R(cudaMemcpyAsync(d_ipairs, img_pairs.data(), sizeof(int32_t) * n_pairs, cudaMemcpyHostToDevice, s));
+    GM_CUDA_R(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
+    const int grid = std::max(1, ctx->num_sms * 8);
+    trk_check_kernel<<<grid, 256, 0, s>>>(d_rows, M, d_off, n_pairs, d_pairs, d_imgs, bad);
+    unsigned long long h_bad = 0;
+    GM_CUDA_R(cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_R(cudaStreamSynchronize(s));
+    if (h_bad)
+        return fail(GM_ERR_INVALID,
+                    "gm_triangulate_image_tracks: %llu match rows outside their images or not sorted by query", h_bad);
+    trk_node_kernel<false><<<grid, 256, 0, s>>>(total, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_off, d_rows,
+                                                d_P, flag, nullptr, nullptr, nullptr, nullptr);
+    GM_CUDA_R(launch_exclusive_scan(flag, (int32_t)total, track_of, bsum, s));
+    int32_t nt = 0;
+    GM_CUDA_R(cudaMemcpyAsync(&nt, track_of + total, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_R(cudaStreamSynchronize(s));
+    *n_tracks = nt;
+    if (nt > cap) return fail(GM_ERR_NOMEM, "gm_triangulate_image_tracks: %d tracks exceed cap %lld", nt, (long long)cap);
+    if (nt == 0) return GM_OK;
+    const bool dev_o = is_device_ptr(X);
+    if (is_device_ptr(nodes) != dev_o || is_device_ptr(n_views) != dev_o)
+        return fail(GM_ERR_INVALID,
+                    "gm_triangulate_image_tracks: X, nodes and n_views must all be host or all device memory");
+    const size_t x_b = align_up(sizeof(double) * 3 * nt, 256);
+    const size_t r_b = align_up(sizeof(int64_t) * nt, 256), v_b = align_up(sizeof(int32_t) * nt, 256);
+    if (!dev_o && (st = ensure_dev(ctx, ctx->d_tri_out, x_b + r_b + v_b)) != GM_OK) return st;
+    char *o = dev_o ? nullptr : static_cast<char *>(ctx->d_tri_out.p);
+    double *dX = dev_o ? X : reinterpret_cast<double *>(o);
+    int64_t *dN = dev_o ? nodes : reinterpret_cast<int64_t *>(o + x_b);
+    int32_t *dV = dev_o ? n_views : reinterpret_cast<int32_t *>(o + x_b + r_b);
+    trk_node_kernel<true><<<grid, 256, 0, s>>>(total, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_off, d_rows, d_P,
+                                               nullptr, track_of, dX, dN, dV);
+    GM_CUDA_R(cudaGetLastError());
+    if (!dev_o) {
+        GM_CUDA_R(cudaMemcpyAsync(X, dX, sizeof(double) * 3 * nt, cudaMemcpyDeviceToHost, s));
+        GM_CUDA_R(cudaMemcpyAsync(nodes, dN, sizeof(int64_t) * nt, cudaMemcpyDeviceToHost, s));
         GM_CUDA_R(cudaMemcpyAsync(n_views, dV, sizeof(int32_t) * nt, cudaMemcpyDeviceToHost, s));
     }
     GM_CUDA_R(cudaStreamSynchronize(s));

@@ -44,7 +44,9 @@ class GmPair(ctypes.Structure):
 class GmStats(ctypes.Structure):
     _fields_ = [("n_pairs", c_i64), ("n_queries", c_i64), ("n_candidates", c_i64), ("n_examined", c_i64),
                 ("n_redecided", c_i64), ("n_matches", c_i64), ("ms_device", c_f32), ("ms_match", c_f32),
-                ("path_used", c_i32), ("kernel_launches", c_i32), ("n_device_errors", c_i64)]
+                ("path_used", c_i32), ("kernel_launches", c_i32), ("n_device_errors", c_i64),
+                ("n_stream_reruns", c_i64), ("n_unstaged_groups", c_i64), ("cta_finish_spread", c_f32),
+                ("reserved0", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -117,6 +119,8 @@ _SIGNATURES = {
     "gm_match_coarse": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), ctypes.POINTER(GmCoarseOpts), c_p, c_p, c_i64,
                                 ctypes.POINTER(c_i64), c_p]),
     "gm_triangulate": (c_i32, [c_p, c_i32, c_p, c_p, c_i64, c_p, c_i64, c_p, c_p, c_p, ctypes.POINTER(c_i64)]),
+    "gm_triangulate_image_tracks": (c_i32, [c_p, c_i32, c_p, c_p, c_i32, c_p, c_p, c_p, c_i64, c_p, c_p, c_p,
+                                            ctypes.POINTER(c_i64)]),
     "gm_select_pairs": (c_i32, [c_p, c_i32, c_i64, c_p, c_p, c_i32, c_i32, c_p, c_i64, ctypes.POINTER(c_i64)]),
     "gm_autotune": (c_i32, [c_p, c_i32, ctypes.POINTER(GmPair), c_i32, ctypes.POINTER(GmTuneResult)]),
     "gm_get_stats": (c_i32, [c_p, ctypes.POINTER(GmStats)]),
@@ -326,6 +330,30 @@ def gm_triangulate(ctx, image_ids, P, labels, X, roots, n_views, cap: int) -> in
         raise err
     _check(st, ctx)
     del k1, k2, k3, k4, k5
+    return nt.value
+
+
+def gm_triangulate_image_tracks(ctx, image_ids, P, pair_images, pair_off, matches, X, nodes, n_views, cap: int) -> int:
+    """image_ids int32 [K] (host), P float64 [K, 3, 4], pair_images int32 [n_pairs, 2] (host), pair_off int64
+    [n_pairs + 1] and matches int32 [M, 2] as gm_match_pairs wrote them, X float64 [cap, 3], nodes int64 [cap],
+    n_views int32 [cap] (numpy or torch CUDA); returns the number of tracks (GeomatchError.required on NOMEM)."""
+    ids = np.ascontiguousarray(image_ids, np.int32)
+    ab = np.ascontiguousarray(pair_images, np.int32).reshape(-1, 2)
+    pp, _, k1 = _ptr(P)
+    po, _, k2 = _ptr(pair_off)
+    pm, _, k3 = _ptr(matches)
+    px, _, k4 = _ptr(X)
+    pn, _, k5 = _ptr(nodes)
+    pv, _, k6 = _ptr(n_views)
+    nt = c_i64(0)
+    st = load_library().gm_triangulate_image_tracks(ctx, int(ids.shape[0]), ids.ctypes.data, pp, int(ab.shape[0]),
+                                                    ab.ctypes.data, po, pm, cap, px, pn, pv, ctypes.byref(nt))
+    if st == GM_ERR_NOMEM and nt.value > cap:
+        err = GeomatchError(st, load_library().gm_last_error(ctx).decode())
+        err.required = nt.value
+        raise err
+    _check(st, ctx)
+    del k1, k2, k3, k4, k5, k6
     return nt.value
 
 
@@ -675,6 +703,24 @@ class Context:
             try:
                 n = gm_triangulate(self.h, image_ids, P, labels, X, roots, nv, cap)
                 return X[:n], roots[:n], nv[:n]
+            except GeomatchError as e:
+                if e.status != GM_ERR_NOMEM or not hasattr(e, "required"):
+                    raise
+                cap = max(e.required, 1)
+
+    def triangulate_image_tracks(self, image_ids, P, pair_images, pair_off, matches):
+        """Per-image tracks of the matches of a gm_match_pairs call (pair_images [n_pairs, 2] image ids) as
+        (X float64 [T, 3], nodes int64 [T], n_views int32 [T]); P float64 [K, 3, 4]."""
+        P = np.ascontiguousarray(P, np.float64).reshape(-1, 12)
+        cap = 1024
+        while True:
+            X = np.empty((cap, 3), np.float64)
+            nodes = np.empty(cap, np.int64)
+            nv = np.empty(cap, np.int32)
+            try:
+                n = gm_triangulate_image_tracks(self.h, image_ids, P, pair_images, pair_off, matches, X, nodes, nv,
+                                                cap)
+                return X[:n], nodes[:n], nv[:n]
             except GeomatchError as e:
                 if e.status != GM_ERR_NOMEM or not hasattr(e, "required"):
                     raise

@@ -387,3 +387,24 @@ def visibility(scene):
     _, start = np.unique(pts, return_index=True)
     point_off = np.append(start, pts.size).astype(np.int64)
     return point_off, cams.astype(np.int32), n_cams
+
+
+def path_visibility(n_cams: int, n_points: int, seed: int = SEED_BASE + 6):
+    """Point -> camera CSR of a long image sequence (the coarse model's visibility of a street or a corridor, Sec.
+    6.1): every point is seen by a run of 2-14 consecutive cameras from a random start (wrapping at the end), and 2 %
+    of the points also by two cameras half the sequence away.  Returns (point_off int64 [P+1], point_cams int32,
+    n_cams); each point's cameras are distinct and ascending."""
+    rng = np.random.default_rng(seed)
+    start = rng.integers(0, n_cams, n_points)
+    deg = rng.integers(2, 15, n_points)
+    far = rng.random(n_points) < 0.02
+    cols = np.arange(16)
+    cam = (start[:, None] + cols[None, :14]) % n_cams
+    cam = np.concatenate([cam, (start[:, None] + n_cams // 2 + cols[None, :2]) % n_cams], 1)
+    keep = np.concatenate([cols[None, :14] < deg[:, None], np.repeat(far[:, None], 2, 1)], 1)
+    cam = np.where(keep, cam, np.iinfo(np.int64).max)
+    cam.sort(axis=1)
+    n = keep.sum(1)
+    off = np.zeros(n_points + 1, np.int64)
+    off[1:] = np.cumsum(n)
+    return off, cam[cam != np.iinfo(np.int64).max].astype(np.int32), n_cams

@@ -183,13 +183,17 @@ int shrink()   // the engine's capacity of the moment bounds every batch; a larg
     const int n = 300;
     std::vector<std::thread> th;
     std::atomic<int> bad{0};
-    for (int w = 0; w < 2; ++w)
-        th.emplace_back([&, w] {
-            for (int k = 0; k < n / 2; ++k) {
+    for (int w = 0; w < 4; ++w)
+        th.emplace_back([&, w] {   // every thread queues all its requests first, so batches can form
+            std::vector<std::pair<uint64_t, gm_pair>> mine;
+            for (int k = 0; k < n / 4; ++k) {
                 const gm_pair p = make(w * 1000 + k, k % 50);
                 uint64_t t = 0;
-                if (S.submit(p, &t) != GM_OK || !check_rows(S, t, p)) ++bad;
+                if (S.submit(p, &t) != GM_OK) ++bad;
+                else mine.emplace_back(t, p);
             }
+            for (auto &tp : mine)
+                if (!check_rows(S, tp.first, tp.second)) ++bad;
         });
     for (auto &t : th) t.join();
     const gm::SchedStats st = S.stats();

@@ -1,6 +1,6 @@
-"""Host logic of bench.py that needs no GPU: the committed ncu summary of the dominant kernel still matches the
-kernel's sources (so the bench reports its DRAM traffic), the clock-record parsing that rejects throttled runs, and
-the single-rank reductions."""
+"""Host logic of bench.py that needs no GPU: the DRAM traffic taken from an ncu summary only while the kernel's
+sources hash to the captured ones, the clock-record parsing that rejects throttled runs, and the single-rank
+reductions."""
 import os
 
 import bench
@@ -8,9 +8,17 @@ import bench
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_dominant_kernel_profile_matches_sources():
-    traffic = bench._profiled_traffic("match_tc_kernel", "gm_match_tc.cu", bench.WORKLOAD)
-    assert traffic is not None and traffic > 1e8
+def test_profiled_traffic_follows_the_kernel_sources(tmp_path):
+    """A summary whose source hash is the kernel's current one gives its DRAM bytes; any other hash gives None (the
+    counters were taken on another kernel), and so does a missing summary."""
+    os.makedirs(tmp_path / "profiles")
+    name = "match_tc_kernel_some_workload"
+    cur = bench._kernel_source_hash("gm_match_tc.cu")
+    for sha, want in ((cur, 5.5e8), ("0" * 64, None)):
+        with open(tmp_path / "profiles" / f"{name}.txt", "w") as fh:
+            fh.write(f"kernel: match_tc_kernel\nsource_sha256: {sha}\ndram_bytes_per_launch: 5.5e8\n")
+        assert bench._profiled_traffic("match_tc_kernel", "gm_match_tc.cu", "some_workload", root=str(tmp_path)) == want
+    assert bench._profiled_traffic("match_tc_kernel", "gm_match_tc.cu", "absent", root=str(tmp_path)) is None
 
 
 def test_profiles_name_their_commands():

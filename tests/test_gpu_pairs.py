@@ -1,4 +1,5 @@
-"""gm_select_pairs (candidate image pairs, Sec. 6.1) against the oracle, through the C ABI: identical rows."""
+"""gm_select_pairs (candidate image pairs, Sec. 6.1) against the oracle, through the C ABI: identical rows, from a
+handful of cameras to 6000 (street-like visibility: every point seen by a run of neighbouring cameras)."""
 import numpy as np
 import pytest
 
@@ -65,5 +66,15 @@ def test_device_inputs_outputs_and_errors(gm):
             ctx.select_pairs(30, off, bad, 1, 4)
         assert e.value.status == gm.GM_ERR_INVALID
         with pytest.raises(gm.GeomatchError) as e:
-            ctx.select_pairs(16385, off, cams, 1, 4)
+            ctx.select_pairs(49153, off, cams, 1, 4)
         assert e.value.status == gm.GM_ERR_INVALID
+
+
+@pytest.mark.parametrize("T,k", [(8, 600), (20, 3), (-1, 2)])
+def test_six_thousand_cameras(gm, T, k):
+    off, cams, _ = scenes.path_visibility(6000, 300000, seed=6000 + k)
+    with gm.Context(device=0) as ctx:
+        got = ctx.select_pairs(6000, off, cams, T, k)
+    want = op.select_pairs(6000, off, cams, T, k)
+    assert len(want) >= 5000   # every query chose at least its neighbours
+    np.testing.assert_array_equal(got, want)
