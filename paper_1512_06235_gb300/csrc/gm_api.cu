@@ -270,6 +270,13 @@ gm_status encode_maps(const ImageDev &dev, TmaMaps &maps)
             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA) != CUDA_SUCCESS)
         return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled failed (records)");
+    const cuuint64_t xdims[2] = {16, (cuuint64_t)dev.n};
+    const cuuint64_t xstrides[1] = {32};
+    const cuuint32_t xbox[2] = {16, 64};
+    if (enc(&maps.ext_tile, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<uint16_t *>(dev.ext_h), xdims, xstrides, xbox,
+            estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail(GM_ERR_CUDA, "cuTensorMapEncodeTiled failed (norm rows)");
     return GM_OK;
 }
 
@@ -319,6 +326,9 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     }
     // the tcgen05 kernel's run table holds match_tc_max_grid_lines() grid lines
     if (path == GM_PATH_TC && max_lines > match_tc_max_grid_lines()) path = GM_PATH_MMA;
+    // every pair with d = inf: the whole-image specialisation of the tcgen05 kernel
+    bool whole_image = P > 0;
+    for (const PairDev &pd : ws.pd) whole_image = whole_image && std::isinf(pd.d);
     const int mt = ctx->mma_mt;
     const int qpi = path == GM_PATH_SIMT ? kQueriesPerItem : path == GM_PATH_TC ? kTcQueriesPerItem : 16 * mt;
 
@@ -373,7 +383,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
             return launch_match_tc(static_cast<const TmaMaps *>(ctx->d_maps.p),
                                    static_cast<const GroupDesc *>(ws.d_grec.p),
                                    static_cast<const int32_t *>(ws.d_grows.p), static_cast<const int32_t *>(ws.d_stream.p),
-                                   i0, i1, gsz > 0 ? gsz : ctx->num_sms, match_j, ctr, cta_time, s);
+                                   i0, i1, gsz > 0 ? gsz : ctx->num_sms, match_j, ctr, cta_time, whole_image, s);
         return launch_match_mma(mt, imgs, d_proc, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
     };
 
@@ -645,11 +655,11 @@ namespace gm {
 namespace {
 
 // Layout of one resident image block: xy, perm, inv_perm, desc, norm, col_off, xy_r, idx_r, row_off, desc_h, scale,
-// norm256, rec (256-byte aligned arrays).
+// norm256, rec, ext_h (256-byte aligned arrays).
 struct ImageLayout {
     int sh = 0, gx = 0, gy = 0;
     int64_t m = 0;
-    size_t offs[13] = {};
+    size_t offs[14] = {};
     size_t tot = 0;
 };
 
@@ -669,9 +679,9 @@ ImageLayout image_layout(const gm_ctx *ctx, int32_t width, int32_t height, int32
     L.gy = (height + cs - 1) / cs;
     L.m = (int64_t)L.gx * L.gy;
     const size_t N = (size_t)n;
-    const size_t sz[13] = {8 * N, 4 * N, 4 * N, 128 * N, 4 * N, 4 * (size_t)(L.m + 2), 8 * N, 4 * N,
-                           4 * (size_t)(L.m + 2), 256 * N, 4 * N, 4 * N, 16 * (N + 1)};
-    for (int k = 0; k < 13; ++k) {
+    const size_t sz[14] = {8 * N, 4 * N, 4 * N, 128 * N, 4 * N, 4 * (size_t)(L.m + 2), 8 * N, 4 * N,
+                           4 * (size_t)(L.m + 2), 256 * N, 4 * N, 4 * N, 16 * (N + 1), 32 * N};
+    for (int k = 0; k < 14; ++k) {
         L.offs[k] = L.tot;
         L.tot += align_up(std::max<size_t>(sz[k], 1), 256);
     }
@@ -695,6 +705,7 @@ ImageDev image_dev(const ImageLayout &L, void *block, int32_t width, int32_t hei
     dev.desc_h = reinterpret_cast<uint16_t *>(bp + L.offs[9]);
     dev.norm256 = reinterpret_cast<int32_t *>(bp + L.offs[11]);
     dev.rec = reinterpret_cast<int4 *>(bp + L.offs[12]);
+    dev.ext_h = reinterpret_cast<uint16_t *>(bp + L.offs[13]);
     return dev;
 }
 
@@ -763,6 +774,7 @@ gm_status bucket_batches(gm_ctx *ctx, int32_t count, const gm_image *imgs, const
                 j.col_off = const_cast<int32_t *>(d.col_off); j.row_off = const_cast<int32_t *>(d.row_off);
                 j.idx_r = const_cast<int32_t *>(d.idx_r); j.desc = const_cast<int8_t *>(d.desc);
                 j.desc_h = const_cast<uint16_t *>(d.desc_h); j.rec = const_cast<int4 *>(d.rec);
+                j.ext_h = const_cast<uint16_t *>(d.ext_h);
             }
             J[k] = j;
             kp[k] = nk;

@@ -209,6 +209,13 @@ __global__ void batch_desc_kernel(const BucketJob *__restrict__ jobs, const int6
     if (live && part == 0) {
         J->norm[row] = sq;
         J->norm256[row] = sq * 256;
+        // the norm row of the whole-image matcher: -(sq >> 11), -(sq & 2047) / 2, 1024 (all exact in fp16)
+        const uint32_t h0 = (uint32_t)__half_as_ushort(__float2half_rn(-(float)(sq >> 11))) |
+                            ((uint32_t)__half_as_ushort(__float2half_rn(-0.5f * (float)(sq & 2047))) << 16);
+        const uint32_t h1 = (uint32_t)__half_as_ushort(__float2half_rn(1024.0f));
+        uint4 *dx = reinterpret_cast<uint4 *>(J->ext_h + (int64_t)row * 16);
+        dx[0] = make_uint4(h0, h1, 0u, 0u);
+        dx[1] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 

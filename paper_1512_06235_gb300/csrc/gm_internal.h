@@ -34,6 +34,9 @@ struct ImageDev {
     const int32_t *row_off;         // [gx*gy + 2]; cell (cx, cy) -> cy*gx + cx
     const uint16_t *desc_h;         // [n][128] fp16 bits of (b - 128), column-major order (tensor-core path)
     const int4 *rec;                // [n + 1] (x, y, norm * 256, position) column-major; [n] = NaN sentinel
+    // [n][16] fp16, column-major: (-(norm >> 11), -(norm & 2047) / 2, 1024, 0 ...), so that the dot product with the
+    // row (1024, 1, 4096, 0 ...) is 2^22 - norm / 2 exactly (the whole-image matcher's extra K step)
+    const uint16_t *ext_h;
 };
 
 // TMA descriptors of one resident image (tcgen05 path): 64-row boxes of the fp16 descriptor rows (64 elements
@@ -43,6 +46,7 @@ struct TmaMaps {
     CUtensorMap desc_tile;   // fp16 descriptors, 64 x 64 box (contiguous chunks)
     CUtensorMap desc_row;    // fp16 descriptors, 64 x 1 box (gather4 of scattered rows)
     CUtensorMap rec_tile;    // records, 4 x 64 box, NaN past the end
+    CUtensorMap ext_tile;    // the fp16 norm rows (ext_h), 16 x 64 box, 32-byte swizzle, zeros past the end
 };
 
 struct PairDev {
@@ -108,6 +112,7 @@ struct BucketJob {
     int8_t *desc;
     uint16_t *desc_h;
     int4 *rec;
+    uint16_t *ext_h;
 };
 
 // Exclusive scan of m int32 counts into off[0 .. m] (off[m] = total); bsum holds m / 1024 + 1 entries.
@@ -149,9 +154,11 @@ int match_mma_blocks_per_sm(int mt);
 // The group streams come from launch_stream; every image of the batch must have max(gx, gy) <=
 // match_tc_max_grid_lines().  cta_time[0..2] (zeroed by the caller) receive the complement of the earliest CTA
 // start, the complement of the first CTA finish and the last CTA finish (globaltimer, ns).
+// whole_image: every pair of the batch has d = inf (every group uses the whole target image): the specialised
+// kernel adds each target's norm through one more K step and keeps the top-2 on the raw accumulator bits.
 cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const int32_t *grows, const int32_t *stream,
                             int64_t item_begin, int64_t item_end, int32_t grid, int32_t *match_j, BatchCounters *ctr,
-                            unsigned long long *cta_time, cudaStream_t st);
+                            unsigned long long *cta_time, bool whole_image, cudaStream_t st);
 // Candidate streams of the tcgen05 groups [item_begin, item_end) of a batch (grec is indexed by item); *used
 // accumulates the stream entries written (zeroed by the caller).
 cudaError_t launch_stream(const ImageDev *imgs, const PairDev *pairs, const int64_t *item_off, int32_t n_pairs,

@@ -59,27 +59,41 @@ constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
 
 constexpr int kAHalf = kM * 128;                    // one K half of a query tile (bytes)
 constexpr int kBHalf = kN * 128;                    // one K half of a candidate chunk
-constexpr int kOffA = 0;                            // kSlots A tiles
-constexpr int kOffB = kOffA + kSlots * 2 * kAHalf;  // kStages candidate chunks
-constexpr int kOffRec = kOffB + kStages * 2 * kBHalf;
-constexpr int kRecStage = kN * 16;                // records of a chunk (16 bytes each)
-constexpr int kOffCtl = kOffRec + kStages * kRecStage;
 
-struct Ctl {
+// Shared-memory layout.  Banded batches: kSlots A tiles, kStages candidate chunks, a 16-byte record per candidate
+// of every chunk, then the control block (with each slot's staged candidate positions).  Whole-image batches
+// (kWhole): the records give way to each chunk's fp16 norm rows (32 bytes per candidate, 32-byte swizzle) and the
+// constant A block of the norm step (kM rows of 32 bytes); no positions are staged.
+template <bool kWhole>
+struct TcLayout {
+    static constexpr int kOffA = 0;
+    static constexpr int kOffB = kOffA + kSlots * 2 * kAHalf;
+    static constexpr int kSide = kWhole ? kN * 32 : kN * 16;   // per stage: norm rows, or records
+    static constexpr int kOffSide = kOffB + kStages * 2 * kBHalf;
+    static constexpr int kOffAExt = kOffSide + kStages * kSide;
+    static constexpr int kOffCtl = kOffAExt + (kWhole ? kM * 32 : 0);
+    static constexpr int kPos = kWhole ? 4 : kPosCap;
+};
+
+template <bool kWhole>
+struct CtlT {
     GroupDesc desc[kSlots];          // the group in each slot
     float2 qxy[kSlots][kM];          // query coordinates
     int32_t rinfo[kSlots][kM][2];    // original A index (-1: no query), |a'|^2 * 256
     alignas(16) int32_t aidx[kSlots][kM];   // A rows to gather
     int32_t merge[kSlots][kM][4];
-    alignas(16) int32_t pos[kSlots][kPosCap];   // the group's candidate positions (staged by the setup warp)
+    alignas(16) int32_t pos[kSlots][TcLayout<kWhole>::kPos];   // the group's candidate positions (staged)
+    alignas(16) uint32_t smask[kSlots][kPosCap / 256];   // their 32-position slices' quadrant masks, 8 per word
     uint64_t stage_full[kStages], stage_empty[kStages], acc_full[kAcc], acc_empty[kAcc];
     uint64_t grp_full[kSlots], grp_empty[kSlots], merge_ready[kSlots], pos_full[kSlots];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
     unsigned long long stat[3];
 };
-constexpr int kSmemBytes = kOffCtl + (int)sizeof(Ctl) + 1024;
-static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
+template <bool kWhole>
+constexpr int smem_bytes() { return TcLayout<kWhole>::kOffCtl + (int)sizeof(CtlT<kWhole>) + 1024; }
+static_assert(smem_bytes<false>() <= 227 * 1024, "shared memory per CTA");
+static_assert(smem_bytes<true>() <= 227 * 1024, "shared memory per CTA");
 static_assert(kPosCap % kN == 0, "staged positions: whole chunks");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -214,6 +228,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// The same for a K extent of 32 bytes in the 32-byte-swizzled K-major layout: stride byte offset 256 (8-row groups
+// of 32-byte rows), swizzle mode 6.
+__device__ __forceinline__ uint64_t smem_desc32(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
+}
+
 // Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A = B = f16, K-major, N >> 3 (bits 17-22), M >> 4
 // (bits 24-28).
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
@@ -245,6 +267,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
+template <class Ctl>
 __device__ __forceinline__ void raise_abort(Ctl &cl, BatchCounters *ctr)
 {
     if (!cl.abort_flag) {
@@ -286,6 +309,7 @@ __device__ __forceinline__ void setup_load(SetupData &sd, const GroupDesc *__res
 
 // Writes the group into slot g (the slot must be free): query data, descriptor and the staged candidate positions
 // (cp.async); pos_full completes with the 32 lanes' cp.async arrivals and lane 0's release.
+template <class Ctl>
 __device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g, const int32_t *__restrict__ stream)
 {
     const int lane = threadIdx.x & 31;
@@ -303,6 +327,8 @@ __device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g,
         const uint32_t dst = smem_u32(cl.pos[g]);
         const int n16 = (sd.d.total + 3) >> 2;
         for (int k = lane; k < n16; k += 32) cp_async16(dst + 16 * k, src + k);
+        // and the slice masks after them (at most four words, in the stream's own 16-byte-rounded reservation)
+        if (lane == 0) cp_async16(smem_u32(cl.smask[g]), src + n16);
     }
     cp_async_arrive(&cl.pos_full[g]);
     __syncwarp();
@@ -310,16 +336,21 @@ __device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g,
 }
 
 // ------------------------------------------------------------------------------------------------ kernel
+template <bool kWhole>
 __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     const TmaMaps *__restrict__ maps, const GroupDesc *__restrict__ gdesc, const int32_t *__restrict__ grows,
     const int32_t *__restrict__ stream, int64_t item_begin, int64_t item_end, int32_t *__restrict__ match_j,
     BatchCounters *__restrict__ ctr, unsigned long long *__restrict__ cta_time)
 {
+    using L = TcLayout<kWhole>;
+    using Ctl = CtlT<kWhole>;
     const uint64_t t_start = globaltimer();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    Ctl &cl = *reinterpret_cast<Ctl *>(base + kOffCtl);
-    const int4 *rec = reinterpret_cast<const int4 *>(base + kOffRec);
+    Ctl &cl = *reinterpret_cast<Ctl *>(base + L::kOffCtl);
+    const int4 *rec = reinterpret_cast<const int4 *>(base + L::kOffSide);
+    constexpr int kRecStage = L::kSide;
+    constexpr int kOffA = L::kOffA, kOffB = L::kOffB, kOffRec = L::kOffSide;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t stride = gridDim.x;
     const int64_t first = item_begin + blockIdx.x;
@@ -344,6 +375,13 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             mbar_init(&cl.merge_ready[g], kEpiWarps / 2);
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (kWhole && tid < 2 * kM) {
+        // the constant A block of the norm step: (1024, 1, 4096, 0 ...) in both 16-byte halves of every 32-byte row
+        // (so the 32-byte swizzle, which only exchanges the halves, leaves it unchanged); then visible to the
+        // tensor core (async proxy)
+        *reinterpret_cast<uint4 *>(base + L::kOffAExt + 16 * tid) = make_uint4(0x3C006400u, 0x00006C00u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&cl.tmem_base)),
@@ -377,7 +415,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             // the group's descriptor, query rows and staged positions are in the slot once pos_full completes
             if (!mbar_wait_warp(&cl.pos_full[g], (gk / kSlots) & 1)) { ok = false; break; }
             const GroupDesc &dg = cl.desc[g];
-            const int total = dg.total, nchunks = (total + kN - 1) / kN, full = dg.flags & 1, b_n = dg.b_n;
+            // whole-image batches: every group reads the whole image (d = inf for every pair)
+            const int total = dg.total, nchunks = (total + kN - 1) / kN, full = kWhole ? 1 : dg.flags & 1,
+                      b_n = dg.b_n;
             {   // this worker's share of the A tile: operation o = wk + 3 lane < 64 gathers rows 4 (o & 31) + 0..3 of
                 // K half o >> 5; grp_full completes with the three workers' arrivals and all the tile's bytes
                 const int nops = (2 * kM / 4 - wk + kWorkers - 1) / kWorkers;
@@ -409,7 +449,11 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                         mbar_expect_tx(&cl.stage_full[sb], 2u * kBHalf + (uint32_t)kRecStage);
                         tma_tile(bstage, dmap, 0, c * kN, &cl.stage_full[sb], 1024u, &ctr->errors);
                         tma_tile(bstage + kBHalf, dmap, 64, c * kN, &cl.stage_full[sb], 1024u, &ctr->errors);
-                        tma_tile(rstage, rmap, 0, c * kN, &cl.stage_full[sb], 128u, &ctr->errors);
+                        if (kWhole)   // the norm rows (zeros past the image's end)
+                            tma_tile(rstage, &maps[dg.b_slot].ext_tile, 0, c * kN, &cl.stage_full[sb], 256u,
+                                     &ctr->errors);
+                        else
+                            tma_tile(rstage, rmap, 0, c * kN, &cl.stage_full[sb], 128u, &ctr->errors);
                     } else {
                         mbar_arrive(&cl.stage_full[sb]);
                     }
@@ -464,6 +508,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                         mma_f16(tmem + b * kN, smem_desc(abase + (ks >> 2) * kAHalf + off),
                                 smem_desc(bbase + (ks >> 2) * kBHalf + off), ks > 0 ? 1u : 0u);
                     }
+                    if (kWhole)   // + 2^22 - |b'|^2 / 2: the constant A block against the chunk's norm rows
+                        mma_f16(tmem + b * kN, smem_desc32(smem_u32(base + L::kOffAExt)),
+                                smem_desc32(smem_u32(base + kOffRec + s * kRecStage)), 1u);
                     mma_commit(&cl.stage_empty[s]);
                     mma_commit(&cl.acc_full[b]);
                 }
@@ -480,11 +527,18 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         int ck = 0;
         for (int gk = 0; gk < n_groups && !cl.abort_flag; ++gk) {
             const int g = gk % kSlots;
-            if (!mbar_wait_warp(&cl.grp_full[g], (gk / kSlots) & 1)) { raise_abort(cl, ctr); break; }
+            if (!mbar_wait_warp(&cl.grp_full[g], (gk / kSlots) & 1) ||
+                !mbar_wait_warp(&cl.pos_full[g], (gk / kSlots) & 1)) { raise_abort(cl, ctr); break; }
             const GroupDesc &gd = cl.desc[g];
             const int total = gd.total, nchunks = (total + kN - 1) / kN;
             const float d = gd.d;
             const bool unbounded = isinf(d);   // the whole image is every row's candidate set
+            // the quadrant masks of the stream's 32-position slices (banded groups): a slice whose mask lacks this
+            // warp's quadrant holds no keypoint inside any of its rows' bands, and is skipped
+            const bool sliced = (gd.flags & 1) == 0;
+            const int n_slices = (total + 31) >> 5;   // slices past the last one hold no keypoint
+            const uint32_t *mwords = positions_staged(gd) ? cl.smask[g]
+                                     : reinterpret_cast<const uint32_t *>(stream + gd.off + ((total + 3) & ~3));
             const int out_i = cl.rinfo[g][row][0];
             const float qx = cl.qxy[g][row].x, qy = cl.qxy[g][row].y;
             float la = 0.0f, lb = 0.0f, lc = 0.0f, llo = -1.0f, lhi = -1.0f;   // no query: never inside
@@ -503,21 +557,69 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             // key = (|a'|^2 + |b'|^2 - 2 dot) * 256 + column with dot taken from the f32 accumulator through
             // bits = float_bits(dot + 1.5 * 2^23) = 0x4B400000 + dot, and 512 * 0x4B400000 = 2^31 (mod 2^32)
             const uint32_t Rc = (uint32_t)cl.rinfo[g][row][1] + 0x80000000u + (uint32_t)(32 * h);
-            int k1 = INT_MAX, k2 = INT_MAX, j1 = 0, cnt = 0;
+            // whole-image batches keep the largest accumulator bits instead (see below): start below every value
+            int k1 = kWhole ? -1 : INT_MAX, k2 = kWhole ? -1 : INT_MAX, j1 = 0, cnt = 0;
             bool ok = true;
             for (int c = 0; c < nchunks; ++c, ++ck) {
                 const int s = ck % kStages, b = ck % kAcc;
                 if (!mbar_wait_warp(&cl.acc_full[b], (ck / kAcc) & 1)) { ok = false; break; }
+                if (sliced) {
+                    const int sl = 2 * c + h;
+                    if (sl >= n_slices || ((mwords[sl >> 3] >> (4 * (sl & 7) + quadrant)) & 1u) == 0u) {
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive(&cl.acc_empty[b]);
+                            mbar_arrive(&cl.stage_empty[s]);
+                        }
+                        continue;
+                    }
+                }
                 tc_fence_after();
                 uint32_t v[32];
                 tmem_ld32(tmem_lane + b * kN, v);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&cl.acc_empty[b]);
-                if (!mbar_wait_warp(&cl.stage_full[s], (ck / kStages) & 1)) { ok = false; break; }   // records
-                const int4 *rs = rec + (s * kRecStage) / 16 + 32 * h;
                 const int k1_before = k1;
                 const int nvalid = total - c * kN - 32 * h;   // real columns of this half-chunk (may exceed 32)
+                if (kWhole) {
+                    // the accumulator holds 2^22 + a'.b' - |b'|^2 / 2 = 2^22 + (|a'|^2 - D) / 2, exactly (half-
+                    // integers below 2^23) and positive, so its bits order like its values: the two smallest
+                    // distances are the two largest bit patterns.  No records are read: the column of a new best
+                    // gives its position (whole-image groups read the image's rows in order).
+                    if (nvalid >= 32) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj += 2) {
+                            const int u = (int)v[jj], w = (int)v[jj + 1];
+                            const int lo = min(u, w), hi = max(u, w);
+                            k2 = __vimax3_s32(k2, lo, min(k1, hi));
+                            k1 = max(k1, hi);
+                        }
+                        cnt += 32;
+                    } else if (nvalid > 0) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            if (jj < nvalid) {
+                                const int x = (int)v[jj];
+                                k2 = max(k2, min(k1, x));
+                                k1 = max(k1, x);
+                            }
+                        }
+                        cnt += nvalid;
+                    }
+                    if (k1 > k1_before) {   // the column of the new best (the lowest one if several are equal)
+                        int col = 0;
+#pragma unroll
+                        for (int jj = 31; jj >= 0; --jj)
+                            if ((int)v[jj] == k1 && jj < nvalid) col = jj;
+                        j1 = c * kN + 32 * h + col;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&cl.stage_empty[s]);
+                    continue;
+                }
+                if (!mbar_wait_warp(&cl.stage_full[s], (ck / kStages) & 1)) { ok = false; break; }   // records
+                const int4 *rs = rec + (s * kRecStage) / 16 + 32 * h;
                 if (unbounded && nvalid > 0) {
                     // d = inf: every real keypoint is a candidate (Eq. 2 holds for any line), so only the key and
                     // the masked-free top-2 remain; columns past the image's end are skipped
@@ -611,12 +713,23 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 if (!mbar_wait_warp(&cl.merge_ready[g], (gk / kSlots) & 1)) { raise_abort(cl, ctr); break; }
                 const int32_t *mg = cl.merge[g][row];
                 const int ok1 = mg[0], ok2 = mg[1], oj1 = mg[2];
-                const int nk2 = min(max(k1, ok1), min(k2, ok2));
-                if (ok1 < k1) { k1 = ok1; j1 = oj1; }
-                k2 = nk2;
+                int64_t D1, D2;
+                if (kWhole) {   // largest bits first; D = |a'|^2 + 2^23 - 2 (the accumulator's value)
+                    const int nk2 = max(min(k1, ok1), max(k2, ok2));
+                    if (ok1 > k1) { k1 = ok1; j1 = oj1; }
+                    k2 = nk2;
+                    const int64_t na = cl.rinfo[g][row][1] >> 8;
+                    D1 = na + 8388608 - (int64_t)(2.0f * __int_as_float(k1));
+                    D2 = na + 8388608 - (int64_t)(2.0f * __int_as_float(k2));
+                } else {
+                    const int nk2 = min(max(k1, ok1), min(k2, ok2));
+                    if (ok1 < k1) { k1 = ok1; j1 = oj1; }
+                    k2 = nk2;
+                    D1 = k1 >> 8;
+                    D2 = k2 >> 8;
+                }
                 cnt += mg[3];
                 if (out_i >= 0) {
-                    const int64_t D1 = k1 >> 8, D2 = k2 >> 8;
                     const int64_t pp = gd.p, qq = gd.q;
                     int outj = -1;
                     if (cnt >= 2 && qq * qq * D1 < pp * pp * D2) outj = __ldg(gd.b_perm + j1);
@@ -658,12 +771,14 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     }
 }
 
+template <bool kWhole>
 cudaError_t prepare()
 {
     static cudaError_t once = [] {
-        cudaError_t e = cudaFuncSetAttribute(match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(match_tc_kernel<kWhole>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_bytes<kWhole>());
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(match_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+            e = cudaFuncSetAttribute(match_tc_kernel<kWhole>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared);
         return e;
     }();
@@ -678,15 +793,20 @@ int match_tc_max_grid_lines() { return kMaxGridLines; }
 
 cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const int32_t *grows, const int32_t *stream,
                             int64_t item_begin, int64_t item_end, int32_t grid, int32_t *match_j, BatchCounters *ctr,
-                            unsigned long long *cta_time, cudaStream_t st)
+                            unsigned long long *cta_time, bool whole_image, cudaStream_t st)
 {
     const int64_t n = item_end - item_begin;
     if (n <= 0) return cudaSuccess;
-    cudaError_t e = prepare();
-    if (e != cudaSuccess) return e;
     const int64_t g = std::max<int64_t>(1, grid > 0 ? std::min<int64_t>(grid, n) : n);
-    match_tc_kernel<<<(unsigned)g, kThreads, kSmemBytes, st>>>(maps, gdesc, grows, stream, item_begin, item_end, match_j,
-                                                             ctr, cta_time);
+    cudaError_t e = whole_image ? prepare<true>() : prepare<false>();
+    if (e != cudaSuccess) return e;
+    if (whole_image)
+        match_tc_kernel<true><<<(unsigned)g, kThreads, smem_bytes<true>(), st>>>(maps, gdesc, grows, stream, item_begin,
+                                                                               item_end, match_j, ctr, cta_time);
+    else
+        match_tc_kernel<false><<<(unsigned)g, kThreads, smem_bytes<false>(), st>>>(maps, gdesc, grows, stream,
+                                                                                 item_begin, item_end, match_j, ctr,
+                                                                                 cta_time);
     return cudaGetLastError();
 }
 

@@ -84,27 +84,25 @@ __device__ __forceinline__ bool taken(const SelRule &r, uint32_t c, int i)
     return c > r.cstar || (c == r.cstar && i <= r.tie_last);
 }
 
-// The co-visible counts of camera q with every camera, in shared memory (row[q] = 0).  Every point of q must list q
-// exactly once (else *bad); a camera listed twice by one point is caught by that camera's own row.
+// The co-visible counts of camera q with every camera, in shared memory (row[q] = 0): one thread per point of q
+// (the point lists are short; independent threads keep many of their dependent loads in flight).  Every point of q
+// must list q exactly once (else *bad); a camera listed twice by one point is caught by that camera's own row.
 __device__ void count_row(uint32_t *row, int q, int32_t n_cams, const int32_t *__restrict__ cam_off,
                           const int32_t *__restrict__ cam_pts, const int64_t *__restrict__ point_off,
                           const int32_t *__restrict__ point_cams, unsigned long long *bad)
 {
     for (int i = threadIdx.x; i < n_cams; i += blockDim.x) row[i] = 0u;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = cam_off[q] + warp; k < cam_off[q + 1]; k += nw) {
-        const int32_t p = cam_pts[k];
-        const int64_t o = point_off[p], o1 = point_off[p + 1];
+    for (int k = cam_off[q] + threadIdx.x; k < cam_off[q + 1]; k += blockDim.x) {
+        const int32_t p = __ldg(cam_pts + k);
+        const int64_t o = __ldg(point_off + p), o1 = __ldg(point_off + p + 1);
         int own = 0;
-        for (int64_t j = o + lane; j < o1; j += 32) {
-            const int c = point_cams[j];
+        for (int64_t j = o; j < o1; ++j) {
+            const int c = __ldg(point_cams + j);
             if (c == q) ++own;
             else atomicAdd(&row[c], 1u);
         }
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) own += __shfl_xor_sync(0xffffffffu, own, s);
-        if (lane == 0 && own != 1) atomicAdd(bad, 1ull);
+        if (own != 1) atomicAdd(bad, 1ull);
     }
     __syncthreads();
 }

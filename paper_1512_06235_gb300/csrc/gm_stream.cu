@@ -4,8 +4,18 @@
 // the strips' upper and lower envelopes over the walked image axis: the maximum of linear functions is convex and
 // lies below the chord between its end values, the minimum is concave and lies above its chord.  Walking the grid
 // column by column (or row by row for steep lines), one run of cells per grid line covers every keypoint any query
-// of the group can accept; the runs are flattened into a list of column-major keypoint positions (the group's
-// candidate stream) in global memory, which the tcgen05 kernel then gathers chunk by chunk.
+// of the group can accept.
+//
+// The group's 128 rows are four quadrants of 32 consecutive lines (the rows of one epilogue warp of the tcgen05
+// matcher); each quadrant has chord envelopes of its own, built the same way.  Every keypoint of the walked runs is
+// tested against the four quadrant envelopes: a keypoint outside all four is in no row's band (it only shared a cell
+// with the band) and is dropped; the others are ordered by their 4-bit quadrant mask (masks of neighbouring
+// quadrants next to each other), so that most 32-position slices of the stream concern one or two quadrants.  After
+// the positions, the stream holds one 4-bit mask per 32-position slice (8 per 32-bit word): the quadrants whose
+// envelope holds a keypoint of the slice.  An epilogue warp skips the slices its quadrant is not in.  Only the
+// order and the dropped keypoints change: every row still tests every keypoint its envelope holds exactly, and the
+// order of a row's candidates never changes its result (the top-2 keys are unique up to equal distances, which the
+// strict ratio test rejects).
 //
 // One warp per group, four groups per block.  Space is reserved with one atomic per block; a stream that would
 // overflow the buffer marks its group (the caller grows the buffer and runs the batch again).  Groups that contain
@@ -22,6 +32,13 @@ constexpr int kWarps = 4;
 constexpr int kMinBlocks = 1;   // resident blocks per SM that __launch_bounds__ asks the register allocation for
 constexpr int kG = kTcQueriesPerItem;   // queries per group
 constexpr int kMaxLines = 1024;
+constexpr int kBinInts = 48;   // per warp: bin counts [16], bin starts [16], bin cursors [16]
+constexpr int kSortCap = 1024; // per warp: walked keypoints that are sorted by quadrant mask (longer walks keep walk order)
+
+// Stream order of the 15 nonzero quadrant masks (by the centre, then the width of the quadrant range they span):
+// bin r holds the keypoints whose mask is c_mask_of_bin[r]; c_bin[m] is the bin of mask m (15: dropped).
+__constant__ int8_t c_bin[16] = {15, 0, 2, 1, 10, 3, 5, 4, 14, 6, 11, 7, 13, 8, 12, 9};
+__constant__ int8_t c_mask_of_bin[16] = {1, 3, 2, 5, 7, 6, 9, 11, 13, 15, 4, 10, 14, 12, 8, 0};
 
 __device__ __forceinline__ int pair_of_item(const int64_t *__restrict__ item_off, int n_pairs, int64_t t)
 {
@@ -34,26 +51,45 @@ __device__ __forceinline__ int pair_of_item(const int64_t *__restrict__ item_off
     return lo;
 }
 
+// The quadrant mask of keypoint (u, v) (walk axis u, cross axis v): bit q set iff the point lies between quadrant
+// q's two chords at u (qe0 / qd: chord value at u = 0 and its rise over the walked axis; empty quadrants hold -inf
+// tops and +inf bottoms, which hold no point).
+__device__ __forceinline__ unsigned quad_mask(float u, float v, float inv_ulim, const float (&top0)[4],
+                                              const float (&dtop)[4], const float (&bot0)[4], const float (&dbot)[4])
+{
+    const float f = u * inv_ulim;
+    unsigned m = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (v <= fmaf(dtop[q], f, top0[q]) && v >= fmaf(dbot[q], f, bot0[q])) m |= 1u << q;
+    return m;
+}
+
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
     const ImageDev *__restrict__ imgs, const PairDev *__restrict__ pairs, const int64_t *__restrict__ item_off,
     int32_t n_pairs, const int32_t *__restrict__ qorder, int64_t item_begin, int64_t item_end,
     GroupDesc *__restrict__ gdesc, int32_t *__restrict__ grows, int32_t *__restrict__ stream, int64_t capacity,
     unsigned long long *__restrict__ used, BatchCounters *__restrict__ ctr, int32_t max_lines)
 {
-    // per warp: run starts [max_lines] and exclusive run offsets [max_lines + 1] (sized for the batch's images, so
-    // that small grids leave room for more resident blocks)
+    // per warp: run starts [max_lines], exclusive run offsets [max_lines + 1], the bin table and the walked keypoints
+    // (position | bin << 28, in walk order) (sized for the batch's images, so that small grids leave room for more
+    // resident blocks)
     extern __shared__ int32_t runs_smem[];
-    int32_t *const run_start_w = runs_smem + (threadIdx.x >> 5) * (2 * max_lines + 1);
+    int32_t *const run_start_w = runs_smem + (threadIdx.x >> 5) * (2 * max_lines + 1 + kBinInts + kSortCap);
     int32_t *const run_excl_w = run_start_w + max_lines;
+    int32_t *const bin_cnt = run_excl_w + max_lines + 1, *const bin_start = bin_cnt + 16, *const bin_cur = bin_cnt + 32;
+    int32_t *const ent = bin_cnt + kBinInts;
     __shared__ int32_t wtotal[kWarps];
     __shared__ unsigned long long wbase[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t item = item_begin + (int64_t)blockIdx.x * kWarps + warp;
     const bool active = item < item_end;
-    int total = 0, full = 0, colwise = 1;
+    int total = 0, kept = 0, n_words = 0, full = 0, colwise = 1;
+    bool sorted = false;   // the walk fits kSortCap: keypoints filtered and ordered by quadrant mask
     const ImageDev *Bp = nullptr;
     const PairDev *Pp = nullptr;
     const ImageDev *Ap = nullptr;
+    float qtop0[4], qdtop[4], qbot0[4], qdbot[4], inv_ulim = 0.0f;
     if (active) {
         const int pi = pair_of_item(item_off, n_pairs, item);
         const PairDev &P = pairs[pi];
@@ -95,9 +131,15 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
         }
         colwise = 2 * votes >= nnorm;
         const float ulim = colwise ? W : H, vlim = colwise ? H : W;
-        float t0 = -INFINITY, t1 = -INFINITY, b0 = INFINITY, b1 = INFINITY, pad = 0.0f;
+        inv_ulim = 1.0f / ulim;
+        // chord end values of every quadrant (rows lane + 32 t form quadrant t), then of the whole group
+        float qt0[4], qt1[4], qb0[4], qb1[4], pad = 0.0f;
+        int qn[4];
 #pragma unroll
         for (int t = 0; t < kG / 32; ++t) {
+            qt0[t] = qt1[t] = -INFINITY;
+            qb0[t] = qb1[t] = INFINITY;
+            qn[t] = 0;
             if (L4[t].mode != kBandNormal) continue;
             float pa = colwise ? L4[t].a : L4[t].b, pb = colwise ? L4[t].b : L4[t].a, c = L4[t].c;
             if (pb < 0.0f) { pa = -pa; pb = -pb; c = -c; }
@@ -105,22 +147,46 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
             if (!(pb > 1e-30f)) { full = 1; continue; }
             const float ib = 1.0f / pb;
             const float e0 = -c * ib, e1 = -fmaf(pa, ulim, c) * ib, h = T * ib;
-            t0 = fmaxf(t0, e0 + h); t1 = fmaxf(t1, e1 + h);
-            b0 = fminf(b0, e0 - h); b1 = fminf(b1, e1 - h);
+            qt0[t] = e0 + h; qt1[t] = e1 + h;
+            qb0[t] = e0 - h; qb1[t] = e1 - h;
+            qn[t] = 1;
             pad = fmaxf(pad, 8.0f * kU * (fabsf(pa) * ulim + fabsf(c) + T) * ib);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            t0 = fmaxf(t0, __shfl_xor_sync(0xffffffffu, t0, o));
-            t1 = fmaxf(t1, __shfl_xor_sync(0xffffffffu, t1, o));
-            b0 = fminf(b0, __shfl_xor_sync(0xffffffffu, b0, o));
-            b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+#pragma unroll
+            for (int t = 0; t < kG / 32; ++t) {
+                qt0[t] = fmaxf(qt0[t], __shfl_xor_sync(0xffffffffu, qt0[t], o));
+                qt1[t] = fmaxf(qt1[t], __shfl_xor_sync(0xffffffffu, qt1[t], o));
+                qb0[t] = fminf(qb0[t], __shfl_xor_sync(0xffffffffu, qb0[t], o));
+                qb1[t] = fminf(qb1[t], __shfl_xor_sync(0xffffffffu, qb1[t], o));
+                qn[t] |= __shfl_xor_sync(0xffffffffu, qn[t], o);
+            }
             pad = fmaxf(pad, __shfl_xor_sync(0xffffffffu, pad, o));
             full |= __shfl_xor_sync(0xffffffffu, full, o);
         }
-        pad += 1e-3f + 4.0f * kU * (fabsf(t0) + fabsf(t1) + fabsf(b0) + fabsf(b1));
-        const float et0 = t0 + pad, et1 = t1 + pad, eb0 = b0 - pad, eb1 = b1 - pad;
+        float t0 = -INFINITY, t1 = -INFINITY, b0 = INFINITY, b1 = INFINITY;
+#pragma unroll
+        for (int t = 0; t < kG / 32; ++t) {
+            t0 = fmaxf(t0, qt0[t]); t1 = fmaxf(t1, qt1[t]);
+            b0 = fminf(b0, qb0[t]); b1 = fminf(b1, qb1[t]);
+        }
+        const float wpad = pad + 1e-3f + 4.0f * kU * (fabsf(t0) + fabsf(t1) + fabsf(b0) + fabsf(b1));
+        const float et0 = t0 + wpad, et1 = t1 + wpad, eb0 = b0 - wpad, eb1 = b1 - wpad;
         if (nnorm > 0 && !(isfinite(et0) && isfinite(et1) && isfinite(eb0) && isfinite(eb1))) full = 1;
+        // quadrant chords for the keypoint test: the walk's margin, each quadrant's own rounding term and 0.01 px
+#pragma unroll
+        for (int t = 0; t < kG / 32; ++t) {
+            if (qn[t]) {
+                const float qpad =
+                    pad + 1.1e-2f + 4.0f * kU * (fabsf(qt0[t]) + fabsf(qt1[t]) + fabsf(qb0[t]) + fabsf(qb1[t]));
+                qtop0[t] = qt0[t] + qpad; qdtop[t] = qt1[t] - qt0[t];
+                qbot0[t] = qb0[t] - qpad; qdbot[t] = qb1[t] - qb0[t];
+            } else {
+                qtop0[t] = -INFINITY; qdtop[t] = 0.0f;
+                qbot0[t] = INFINITY; qdbot[t] = 0.0f;
+            }
+        }
         const int nlines = colwise ? B.gx : B.gy;
         if (full) {
             total = B.n;
@@ -175,11 +241,61 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
             }
             if (lane == 0) run_excl_w[nlines] = carry;
             total = carry;
+            sorted = total <= kSortCap;
+            if (sorted) {
+                // every walked keypoint's quadrant mask and bin, kept in walk order (position | bin << 28); lane-local
+                // bin counts in 16-bit fields, four bins per 64-bit word
+                const float2 *pxy = colwise ? B.xy : B.xy_r;
+                uint64_t c40 = 0ull, c41 = 0ull, c42 = 0ull, c43 = 0ull;
+                for (int kk = lane; kk < nlines; kk += 32) {
+                    const int e0 = run_excl_w[kk], len = run_excl_w[kk + 1] - e0, st = run_start_w[kk];
+                    for (int k = 0; k < len; ++k) {
+                        const float2 p = __ldg(pxy + st + k);
+                        const unsigned m = colwise ? quad_mask(p.x, p.y, inv_ulim, qtop0, qdtop, qbot0, qdbot)
+                                                   : quad_mask(p.y, p.x, inv_ulim, qtop0, qdtop, qbot0, qdbot);
+                        const int bin = c_bin[m];
+                        const int pos = colwise ? st + k : B.idx_r[st + k];
+                        ent[e0 + k] = pos | (bin << 28);
+                        const uint64_t inc = bin < 15 ? 1ull << (16 * (bin & 3)) : 0ull;
+                        const int w4 = bin >> 2;
+                        c40 += w4 == 0 ? inc : 0ull;
+                        c41 += w4 == 1 ? inc : 0ull;
+                        c42 += w4 == 2 ? inc : 0ull;
+                        c43 += w4 == 3 ? inc : 0ull;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    c40 += __shfl_xor_sync(0xffffffffu, c40, o);
+                    c41 += __shfl_xor_sync(0xffffffffu, c41, o);
+                    c42 += __shfl_xor_sync(0xffffffffu, c42, o);
+                    c43 += __shfl_xor_sync(0xffffffffu, c43, o);
+                }
+                // bin starts (exclusive scan in bin order) and the kept total
+                const uint64_t mine = (lane >> 2) == 0 ? c40 : (lane >> 2) == 1 ? c41 : (lane >> 2) == 2 ? c42 : c43;
+                const int cnt = lane < 15 ? (int)((mine >> (16 * (lane & 3))) & 0xffffull) : 0;
+                int incl = cnt;
+#pragma unroll
+                for (int s = 1; s < 32; s <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, incl, s);
+                    if (lane >= s) incl += u;
+                }
+                if (lane < 16) {
+                    bin_cnt[lane] = cnt;
+                    bin_start[lane] = incl - cnt;
+                    bin_cur[lane] = incl - cnt;
+                }
+                kept = __shfl_sync(0xffffffffu, incl, 31);
+            } else {
+                kept = total;   // a long walk keeps its order and every keypoint; its slices concern every quadrant
+            }
+            n_words = ((kept + 31) / 32 + 7) / 8;
+            __syncwarp();
         }
     }
-    // reserve the block's space with one atomic; every stream starts on a 16-byte boundary (reservations are
-    // rounded up to four positions) so that the matcher can stage it with 16-byte copies
-    if (lane == 0) wtotal[warp] = (active && !full) ? (total + 3) & ~3 : 0;
+    // reserve the block's space with one atomic; every stream starts on a 16-byte boundary (positions and mask
+    // words are each rounded up to four entries) so that the matcher can stage it with 16-byte copies
+    if (lane == 0) wtotal[warp] = (active && !full) ? ((kept + 3) & ~3) + ((n_words + 3) & ~3) : 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long sum = 0;
@@ -193,7 +309,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
     __syncthreads();
     if (!active) return;
     const unsigned long long off = wbase[warp];
-    const bool overflow = !full && off + (unsigned long long)((total + 3) & ~3) > (unsigned long long)capacity;
+    const int reserve = ((kept + 3) & ~3) + ((n_words + 3) & ~3);
+    const bool overflow = !full && off + (unsigned long long)reserve > (unsigned long long)capacity;
     if (lane == 0) {
         const PairDev &P = *Pp;
         const ImageDev &A = *Ap, &B = *Bp;
@@ -209,7 +326,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
         r.b_slot = P.b;
         r.a_n = A.n;
         r.b_n = B.n;
-        r.total = overflow ? 0 : total;
+        r.total = overflow ? 0 : (full ? total : kept);
         r.flags = (full ? 1 : 0) | (overflow ? 2 : 0);
         r.p = P.p;
         r.q = P.q;
@@ -220,19 +337,59 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
         r.qoff = P.qoff;
         gdesc[item] = r;
         if (overflow) atomicAdd(&ctr->overflow, 1ull);
-        else if (!full && total > kTcStagedPositions) atomicAdd(&ctr->unstaged, 1ull);
-        atomicAdd(&ctr->examined, (unsigned long long)total * kG);
+        else if (!full && kept > kTcStagedPositions) atomicAdd(&ctr->unstaged, 1ull);
+        if (full) atomicAdd(&ctr->examined, (unsigned long long)total * kG);
     }
-    if (full || overflow || total == 0) return;
-    // flatten the runs: every lane writes the positions of its grid lines
+    if (full || overflow || kept == 0) return;
     const ImageDev &B = *Bp;
-    const int nlines = colwise ? B.gx : B.gy;
-    for (int kk = lane; kk < nlines; kk += 32) {
-        const int e0 = run_excl_w[kk], len = run_excl_w[kk + 1] - e0;
-        const int st = run_start_w[kk];
-        int32_t *dst = stream + off + e0;
-        for (int k = 0; k < len; ++k) dst[k] = colwise ? st + k : B.idx_r[st + k];
+    int32_t *dst = stream + off;
+    if (sorted) {
+        // the kept keypoints in bin order: 32 walked keypoints at a time, each lane's rank among the lanes of its bin
+        // (walk order within a bin), one cursor update per bin present
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = e0 + lane;
+            const int x = e < total ? ent[e] : (15 << 28);
+            const int bin = (int)((unsigned)x >> 28);
+            const unsigned grp = __match_any_sync(0xffffffffu, bin);
+            const int rank = __popc(grp & lanemask_lt());
+            if (bin < 15) dst[bin_cur[bin] + rank] = x & 0x0fffffff;
+            __syncwarp();
+            if (bin < 15 && rank == 0) bin_cur[bin] += __popc(grp);
+            __syncwarp();
+        }
+    } else {
+        // walk order, every lane the keypoints of its grid lines
+        const int nlines = colwise ? B.gx : B.gy;
+        for (int kk = lane; kk < nlines; kk += 32) {
+            const int e0 = run_excl_w[kk], len = run_excl_w[kk + 1] - e0, st = run_start_w[kk];
+            for (int k = 0; k < len; ++k) dst[e0 + k] = colwise ? st + k : B.idx_r[st + k];
+        }
     }
+    // the 4-bit quadrant mask of every 32-position slice (the masks of the bins it overlaps), 8 slices per word;
+    // the elements the epilogue will test: 32 x 32 per quadrant of every slice
+    const int n_slices = (kept + 31) / 32;
+    unsigned long long elems = 0;
+    uint32_t *words = reinterpret_cast<uint32_t *>(dst + ((kept + 3) & ~3));
+    for (int w = lane; w < n_words; w += 32) {
+        uint32_t word = 0u;
+        for (int j = 0; j < 8; ++j) {
+            const int sl = 8 * w + j;
+            if (sl >= n_slices) break;
+            const int lo = 32 * sl, hi = min(32 * sl + 32, kept);
+            unsigned m = sorted ? 0u : 0xfu;
+            if (sorted)
+                for (int bin = 0; bin < 15; ++bin) {
+                    const int b0 = bin_start[bin], b1 = b0 + bin_cnt[bin];
+                    if (b0 < hi && b1 > lo) m |= (unsigned)c_mask_of_bin[bin];
+                }
+            word |= m << (4 * j);
+            elems += (unsigned long long)__popc(m) * 32ull * 32ull;
+        }
+        words[w] = word;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) elems += __shfl_xor_sync(0xffffffffu, elems, o);
+    if (lane == 0) atomicAdd(&ctr->examined, elems);
 }
 
 }  // namespace
@@ -246,9 +403,10 @@ cudaError_t launch_stream(const ImageDev *imgs, const PairDev *pairs, const int6
     if (n <= 0) return cudaSuccess;
     if (max_lines < 1 || max_lines > kMaxLines) return cudaErrorInvalidValue;
     static const cudaError_t attr = cudaFuncSetAttribute(stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         (int)(sizeof(int32_t) * kWarps * (2 * kMaxLines + 1)));
+                                                         (int)(sizeof(int32_t) * kWarps *
+                                                               (2 * kMaxLines + 1 + kBinInts + kSortCap)));
     if (attr != cudaSuccess) return attr;
-    const size_t smem = sizeof(int32_t) * kWarps * (2 * (size_t)max_lines + 1);
+    const size_t smem = sizeof(int32_t) * kWarps * (2 * (size_t)max_lines + 1 + kBinInts + kSortCap);
     stream_kernel<<<(unsigned)((n + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
         imgs, pairs, item_off, n_pairs, qorder, item_begin, item_end, gdesc, grows, stream, capacity, used, ctr,
         max_lines);

@@ -167,10 +167,12 @@ __device__ __forceinline__ int pair_of_row(const int64_t *__restrict__ off, int 
     return lo;
 }
 
-// Every row names features inside its images, and i increases strictly within a pair (one match per query).
-__global__ void trk_check_kernel(const int2 *__restrict__ rows, int64_t n_rows, const int64_t *__restrict__ off,
-                                 int n_pairs, const TrkPair *__restrict__ pairs, const TriImage *__restrict__ imgs,
-                                 unsigned long long *bad)
+// Every row names features inside its images, and i increases strictly within a pair (one match per query); each
+// valid row is entered in its pair's dense query index: slot[pbase[p] + i] = row (slots start at -1).
+__global__ void trk_scatter_kernel(const int2 *__restrict__ rows, int64_t n_rows, const int64_t *__restrict__ off,
+                                   int n_pairs, const TrkPair *__restrict__ pairs, const TriImage *__restrict__ imgs,
+                                   const int64_t *__restrict__ pbase, int32_t *__restrict__ slot,
+                                   unsigned long long *bad)
 {
     for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n_rows; m += (int64_t)gridDim.x * blockDim.x) {
         const int p = pair_of_row(off, n_pairs, m);
@@ -178,30 +180,20 @@ __global__ void trk_check_kernel(const int2 *__restrict__ rows, int64_t n_rows, 
         bool ok = r.x >= 0 && r.x < imgs[pairs[p].ka].n && r.y >= 0 && r.y < imgs[pairs[p].kb].n;
         if (m + 1 < off[p + 1]) ok = ok && rows[m + 1].x > r.x;
         if (!ok) atomicAdd(bad, 1ull);
+        else slot[pbase[p] + r.x] = (int32_t)m;
     }
 }
 
-// The row of pair p whose query is f, or -1 (binary search over the pair's rows, sorted by query).
-__device__ __forceinline__ int64_t find_row(const int2 *__restrict__ rows, int64_t lo, int64_t hi, int f)
-{
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        const int x = __ldg(&rows[mid].x);
-        if (x == f) return mid;
-        if (x < f) lo = mid + 1;
-        else hi = mid;
-    }
-    return -1;
-}
-
-// Pass 1 (count = false): flag[v] = 1 if node v matched in any pair of its image.  Pass 2 (count = true): for every
+// Pass 1 (kSolve = false): flag[v] = 1 if node v matched in any pair of its image.  Pass 2 (kSolve = true): for every
 // flagged node, the normal equations of its track -- its own observation, then one per pair of its image (in the
-// caller's order) in which it matched -- solved into the track's slot track_of[v].
+// caller's order) in which it matched -- solved into the track's slot track_of[v].  Consecutive nodes read
+// consecutive entries of each pair's dense query index.
 template <bool kSolve>
 __global__ void trk_node_kernel(int64_t n_nodes, const TriImage *__restrict__ imgs, int n_images,
                                 const int32_t *__restrict__ img_poff, const int32_t *__restrict__ img_pairs,
-                                const TrkPair *__restrict__ pairs, const int64_t *__restrict__ off,
-                                const int2 *__restrict__ rows, const double *__restrict__ P, int32_t *__restrict__ flag,
+                                const TrkPair *__restrict__ pairs, const int64_t *__restrict__ pbase,
+                                const int32_t *__restrict__ slot, const int2 *__restrict__ rows,
+                                const double *__restrict__ P, int32_t *__restrict__ flag,
                                 const int32_t *__restrict__ track_of, double *__restrict__ X,
                                 int64_t *__restrict__ nodes, int32_t *__restrict__ n_views)
 {
@@ -210,10 +202,8 @@ __global__ void trk_node_kernel(int64_t n_nodes, const TriImage *__restrict__ im
         const int f = (int)(v - imgs[k].base);
         if (!kSolve) {
             int found = 0;
-            for (int t = img_poff[k]; t < img_poff[k + 1] && !found; ++t) {
-                const int p = img_pairs[t];
-                found = find_row(rows, off[p], off[p + 1], f) >= 0;
-            }
+            for (int t = img_poff[k]; t < img_poff[k + 1] && !found; ++t)
+                found = __ldg(slot + pbase[img_pairs[t]] + f) >= 0;
             flag[v] = found;
             continue;
         }
@@ -225,7 +215,7 @@ __global__ void trk_node_kernel(int64_t n_nodes, const TriImage *__restrict__ im
         int nv = 1;
         for (int t = img_poff[k]; t < img_poff[k + 1]; ++t) {
             const int p = img_pairs[t];
-            const int64_t m = find_row(rows, off[p], off[p + 1], f);
+            const int32_t m = __ldg(slot + pbase[p] + f);
             if (m < 0) continue;
             const int kb = pairs[p].kb;
             const TriImage &B = imgs[kb];
@@ -422,8 +412,13 @@ gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32
     const size_t m_b = dev_m ? 0 : align_up(sizeof(int32_t) * 2 * (size_t)M, 256);
     const size_t fl_b = align_up(4 * N, 256), tr_b = align_up(4 * (N + 1), 256);
     const size_t bs_b = align_up(4 * (N / 1024 + 2), 256);
+    // every pair's dense query index: one int32 per feature of its query image
+    std::vector<int64_t> pbase(n_pairs + 1, 0);
+    for (int32_t p = 0; p < n_pairs; ++p) pbase[p + 1] = pbase[p] + imgs[pairs[p].ka].n;
+    const size_t pb_b = align_up(sizeof(int64_t) * (n_pairs + 1), 256);
+    const size_t sl_b = align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(pbase[n_pairs], 1), 256);
     gm_status st = ensure_dev(ctx, ctx->d_tri,
-                              img_b + p_b + off_b + pr_b + ip_b + il_b + m_b + fl_b + tr_b + bs_b + 256);
+                              img_b + p_b + off_b + pr_b + ip_b + il_b + m_b + fl_b + tr_b + bs_b + 256 + pb_b + sl_b);
     if (st != GM_OK) return st;
     char *w = static_cast<char *>(ctx->d_tri.p);
     TriImage *d_imgs = reinterpret_cast<TriImage *>(w);
@@ -450,6 +445,10 @@ gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32
     int32_t *track_of = reinterpret_cast<int32_t *>(w + fl_b);
     int32_t *bsum = reinterpret_cast<int32_t *>(w + fl_b + tr_b);
     unsigned long long *bad = reinterpret_cast<unsigned long long *>(w + fl_b + tr_b + bs_b);
+    int64_t *d_pbase = reinterpret_cast<int64_t *>(w + fl_b + tr_b + bs_b + 256);
+    int32_t *slot = reinterpret_cast<int32_t *>(w + fl_b + tr_b + bs_b + 256 + pb_b);
+    GM_CUDA_R(cudaMemcpyAsync(d_pbase, pbase.data(), sizeof(int64_t) * (n_pairs + 1), cudaMemcpyHostToDevice, s));
+    GM_CUDA_R(cudaMemsetAsync(slot, 0xff, sizeof(int32_t) * (size_t)pbase[n_pairs], s));
     GM_CUDA_R(cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(TriImage) * n_images, cudaMemcpyHostToDevice, s));
     GM_CUDA_R(cudaMemcpyAsync(d_P, P, sizeof(double) * 12 * n_images,
                               dev_p ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -459,15 +458,15 @@ gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32
     GM_CUDA_R(cudaMemcpyAsync(d_ipairs, img_pairs.data(), sizeof(int32_t) * n_pairs, cudaMemcpyHostToDevice, s));
     GM_CUDA_R(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
     const int grid = std::max(1, ctx->num_sms * 8);
-    trk_check_kernel<<<grid, 256, 0, s>>>(d_rows, M, d_off, n_pairs, d_pairs, d_imgs, bad);
+    trk_scatter_kernel<<<grid, 256, 0, s>>>(d_rows, M, d_off, n_pairs, d_pairs, d_imgs, d_pbase, slot, bad);
     unsigned long long h_bad = 0;
     GM_CUDA_R(cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, s));
     GM_CUDA_R(cudaStreamSynchronize(s));
     if (h_bad)
         return fail(GM_ERR_INVALID,
                     "gm_triangulate_image_tracks: %llu match rows outside their images or not sorted by query", h_bad);
-    trk_node_kernel<false><<<grid, 256, 0, s>>>(total, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_off, d_rows,
-                                                d_P, flag, nullptr, nullptr, nullptr, nullptr);
+    trk_node_kernel<false><<<grid, 256, 0, s>>>(total, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_pbase, slot,
+                                                d_rows, d_P, flag, nullptr, nullptr, nullptr, nullptr);
     GM_CUDA_R(launch_exclusive_scan(flag, (int32_t)total, track_of, bsum, s));
     int32_t nt = 0;
     GM_CUDA_R(cudaMemcpyAsync(&nt, track_of + total, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -486,8 +485,8 @@ gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32
     double *dX = dev_o ? X : reinterpret_cast<double *>(o);
     int64_t *dN = dev_o ? nodes : reinterpret_cast<int64_t *>(o + x_b);
     int32_t *dV = dev_o ? n_views : reinterpret_cast<int32_t *>(o + x_b + r_b);
-    trk_node_kernel<true><<<grid, 256, 0, s>>>(total, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_off, d_rows, d_P,
-                                               nullptr, track_of, dX, dN, dV);
+    trk_node_kernel<true><<<grid, 256, 0, s>>>(total, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_pbase, slot,
+                                               d_rows, d_P, nullptr, track_of, dX, dN, dV);
     GM_CUDA_R(cudaGetLastError());
     if (!dev_o) {
         GM_CUDA_R(cudaMemcpyAsync(X, dX, sizeof(double) * 3 * nt, cudaMemcpyDeviceToHost, s));
