@@ -243,45 +243,49 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
             total = carry;
             sorted = total <= kSortCap;
             if (sorted) {
-                // every walked keypoint's quadrant mask and bin, kept in walk order (position | bin << 28); lane-local
-                // bin counts in 16-bit fields, four bins per 64-bit word
+                // every walked keypoint's quadrant mask and bin, kept in walk order (position | bin << 28).  The
+                // keypoints are taken 32 at a time by the whole warp: every non-empty grid line marks its first
+                // position, and a running maximum of the marks gives each position its line.
                 const float2 *pxy = colwise ? B.xy : B.xy_r;
-                uint64_t c40 = 0ull, c41 = 0ull, c42 = 0ull, c43 = 0ull;
-                for (int kk = lane; kk < nlines; kk += 32) {
-                    const int e0 = run_excl_w[kk], len = run_excl_w[kk + 1] - e0, st = run_start_w[kk];
-                    for (int k = 0; k < len; ++k) {
-                        const float2 p = __ldg(pxy + st + k);
+                for (int e = lane; e < total; e += 32) ent[e] = -1;
+                if (lane < 16) bin_cnt[lane] = 0;
+                __syncwarp();
+                for (int kk = lane; kk < nlines; kk += 32)
+                    if (run_excl_w[kk + 1] > run_excl_w[kk]) ent[run_excl_w[kk]] = kk;
+                __syncwarp();
+                int line_carry = -1;
+                for (int e0 = 0; e0 < total; e0 += 32) {
+                    const int e = e0 + lane;
+                    int line = e < total ? ent[e] : -1;
+#pragma unroll
+                    for (int sft = 1; sft < 32; sft <<= 1) {
+                        const int u = __shfl_up_sync(0xffffffffu, line, sft);
+                        if (lane >= sft) line = max(line, u);
+                    }
+                    line = max(line, line_carry);
+                    line_carry = __shfl_sync(0xffffffffu, line, 31);
+                    int bin = 15;
+                    if (e < total) {
+                        const int idx = run_start_w[line] + (e - run_excl_w[line]);
+                        const float2 p = __ldg(pxy + idx);
                         const unsigned m = colwise ? quad_mask(p.x, p.y, inv_ulim, qtop0, qdtop, qbot0, qdbot)
                                                    : quad_mask(p.y, p.x, inv_ulim, qtop0, qdtop, qbot0, qdbot);
-                        const int bin = c_bin[m];
-                        const int pos = colwise ? st + k : B.idx_r[st + k];
-                        ent[e0 + k] = pos | (bin << 28);
-                        const uint64_t inc = bin < 15 ? 1ull << (16 * (bin & 3)) : 0ull;
-                        const int w4 = bin >> 2;
-                        c40 += w4 == 0 ? inc : 0ull;
-                        c41 += w4 == 1 ? inc : 0ull;
-                        c42 += w4 == 2 ? inc : 0ull;
-                        c43 += w4 == 3 ? inc : 0ull;
+                        bin = c_bin[m];
+                        ent[e] = (colwise ? idx : __ldg(B.idx_r + idx)) | (bin << 28);
                     }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    c40 += __shfl_xor_sync(0xffffffffu, c40, o);
-                    c41 += __shfl_xor_sync(0xffffffffu, c41, o);
-                    c42 += __shfl_xor_sync(0xffffffffu, c42, o);
-                    c43 += __shfl_xor_sync(0xffffffffu, c43, o);
+                    const unsigned grp = __match_any_sync(0xffffffffu, bin);
+                    if (bin < 15 && (grp & lanemask_lt()) == 0u) bin_cnt[bin] += __popc(grp);
+                    __syncwarp();
                 }
                 // bin starts (exclusive scan in bin order) and the kept total
-                const uint64_t mine = (lane >> 2) == 0 ? c40 : (lane >> 2) == 1 ? c41 : (lane >> 2) == 2 ? c42 : c43;
-                const int cnt = lane < 15 ? (int)((mine >> (16 * (lane & 3))) & 0xffffull) : 0;
+                const int cnt = lane < 15 ? bin_cnt[lane] : 0;
                 int incl = cnt;
 #pragma unroll
-                for (int s = 1; s < 32; s <<= 1) {
-                    const int u = __shfl_up_sync(0xffffffffu, incl, s);
-                    if (lane >= s) incl += u;
+                for (int sft = 1; sft < 32; sft <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, incl, sft);
+                    if (lane >= sft) incl += u;
                 }
                 if (lane < 16) {
-                    bin_cnt[lane] = cnt;
                     bin_start[lane] = incl - cnt;
                     bin_cur[lane] = incl - cnt;
                 }
