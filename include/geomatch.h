@@ -73,10 +73,13 @@ enum {
     GM_OPT_GRAPH = 4,       /* 1 = replay batches through a captured CUDA graph when the shape repeats */
     GM_OPT_MMA_GROUP = 5,   /* queries per group of the mma path: 16 (default) or 32 */
     GM_OPT_STREAM_CAP = 6,  /* entries of the tcgen05 path's candidate-stream buffer (grown automatically) */
-    GM_OPT_EVICT_LRU = 7    /* 1 = an image put that would exceed the memory budget first evicts the least recently
+    GM_OPT_EVICT_LRU = 7,   /* 1 = an image put that would exceed the memory budget first evicts the least recently
                                used images (last put or matched), with their coarse views, as gm_image_evict would
                                -- never one of the images being put nor one that an unfinished serving request
                                names; 0 (default) = refuse with GM_ERR_BUDGET */
+    GM_OPT_TC_PIPE = 8      /* pipeline geometry of the tcgen05 path: 0 (default) = 6 candidate chunks and 3 query
+                               groups in flight, 1024 positions staged per group; 1 = 8 chunks, 2 groups, 1024;
+                               2 = 4 chunks, 4 groups, 512 (longer candidate streams are read from global memory) */
 };
 
 typedef struct {
@@ -127,6 +130,7 @@ typedef struct {
     int32_t cell_px;             /* grid cell size chosen: 4, 8 or 16 px */
     float ms;                    /* device time of the batch with these settings (best of the timed runs) */
     int32_t from_cache;          /* 1 if the settings came from the tuner_cache file without timing */
+    int32_t tc_pipe;             /* GM_OPT_TC_PIPE chosen (the tcgen05 path's pipeline geometry; 0 on other paths) */
 } gm_tune_result;
 
 /* Creates a context on cfg->device.  *out receives the handle.  Errors: GM_ERR_INVALID (null pointer, bad
@@ -325,9 +329,10 @@ GM_API gm_status gm_match_pairs_approx(gm_ctx *ctx, int32_t n_pairs, const gm_pa
 GM_API gm_status gm_selftest_wait(gm_ctx *ctx, int32_t limit_us, int32_t set_flag);
 
 /* Autotuner (a tuning aid; the paper has no counterpart).  Times gm_match_pairs on this batch for every distance
- * path (tc; mma with 16- and 32-query groups; simt) and grid cell size (4, 8, 16 px), `repeats` timed runs each
- * after one warm-up, and leaves the fastest setting in the context: GM_OPT_PATH, GM_OPT_MMA_GROUP and
- * GM_OPT_CELL_PX, with the batch's images re-binned from their resident copies to the chosen cell size.  Every
+ * path (tc in each of its three pipeline geometries; mma with 16- and 32-query groups; simt) and grid cell size
+ * (4, 8, 16 px), `repeats` timed runs each after one warm-up, and leaves the fastest setting in the context:
+ * GM_OPT_PATH, GM_OPT_TC_PIPE, GM_OPT_MMA_GROUP and GM_OPT_CELL_PX, with the batch's images re-binned from their
+ * resident copies to the chosen cell size.  Every
  * setting gives identical match lists.  With cfg->tuner_cache set, the choice is appended to that text file under
  * the batch's signature (pair count, query and target totals, band sum, image size) and a later call with the same
  * signature applies it without timing (*out->from_cache = 1).  Errors: GM_ERR_INVALID (null pointer, n_pairs < 1,

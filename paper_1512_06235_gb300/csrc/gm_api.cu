@@ -383,7 +383,8 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
             return launch_match_tc(static_cast<const TmaMaps *>(ctx->d_maps.p),
                                    static_cast<const GroupDesc *>(ws.d_grec.p),
                                    static_cast<const int32_t *>(ws.d_grows.p), static_cast<const int32_t *>(ws.d_stream.p),
-                                   i0, i1, gsz > 0 ? gsz : ctx->num_sms, match_j, ctr, cta_time, whole_image, s);
+                                   i0, i1, gsz > 0 ? gsz : ctx->num_sms, match_j, ctr, cta_time, whole_image,
+                                   ctx->tc_pipe, s);
         return launch_match_mma(mt, imgs, d_proc, d_item_off, P, qorder, i0, i1, gsz, next, match_j, ctr, s);
     };
 
@@ -440,7 +441,7 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
     };
     ws.path_used = path;
     if (!ctx->graph || ctx->schedule == 1) return enqueue(false);
-    const GraphKey key{P, Q, n_items, path, mt, grid, ws.stream_cap, tab_bytes, ws.d_tab.p, ws.d_qorder.p,
+    const GraphKey key{P, Q, n_items, path, mt, ctx->tc_pipe, 0, grid, ws.stream_cap, tab_bytes, ws.d_tab.p, ws.d_qorder.p,
                        ws.d_matchj.p, ws.d_counts.p, ws.d_off.p, rows, ws.d_ctr.p, ws.d_grec.p, ws.d_grows.p,
                        ws.d_stream.p, ctx->d_imgs.p, ctx->d_maps.p, ws.h_tab.p, ws.h_off.p, s};
     if (ws.gexec && std::memcmp(&key, &ws.gkey, sizeof(key)) == 0) {
@@ -643,6 +644,10 @@ gm_status gm_set_option(gm_ctx *ctx, int32_t key, int64_t value)
     case GM_OPT_EVICT_LRU:
         if (value < 0 || value > 1) return fail(GM_ERR_INVALID, "bad eviction flag");
         ctx->evict_lru = (int32_t)value;
+        return GM_OK;
+    case GM_OPT_TC_PIPE:
+        if (value < 0 || value >= kTcPipes) return fail(GM_ERR_INVALID, "tc pipeline geometry must be 0, 1 or 2");
+        ctx->tc_pipe = (int32_t)value;
         return GM_OK;
     default:
         return fail(GM_ERR_INVALID, "unknown option %d", key);

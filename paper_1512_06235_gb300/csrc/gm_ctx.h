@@ -68,7 +68,7 @@ struct CoarseViews {
 // Everything a captured batch depends on besides the contents of its pinned tables and device buffers.
 struct GraphKey {
     int64_t P, Q, n_items;
-    int32_t path, mt;
+    int32_t path, mt, pipe, pad0;
     int64_t grid, stream_cap;
     size_t tab_bytes;
     const void *d_tab, *d_qorder, *d_matchj, *d_counts, *d_off, *rows, *d_ctr, *d_grec, *d_grows, *d_stream, *d_imgs,
@@ -127,6 +127,7 @@ struct gm_ctx {
     int32_t max_inflight = 2;
     int32_t num_sms = 0;
     int32_t mma_mt = 1;             // m16 tiles per query group of the tensor-core path
+    int32_t tc_pipe = 0;            // pipeline geometry of the tcgen05 path (GM_OPT_TC_PIPE)
 
     std::unordered_map<int32_t, gm::ImageSlot *> images;
     std::vector<gm::ImageSlot *> slots;

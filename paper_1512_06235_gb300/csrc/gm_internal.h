@@ -156,9 +156,12 @@ int match_mma_blocks_per_sm(int mt);
 // start, the complement of the first CTA finish and the last CTA finish (globaltimer, ns).
 // whole_image: every pair of the batch has d = inf (every group uses the whole target image): the specialised
 // kernel adds each target's norm through one more K step and keeps the top-2 on the raw accumulator bits.
+// pipe (0 .. kTcPipes - 1) selects the banded kernel's pipeline geometry: (candidate chunks in flight, query groups
+// in flight, positions staged per group) = (6, 3, 1024), (8, 2, 1024) or (4, 4, 512).
+constexpr int kTcPipes = 3;
 cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const int32_t *grows, const int32_t *stream,
                             int64_t item_begin, int64_t item_end, int32_t grid, int32_t *match_j, BatchCounters *ctr,
-                            unsigned long long *cta_time, bool whole_image, cudaStream_t st);
+                            unsigned long long *cta_time, bool whole_image, int32_t pipe, cudaStream_t st);
 // Candidate streams of the tcgen05 groups [item_begin, item_end) of a batch (grec is indexed by item); *used
 // accumulates the stream entries written (zeroed by the caller).
 cudaError_t launch_stream(const ImageDev *imgs, const PairDev *pairs, const int64_t *item_off, int32_t n_pairs,

@@ -44,10 +44,7 @@ namespace {
 
 constexpr int kM = 128;             // queries per group (tensor-memory lanes)
 constexpr int kN = 64;              // candidates per chunk
-constexpr int kStages = 6;          // candidate chunks in flight
 constexpr int kAcc = 4;             // accumulator buffers in tensor memory
-constexpr int kSlots = 3;           // query groups in flight
-constexpr int kPosCap = kTcStagedPositions;   // candidate positions a slot stages in shared memory (multiple of kN)
 constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
 constexpr int kEpiWarps = 8;
 constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;   // worker warps: 8, 10, 11
@@ -60,12 +57,18 @@ constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
 constexpr int kAHalf = kM * 128;                    // one K half of a query tile (bytes)
 constexpr int kBHalf = kN * 128;                    // one K half of a candidate chunk
 
-// Shared-memory layout.  Banded batches: kSlots A tiles, kStages candidate chunks, a 16-byte record per candidate
-// of every chunk, then the control block (with each slot's staged candidate positions).  Whole-image batches
+// Pipeline geometry of one kernel instantiation: candidate chunks in flight (stages), query groups in flight
+// (slots) and the candidate positions a slot stages in shared memory.  The banded kernel comes in the geometries of
+// kTcPipes (gm_autotune times them; GM_OPT_TC_PIPE picks one); the whole-image kernel uses the first.
+//
+// Shared-memory layout.  Banded batches: the slots' A tiles, the candidate chunks, a 16-byte record per candidate of
+// every chunk, then the control block (with each slot's staged candidate positions).  Whole-image batches
 // (kWhole): the records give way to each chunk's fp16 norm rows (32 bytes per candidate, 32-byte swizzle) and the
 // constant A block of the norm step (kM rows of 32 bytes); no positions are staged.
-template <bool kWhole>
-struct TcLayout {
+template <bool W, int STG, int SLT, int POS>
+struct TcCfg {
+    static constexpr bool kWhole = W;
+    static constexpr int kStages = STG, kSlots = SLT, kPosCap = POS;
     static constexpr int kOffA = 0;
     static constexpr int kOffB = kOffA + kSlots * 2 * kAHalf;
     static constexpr int kSide = kWhole ? kN * 32 : kN * 16;   // per stage: norm rows, or records
@@ -73,28 +76,40 @@ struct TcLayout {
     static constexpr int kOffAExt = kOffSide + kStages * kSide;
     static constexpr int kOffCtl = kOffAExt + (kWhole ? kM * 32 : 0);
     static constexpr int kPos = kWhole ? 4 : kPosCap;
+    static constexpr int kMaskWords = kPosCap / 256 < 4 ? 4 : kPosCap / 256;
+    static_assert(kPosCap % kN == 0 && kPosCap % 256 == 0, "staged positions: whole chunks and mask words");
+    static_assert(kMaskWords % 4 == 0, "mask rows: whole 16-byte copies");
 };
 
-template <bool kWhole>
+template <class C>
 struct CtlT {
-    GroupDesc desc[kSlots];          // the group in each slot
-    float2 qxy[kSlots][kM];          // query coordinates
-    int32_t rinfo[kSlots][kM][2];    // original A index (-1: no query), |a'|^2 * 256
-    alignas(16) int32_t aidx[kSlots][kM];   // A rows to gather
-    int32_t merge[kSlots][kM][4];
-    alignas(16) int32_t pos[kSlots][TcLayout<kWhole>::kPos];   // the group's candidate positions (staged)
-    alignas(16) uint32_t smask[kSlots][kPosCap / 256];   // their 32-position slices' quadrant masks, 8 per word
-    uint64_t stage_full[kStages], stage_empty[kStages], acc_full[kAcc], acc_empty[kAcc];
-    uint64_t grp_full[kSlots], grp_empty[kSlots], merge_ready[kSlots], pos_full[kSlots];
+    GroupDesc desc[C::kSlots];          // the group in each slot
+    float2 qxy[C::kSlots][kM];          // query coordinates
+    int32_t rinfo[C::kSlots][kM][2];    // original A index (-1: no query), |a'|^2 * 256
+    alignas(16) int32_t aidx[C::kSlots][kM];   // A rows to gather
+    int32_t merge[C::kSlots][kM][4];
+    alignas(16) int32_t pos[C::kSlots][C::kPos];   // the group's candidate positions (staged)
+    // their 32-position slices' quadrant masks, 8 per word; a row is at least 16 bytes (the set-up copies the
+    // words with one 16-byte cp.async, which needs a 16-byte-aligned destination of that size)
+    alignas(16) uint32_t smask[C::kSlots][C::kMaskWords];
+    uint64_t stage_full[C::kStages], stage_empty[C::kStages], acc_full[kAcc], acc_empty[kAcc];
+    uint64_t grp_full[C::kSlots], grp_empty[C::kSlots], merge_ready[C::kSlots], pos_full[C::kSlots];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
     unsigned long long stat[3];
 };
-template <bool kWhole>
-constexpr int smem_bytes() { return TcLayout<kWhole>::kOffCtl + (int)sizeof(CtlT<kWhole>) + 1024; }
-static_assert(smem_bytes<false>() <= 227 * 1024, "shared memory per CTA");
-static_assert(smem_bytes<true>() <= 227 * 1024, "shared memory per CTA");
-static_assert(kPosCap % kN == 0, "staged positions: whole chunks");
+template <class C>
+constexpr int smem_bytes() { return C::kOffCtl + (int)sizeof(CtlT<C>) + 1024; }
+
+// the banded geometries (index = GM_OPT_TC_PIPE) and the whole-image one
+using TcPipe0 = TcCfg<false, 6, 3, 1024>;
+using TcPipe1 = TcCfg<false, 8, 2, 1024>;
+using TcPipe2 = TcCfg<false, 4, 4, 512>;
+using TcWhole = TcCfg<true, 6, 3, 1024>;
+static_assert(smem_bytes<TcPipe0>() <= 227 * 1024, "shared memory per CTA");
+static_assert(smem_bytes<TcPipe1>() <= 227 * 1024, "shared memory per CTA");
+static_assert(smem_bytes<TcPipe2>() <= 227 * 1024, "shared memory per CTA");
+static_assert(smem_bytes<TcWhole>() <= 227 * 1024, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -207,8 +222,14 @@ __device__ __forceinline__ void mbar_expect_tx_only(uint64_t *bar, uint32_t byte
                  : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+// 16-byte cp.async.  Both addresses must be 16-byte aligned: a request that is not is counted in *bad and not issued
+// (the copy's bytes never arrive; the batch then fails with a device error instead of a misaligned access).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, unsigned long long *bad)
 {
+    if (((dst | (uint32_t)reinterpret_cast<uintptr_t>(src)) & 15u) != 0u) {
+        atomicAdd(bad, 1ull);
+        return;
+    }
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
 }
 
@@ -278,6 +299,7 @@ __device__ __forceinline__ void raise_abort(Ctl &cl, BatchCounters *ctr)
 
 // A banded group whose candidate stream fits the slot (and starts on a 16-byte boundary, as gm_stream.cu lays
 // them out) has its positions staged in shared memory; otherwise the loader reads them from global memory.
+template <int kPosCap>
 __device__ __forceinline__ bool positions_staged(const GroupDesc &d)
 {
     return (d.flags & 3) == 0 && d.total > 0 && d.total <= kPosCap && (d.off & 3) == 0;
@@ -309,8 +331,9 @@ __device__ __forceinline__ void setup_load(SetupData &sd, const GroupDesc *__res
 
 // Writes the group into slot g (the slot must be free): query data, descriptor and the staged candidate positions
 // (cp.async); pos_full completes with the 32 lanes' cp.async arrivals and lane 0's release.
-template <class Ctl>
-__device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g, const int32_t *__restrict__ stream)
+template <int kPosCap, class Ctl>
+__device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g, const int32_t *__restrict__ stream,
+                                            unsigned long long *bad)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -322,13 +345,13 @@ __device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g,
         cl.aidx[g][r] = sd.s4[t] >= 0 ? sd.s4[t] : 0;
     }
     if (lane == 0) cl.desc[g] = sd.d;
-    if (positions_staged(sd.d)) {   // the candidate stream, 16 bytes per copy (the tail of the last copy is unused)
+    if (positions_staged<kPosCap>(sd.d)) {   // the candidate stream, 16 bytes per copy (the tail of the last copy is unused)
         const int4 *src = reinterpret_cast<const int4 *>(stream + sd.d.off);
         const uint32_t dst = smem_u32(cl.pos[g]);
         const int n16 = (sd.d.total + 3) >> 2;
-        for (int k = lane; k < n16; k += 32) cp_async16(dst + 16 * k, src + k);
+        for (int k = lane; k < n16; k += 32) cp_async16(dst + 16 * k, src + k, bad);
         // and the slice masks after them (at most four words, in the stream's own 16-byte-rounded reservation)
-        if (lane == 0) cp_async16(smem_u32(cl.smask[g]), src + n16);
+        if (lane == 0) cp_async16(smem_u32(cl.smask[g]), src + n16, bad);
     }
     cp_async_arrive(&cl.pos_full[g]);
     __syncwarp();
@@ -336,14 +359,15 @@ __device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g,
 }
 
 // ------------------------------------------------------------------------------------------------ kernel
-template <bool kWhole>
+template <class L>
 __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     const TmaMaps *__restrict__ maps, const GroupDesc *__restrict__ gdesc, const int32_t *__restrict__ grows,
     const int32_t *__restrict__ stream, int64_t item_begin, int64_t item_end, int32_t *__restrict__ match_j,
     BatchCounters *__restrict__ ctr, unsigned long long *__restrict__ cta_time)
 {
-    using L = TcLayout<kWhole>;
-    using Ctl = CtlT<kWhole>;
+    using Ctl = CtlT<L>;
+    constexpr bool kWhole = L::kWhole;
+    constexpr int kStages = L::kStages, kSlots = L::kSlots, kPosCap = L::kPosCap;
     const uint64_t t_start = globaltimer();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -409,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             const int g = gk % kSlots;
             if (gk % kWorkers == wk) {
                 if (!mbar_wait_warp(&cl.grp_empty[g], ((gk / kSlots) & 1) ^ 1)) { ok = false; break; }
-                setup_store(cl, nxt, g, stream);
+                setup_store<kPosCap>(cl, nxt, g, stream, &ctr->errors);
                 if (gk + kWorkers < n_groups) setup_load(nxt, gdesc, grows, first + (int64_t)(gk + kWorkers) * stride);
             }
             // the group's descriptor, query rows and staged positions are in the slot once pos_full completes
@@ -435,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             const CUtensorMap *rmap = &maps[dg.b_slot].rec_tile;
             const CUtensorMap *gmap = &maps[dg.b_slot].desc_row;
             const int4 *brec = dg.b_rec;
-            const bool staged = positions_staged(dg);
+            const bool staged = positions_staged<kPosCap>(dg);
             const int32_t *gs = stream + dg.off;
             const int32_t *ps = cl.pos[g];
             for (int c = 0; c < nchunks; ++c, ++ck) {
@@ -478,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                                     &ctr->errors);
                     }
                     const int e = wk + kWorkers * lane;
-                    if (e < kN) cp_async16(rstage + e * 16, brec + (e < lim ? rows[e] : b_n));
+                    if (e < kN) cp_async16(rstage + e * 16, brec + (e < lim ? rows[e] : b_n), &ctr->errors);
                     cp_async_arrive(&cl.stage_full[sb]);
                 }
             }
@@ -537,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             // warp's quadrant holds no keypoint inside any of its rows' bands, and is skipped
             const bool sliced = (gd.flags & 1) == 0;
             const int n_slices = (total + 31) >> 5;   // slices past the last one hold no keypoint
-            const uint32_t *mwords = positions_staged(gd) ? cl.smask[g]
+            const uint32_t *mwords = positions_staged<kPosCap>(gd) ? cl.smask[g]
                                      : reinterpret_cast<const uint32_t *>(stream + gd.off + ((total + 3) & ~3));
             const int out_i = cl.rinfo[g][row][0];
             const float qx = cl.qxy[g][row].x, qy = cl.qxy[g][row].y;
@@ -771,18 +795,30 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     }
 }
 
-template <bool kWhole>
+template <class L>
 cudaError_t prepare()
 {
     static cudaError_t once = [] {
-        cudaError_t e = cudaFuncSetAttribute(match_tc_kernel<kWhole>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem_bytes<kWhole>());
+        cudaError_t e = cudaFuncSetAttribute(match_tc_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_bytes<L>());
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(match_tc_kernel<kWhole>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            e = cudaFuncSetAttribute(match_tc_kernel<L>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared);
         return e;
     }();
     return once;
+}
+
+template <class L>
+cudaError_t launch_cfg(const TmaMaps *maps, const GroupDesc *gdesc, const int32_t *grows, const int32_t *stream,
+                       int64_t item_begin, int64_t item_end, int64_t g, int32_t *match_j, BatchCounters *ctr,
+                       unsigned long long *cta_time, cudaStream_t st)
+{
+    const cudaError_t e = prepare<L>();
+    if (e != cudaSuccess) return e;
+    match_tc_kernel<L><<<(unsigned)g, kThreads, smem_bytes<L>(), st>>>(maps, gdesc, grows, stream, item_begin, item_end,
+                                                                     match_j, ctr, cta_time);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -793,21 +829,20 @@ int match_tc_max_grid_lines() { return kMaxGridLines; }
 
 cudaError_t launch_match_tc(const TmaMaps *maps, const GroupDesc *gdesc, const int32_t *grows, const int32_t *stream,
                             int64_t item_begin, int64_t item_end, int32_t grid, int32_t *match_j, BatchCounters *ctr,
-                            unsigned long long *cta_time, bool whole_image, cudaStream_t st)
+                            unsigned long long *cta_time, bool whole_image, int32_t pipe, cudaStream_t st)
 {
     const int64_t n = item_end - item_begin;
     if (n <= 0) return cudaSuccess;
     const int64_t g = std::max<int64_t>(1, grid > 0 ? std::min<int64_t>(grid, n) : n);
-    cudaError_t e = whole_image ? prepare<true>() : prepare<false>();
-    if (e != cudaSuccess) return e;
     if (whole_image)
-        match_tc_kernel<true><<<(unsigned)g, kThreads, smem_bytes<true>(), st>>>(maps, gdesc, grows, stream, item_begin,
-                                                                               item_end, match_j, ctr, cta_time);
-    else
-        match_tc_kernel<false><<<(unsigned)g, kThreads, smem_bytes<false>(), st>>>(maps, gdesc, grows, stream,
-                                                                                 item_begin, item_end, match_j, ctr,
-                                                                                 cta_time);
-    return cudaGetLastError();
+        return launch_cfg<TcWhole>(maps, gdesc, grows, stream, item_begin, item_end, g, match_j, ctr, cta_time, st);
+    if (pipe == 1)
+        return launch_cfg<TcPipe1>(maps, gdesc, grows, stream, item_begin, item_end, g, match_j, ctr, cta_time, st);
+    if (pipe == 2)
+        return launch_cfg<TcPipe2>(maps, gdesc, grows, stream, item_begin, item_end, g, match_j, ctr, cta_time, st);
+    return launch_cfg<TcPipe0>(maps, gdesc, grows, stream, item_begin, item_end, g, match_j, ctr, cta_time, st);
 }
+
+int match_tc_pipes() { return kTcPipes; }
 
 }  // namespace gm

@@ -40,13 +40,23 @@ constexpr int kSortCap = 1024; // per warp: walked keypoints that are sorted by 
 __constant__ int8_t c_bin[16] = {15, 0, 2, 1, 10, 3, 5, 4, 14, 6, 11, 7, 13, 8, 12, 9};
 __constant__ int8_t c_mask_of_bin[16] = {1, 3, 2, 5, 7, 6, 9, 11, 13, 15, 4, 10, 14, 12, 8, 0};
 
+// The pair that owns work item t (the largest k with item_off[k] <= t), found by the whole warp: each round the 32
+// lanes probe 32 evenly spaced offsets of the remaining range, so a batch of n pairs takes about log32(n) rounds of
+// dependent loads instead of log2(n).  Every lane returns the same pair.
 __device__ __forceinline__ int pair_of_item(const int64_t *__restrict__ item_off, int n_pairs, int64_t t)
 {
-    int lo = 0, hi = n_pairs;
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n_pairs;   // item_off[lo] <= t < item_off[hi] (item_off[n_pairs] is past every item)
     while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (item_off[mid] <= t) lo = mid;
-        else hi = mid;
+        const int span = hi - lo;
+        const int probe = lo + (int)(((int64_t)span * lane) >> 5);   // lane 0 probes lo itself
+        const bool le = __ldg(item_off + probe) <= t;
+        const unsigned bal = __ballot_sync(0xffffffffu, le);
+        const int last = 31 - __clz(bal);   // the last lane whose probe is <= t (lane 0 always is)
+        const int nlo = __shfl_sync(0xffffffffu, probe, last);
+        const int nhi = last < 31 ? __shfl_sync(0xffffffffu, probe, last + 1) : hi;
+        lo = nlo;
+        hi = max(nhi, nlo + 1);
     }
     return lo;
 }
@@ -254,7 +264,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
                     if (run_excl_w[kk + 1] > run_excl_w[kk]) ent[run_excl_w[kk]] = kk;
                 __syncwarp();
                 int line_carry = -1;
-                for (int e0 = 0; e0 < total; e0 += 32) {
+                for (int e0 = 0; e0 < total; e0 += 32) {   // every position's index in the walked order
                     const int e = e0 + lane;
                     int line = e < total ? ent[e] : -1;
 #pragma unroll
@@ -264,18 +274,36 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
                     }
                     line = max(line, line_carry);
                     line_carry = __shfl_sync(0xffffffffu, line, 31);
-                    int bin = 15;
-                    if (e < total) {
-                        const int idx = run_start_w[line] + (e - run_excl_w[line]);
-                        const float2 p = __ldg(pxy + idx);
-                        const unsigned m = colwise ? quad_mask(p.x, p.y, inv_ulim, qtop0, qdtop, qbot0, qdbot)
-                                                   : quad_mask(p.y, p.x, inv_ulim, qtop0, qdtop, qbot0, qdbot);
-                        bin = c_bin[m];
-                        ent[e] = (colwise ? idx : __ldg(B.idx_r + idx)) | (bin << 28);
+                    if (e < total) ent[e] = run_start_w[line] + (e - run_excl_w[line]);
+                }
+                __syncwarp();
+                // masks and bins, eight keypoints per lane in flight at a time
+                constexpr int kU8 = 8;
+                for (int e0 = 0; e0 < total; e0 += 32 * kU8) {
+                    float2 pt[kU8];
+                    int idx[kU8];
+#pragma unroll
+                    for (int u = 0; u < kU8; ++u) {
+                        const int e = e0 + 32 * u + lane;
+                        idx[u] = e < total ? ent[e] : 0;
+                        pt[u] = e < total ? __ldg(pxy + idx[u]) : make_float2(0.0f, 0.0f);
+                        if (!colwise && e < total) idx[u] = __ldg(B.idx_r + idx[u]);
                     }
-                    const unsigned grp = __match_any_sync(0xffffffffu, bin);
-                    if (bin < 15 && (grp & lanemask_lt()) == 0u) bin_cnt[bin] += __popc(grp);
-                    __syncwarp();
+#pragma unroll
+                    for (int u = 0; u < kU8; ++u) {
+                        const int e = e0 + 32 * u + lane;
+                        int bin = 15;
+                        if (e < total) {
+                            const unsigned m = colwise
+                                                   ? quad_mask(pt[u].x, pt[u].y, inv_ulim, qtop0, qdtop, qbot0, qdbot)
+                                                   : quad_mask(pt[u].y, pt[u].x, inv_ulim, qtop0, qdtop, qbot0, qdbot);
+                            bin = c_bin[m];
+                            ent[e] = idx[u] | (bin << 28);
+                        }
+                        const unsigned grp = __match_any_sync(0xffffffffu, bin);
+                        if (bin < 15 && (grp & lanemask_lt()) == 0u) bin_cnt[bin] += __popc(grp);
+                        __syncwarp();
+                    }
                 }
                 // bin starts (exclusive scan in bin order) and the kept total
                 const int cnt = lane < 15 ? bin_cnt[lane] : 0;

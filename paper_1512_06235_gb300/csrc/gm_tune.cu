@@ -103,7 +103,8 @@ bool cache_lookup(const std::string &file, const std::string &sig, gm_tune_resul
         const char *bar = std::strchr(line, '|');
         if (!bar || std::string(line, bar - line) != sig) continue;
         gm_tune_result t{};
-        if (std::sscanf(bar + 1, " path=%d group=%d cell=%d ms=%f", &t.path, &t.mma_group, &t.cell_px, &t.ms) == 4) {
+        if (std::sscanf(bar + 1, " path=%d group=%d cell=%d ms=%f pipe=%d", &t.path, &t.mma_group, &t.cell_px, &t.ms,
+                        &t.tc_pipe) >= 4) {   // entries without a pipeline geometry take the default
             r = t;
             found = true;   // the last entry for a signature wins
         }
@@ -116,7 +117,8 @@ void cache_store(const std::string &file, const std::string &sig, const gm_tune_
 {
     FILE *f = std::fopen(file.c_str(), "a");
     if (!f) return;
-    std::fprintf(f, "%s| path=%d group=%d cell=%d ms=%.4f\n", sig.c_str(), r.path, r.mma_group, r.cell_px, r.ms);
+    std::fprintf(f, "%s| path=%d group=%d cell=%d ms=%.4f pipe=%d\n", sig.c_str(), r.path, r.mma_group, r.cell_px,
+                 r.ms, r.tc_pipe);
     std::fclose(f);
 }
 
@@ -152,6 +154,7 @@ gm_status gm_autotune(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int32_
         ctx->cell_shift = sh;
         ctx->path = r.path;
         ctx->mma_mt = r.mma_group / 16;
+        ctx->tc_pipe = r.tc_pipe >= 0 && r.tc_pipe < kTcPipes ? r.tc_pipe : 0;
         return GM_OK;
     };
     const std::string sig = signature(ctx, n_pairs, pairs);
@@ -168,19 +171,22 @@ gm_status gm_autotune(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int32_
     std::vector<int64_t> off(n_pairs + 1);
     const size_t rows_b = align_up(sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(cap, 1), 256);
     // the match rows of the trial runs go to the tuner's own device buffer (re-binning reuses it later)
-    const int32_t saved_path = ctx->path, saved_mt = ctx->mma_mt, saved_graph = ctx->graph;
+    const int32_t saved_path = ctx->path, saved_mt = ctx->mma_mt, saved_graph = ctx->graph, saved_pipe = ctx->tc_pipe;
     ctx->graph = 0;
     best.ms = INFINITY;
     const int cells[3] = {4, 8, 16};
-    const int cand[4][2] = {{GM_PATH_TC, 16}, {GM_PATH_MMA, 16}, {GM_PATH_MMA, 32}, {GM_PATH_SIMT, 16}};
+    // (path, mma group, tc pipeline geometry)
+    const int cand[6][3] = {{GM_PATH_TC, 16, 0}, {GM_PATH_TC, 16, 1}, {GM_PATH_TC, 16, 2},
+                            {GM_PATH_MMA, 16, 0}, {GM_PATH_MMA, 32, 0}, {GM_PATH_SIMT, 16, 0}};
     gm_status st = GM_OK;
     for (int ci = 0; ci < 3 && st == GM_OK; ++ci) {
         for (int32_t id : ids)
             if ((st = rebin(ctx, ctx->images.at(id), ci + 2)) != GM_OK) break;
         if (st != GM_OK) break;
-        for (int pi = 0; pi < 4 && st == GM_OK; ++pi) {
+        for (int pi = 0; pi < 6 && st == GM_OK; ++pi) {
             ctx->path = cand[pi][0];
             ctx->mma_mt = cand[pi][1] / 16;
+            ctx->tc_pipe = cand[pi][2];
             if ((st = ensure_dev(ctx, ctx->d_tune, rows_b)) != GM_OK) break;
             float ms = INFINITY;
             for (int r = 0; r <= repeats && st == GM_OK; ++r) {   // one untimed warm-up run
@@ -191,6 +197,7 @@ gm_status gm_autotune(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int32_
             if (st == GM_OK && ms < best.ms) {
                 best.path = cand[pi][0];
                 best.mma_group = cand[pi][1];
+                best.tc_pipe = cand[pi][2];
                 best.cell_px = cells[ci];
                 best.ms = ms;
             }
@@ -198,6 +205,7 @@ gm_status gm_autotune(gm_ctx *ctx, int32_t n_pairs, const gm_pair *pairs, int32_
     }
     ctx->path = saved_path;
     ctx->mma_mt = saved_mt;
+    ctx->tc_pipe = saved_pipe;
     ctx->graph = saved_graph;
     if (st != GM_OK) return st;
     best.from_cache = 0;

@@ -21,8 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libgeomatch.so")
 GM_OK, GM_ERR_INVALID, GM_ERR_NOMEM, GM_ERR_BUDGET, GM_ERR_NOT_FOUND, GM_ERR_CUDA, GM_ERR_TIMEOUT, \
     GM_ERR_CANCELLED, GM_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6, -7, -8
 GM_PATH_AUTO, GM_PATH_TC, GM_PATH_MMA, GM_PATH_SIMT = 0, 1, 2, 3
-GM_OPT_PATH, GM_OPT_SCHEDULE, GM_OPT_CELL_PX, GM_OPT_GRAPH, GM_OPT_MMA_GROUP, GM_OPT_STREAM_CAP, GM_OPT_EVICT_LRU = \
-    1, 2, 3, 4, 5, 6, 7
+GM_OPT_PATH, GM_OPT_SCHEDULE, GM_OPT_CELL_PX, GM_OPT_GRAPH, GM_OPT_MMA_GROUP, GM_OPT_STREAM_CAP, GM_OPT_EVICT_LRU, \
+    GM_OPT_TC_PIPE = 1, 2, 3, 4, 5, 6, 7, 8
 
 _STATUS_NAMES = {0: "GM_OK", -1: "GM_ERR_INVALID", -2: "GM_ERR_NOMEM", -3: "GM_ERR_BUDGET", -4: "GM_ERR_NOT_FOUND",
                  -5: "GM_ERR_CUDA", -6: "GM_ERR_TIMEOUT", -7: "GM_ERR_CANCELLED", -8: "GM_ERR_BUSY"}
@@ -79,7 +79,7 @@ class GmApproxStats(ctypes.Structure):
 
 class GmTuneResult(ctypes.Structure):
     _fields_ = [("path", c_i32), ("mma_group", c_i32), ("cell_px", c_i32), ("ms", ctypes.c_float),
-                ("from_cache", c_i32)]
+                ("from_cache", c_i32), ("tc_pipe", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -428,3 +428,29 @@ def test_extreme_descriptors_exact(gm, path):
         np.testing.assert_array_equal(rows[k], want, err_msg=f"pair {k}")
     assert rows[0].shape[0] == 4 and (rows[0][:, 1] == 1).all()   # every zero query picks 81 x 255 + 244
     assert rows[1].shape[0] == 0
+
+
+def test_tc_pipeline_geometries_equal(gm):
+    """The tcgen05 path's three pipeline geometries (GM_OPT_TC_PIPE: 6 chunks / 3 groups / 1024 staged positions,
+    8 / 2 / 1024, 4 / 4 / 512) give identical rows; with 16000-keypoint images at d = 16 px, streams longer than 512
+    positions are read from global memory by the third.  Every 8th pair is checked against the oracle."""
+    sc = scenes.street(n_images=60, n_points=120_000, n_kp=16000, n_pairs=80, d=16.0)
+    with gm.Context(device=0) as ctx:
+        ctx.put_images({k: im for k, im in enumerate(sc.images)})
+        got = []
+        for pipe in range(3):
+            ctx.set_option(gm.GM_OPT_TC_PIPE, pipe)
+            off, m = ctx.match_pairs(sc.pairs)
+            st = ctx.stats()
+            assert st["path_used"] == gm.GM_PATH_TC and st["n_device_errors"] == 0
+            got.append((gm.split_matches(off, m), st["n_candidates"]))
+        with pytest.raises(gm.GeomatchError):
+            ctx.set_option(gm.GM_OPT_TC_PIPE, 3)
+    for rows, nc in got[1:]:
+        assert nc == got[0][1]
+        for k in range(len(sc.pairs)):
+            np.testing.assert_array_equal(rows[k], got[0][0][k], err_msg=f"pair {k}")
+    sample = list(range(0, len(sc.pairs), 8))
+    wants = oracle.match_batch(sc.images, [sc.pairs[k] for k in sample])[0]
+    for k, mj in zip(sample, wants):
+        np.testing.assert_array_equal(got[0][0][k], oracle.matches_from_match_j(mj), err_msg=f"pair {k}")
