@@ -414,10 +414,12 @@ def run_headline(args, gm, dev, local, rank, world, peaks, peak_kind):
         ctx.set_option(gm.GM_OPT_SCHEDULE, args.schedule)
     if args.group != 16:
         ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
+    if args.tc_pipe >= 0:
+        ctx.set_option(gm.GM_OPT_TC_PIPE, args.tc_pipe)
     ctx.put_images({k: sc.images[k] for k in used})
     gp = _pair_array(gm, pairs)
     tune = None
-    if kind == "street" and not args.path and not args.cell and not args.no_autotune:
+    if kind == "street" and not args.path and not args.cell and args.tc_pipe < 0 and not args.no_autotune:
         tune = ctx.autotune(gp, repeats=1)
     if not args.no_graph:
         ctx.set_option(gm.GM_OPT_GRAPH, 1)
@@ -493,8 +495,12 @@ def run_headline(args, gm, dev, local, rank, world, peaks, peak_kind):
         e2e_ctx.set_option(gm.GM_OPT_PATH, tune["path"])
         e2e_ctx.set_option(gm.GM_OPT_MMA_GROUP, tune["mma_group"])
         e2e_ctx.set_option(gm.GM_OPT_CELL_PX, tune["cell_px"])
-    elif args.group != 16:
-        e2e_ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
+        e2e_ctx.set_option(gm.GM_OPT_TC_PIPE, tune["tc_pipe"])
+    else:
+        if args.group != 16:
+            e2e_ctx.set_option(gm.GM_OPT_MMA_GROUP, args.group)
+        if args.tc_pipe >= 0:
+            e2e_ctx.set_option(gm.GM_OPT_TC_PIPE, args.tc_pipe)
     if not args.no_graph:
         e2e_ctx.set_option(gm.GM_OPT_GRAPH, 1)
     batch = gm.make_images([(k, w, h, xy, scl, ds) for k, (w, h, xy, scl, ds) in pinned.items()])
@@ -552,6 +558,7 @@ def run_headline(args, gm, dev, local, rank, world, peaks, peak_kind):
             "config": {"workload": workload, "pairs": len(pairs), "images": len(used),
                        "keypoints": int(sum(sc.images[k].n for k in used)), "band_px": band, "ratio": 0.8,
                        "cell_px": args.cell or (tune["cell_px"] if tune else "auto (4)"), "group": args.group,
+                       "tc_pipe": tune["tc_pipe"] if tune else max(args.tc_pipe, 0),
                        "l2": "flushed between steps (512 MB write)", "path": st["path_used"],
                        "schedule": "persistent batch" if not args.schedule else "one pair per launch",
                        "graph": not args.no_graph and not args.schedule,
@@ -1170,6 +1177,8 @@ def main():
                          "coarse: coarse-stage matching; approx: the paper's approximate search")
     ap.add_argument("--sample", type=int, default=200, help="pairs of the oracle's parity / CPU-baseline sample")
     ap.add_argument("--no-autotune", action="store_true", help="street: keep the library's default setting")
+    ap.add_argument("--tc-pipe", type=int, default=-1,
+                    help="tcgen05 pipeline geometry (GM_OPT_TC_PIPE, 0-2); street: set instead of autotuned")
     ap.add_argument("--no-one-pair", action="store_true", help="skip the one-pair-per-launch comparison")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving leg: Poisson arrivals, req/s")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving leg duration (0: skip)")

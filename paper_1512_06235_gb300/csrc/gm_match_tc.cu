@@ -612,13 +612,19 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                     // distances are the two largest bit patterns.  No records are read: the column of a new best
                     // gives its position (whole-image groups read the image's rows in order).
                     if (nvalid >= 32) {
+                        // two independent top-2 chains (column pairs 4t, 4t + 1 and 4t + 2, 4t + 3), merged after
+                        int b1 = -1, b2 = -1;
 #pragma unroll
-                        for (int jj = 0; jj < 32; jj += 2) {
-                            const int u = (int)v[jj], w = (int)v[jj + 1];
-                            const int lo = min(u, w), hi = max(u, w);
+                        for (int jj = 0; jj < 32; jj += 4) {
+                            const int u = (int)v[jj], w = (int)v[jj + 1], x = (int)v[jj + 2], y = (int)v[jj + 3];
+                            const int lo = min(u, w), hi = max(u, w), lo2 = min(x, y), hi2 = max(x, y);
                             k2 = __vimax3_s32(k2, lo, min(k1, hi));
                             k1 = max(k1, hi);
+                            b2 = __vimax3_s32(b2, lo2, min(b1, hi2));
+                            b1 = max(b1, hi2);
                         }
+                        k2 = __vimax3_s32(k2, b2, min(k1, b1));
+                        k1 = max(k1, b1);
                         cnt += 32;
                     } else if (nvalid > 0) {
 #pragma unroll
@@ -633,9 +639,14 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                     }
                     if (k1 > k1_before) {   // the column of the new best (the lowest one if several are equal)
                         int col = 0;
+                        if (nvalid >= 32) {
 #pragma unroll
-                        for (int jj = 31; jj >= 0; --jj)
-                            if ((int)v[jj] == k1 && jj < nvalid) col = jj;
+                            for (int jj = 31; jj >= 0; --jj) col = (int)v[jj] == k1 ? jj : col;
+                        } else {
+#pragma unroll
+                            for (int jj = 31; jj >= 0; --jj)
+                                if ((int)v[jj] == k1 && jj < nvalid) col = jj;
+                        }
                         j1 = c * kN + 32 * h + col;
                     }
                     __syncwarp();
