@@ -746,7 +746,7 @@ def run_pairs(args, gm, dev, local, peaks, peak_kind):
                        "top_k": k, "pairs_out": n},
             "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
-                         "kernel": "row_kernel (three passes) + transpose",
+                         "kernel": "select_kernel (row counts, rule, sparse row) + pair_kernel (count, emit) + transpose",
                          "algorithmic_bytes": alg, "peak_source": f"{peak_kind} (STREAM-style copy)"},
             "sixteen_thousand": {"workload": "select_pairs_path_16000img_2000000pts", "ms_per_step": ms16,
                                  "selections_per_s": 1e3 / ms16, "observations": int(cams16.size),

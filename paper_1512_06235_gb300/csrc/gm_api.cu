@@ -591,8 +591,8 @@ gm_status gm_destroy(gm_ctx *ctx)
     workspace_free(ctx, ctx->ws2);   // shares ws's stream: freed first
     workspace_free(ctx, ctx->ws);
     for (DevBuf *b : {&ctx->d_imgs, &ctx->d_maps, &ctx->d_stage, &ctx->d_work, &ctx->d_bad, &ctx->d_bitmap, &ctx->d_tune,
-                      &ctx->d_btab, &ctx->d_pairs, &ctx->d_pairs_out, &ctx->d_tracks, &ctx->d_tri, &ctx->d_tri_out,
-                      &ctx->d_coarse_tab, &ctx->d_coarse_stage, &ctx->d_coarse_out, &ctx->d_approx, &ctx->d_segs,
+                      &ctx->d_btab, &ctx->d_pairs, &ctx->d_pairs_out, &ctx->d_pairs_pool, &ctx->d_tracks, &ctx->d_tri,
+                      &ctx->d_tri_out, &ctx->d_coarse_tab, &ctx->d_coarse_stage, &ctx->d_coarse_out, &ctx->d_approx, &ctx->d_segs,
                       &ctx->d_selftest})
         free_dev(ctx, *b);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);

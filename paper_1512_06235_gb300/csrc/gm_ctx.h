@@ -137,7 +137,8 @@ struct gm_ctx {
     size_t bytes_work = 0;          // every DevBuf of the context and of the server slots
 
     gm::Workspace ws;               // synchronous calls
-    gm::DevBuf d_stage, d_work, d_bad, d_bitmap, d_tune, d_btab, d_pairs, d_pairs_out, d_tracks, d_tri, d_tri_out;
+    gm::DevBuf d_stage, d_work, d_bad, d_bitmap, d_tune, d_btab, d_pairs, d_pairs_out, d_pairs_pool, d_tracks, d_tri,
+        d_tri_out;
     gm::Workspace ws2;              // second batch of the coarse stage's preemptive schedule (shares ws's stream)
     gm::DevBuf d_coarse_tab, d_coarse_stage, d_coarse_out;
     gm::DevBuf d_approx;            // gm_match_pairs_approx: every array of one call

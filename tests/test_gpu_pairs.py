@@ -78,3 +78,19 @@ def test_six_thousand_cameras(gm, T, k):
     want = op.select_pairs(6000, off, cams, T, k)
     assert len(want) >= 5000   # every query chose at least its neighbours
     np.testing.assert_array_equal(got, want)
+
+
+def test_wide_camera_range_and_bad_ids(gm):
+    """30000 cameras of which only the first 900 see points: the transpose takes its global-memory path (too many
+    cameras for a block-local histogram) and every row is 30000 counts wide, yet with T >= 0 the idle cameras are
+    never candidates, so the rows equal the oracle's over the 900 cameras.  A camera id past n_cams is an error."""
+    off, cams, _ = scenes.path_visibility(900, 60000, seed=77)
+    want = op.select_pairs(900, off, cams, 3, 40)
+    with gm.Context(device=0) as ctx:
+        np.testing.assert_array_equal(ctx.select_pairs(30000, off, cams, 3, 40), want)
+        np.testing.assert_array_equal(ctx.select_pairs(900, off, cams, 3, 40), want)
+        bad = cams.copy()
+        bad[len(bad) // 2] = 900
+        with pytest.raises(gm.GeomatchError) as e:
+            ctx.select_pairs(900, off, bad, 3, 40)
+        assert e.value.status == gm.GM_ERR_INVALID
