@@ -1,4 +1,5 @@
-// gm_match_tc.cu -- tcgen05 matching path: warp-specialised pipeline of 128-query x 64-candidate tensor-core tiles.
+// gm_match_tc.cu -- tcgen05 matching path: warp-specialised pipeline of 128-query x 64-candidate tensor-core tiles
+// (128-candidate tiles when every pair is matched against the whole target image).
 //
 // App. A Steps 3-4 for groups of 128 consecutive queries of one pair (queries sorted by the position of their
 // epipolar line, so a group's bands nearly coincide; every query keeps its own exact band).  One persistent CTA
@@ -15,7 +16,8 @@
 //       (records by cp.async, completion through cp.async.mbarrier.arrive), the contiguous rows of whole-image
 //       groups by TMA tile loads (64-row boxes, 128-byte swizzle; rows past the image read as NaN records); slots
 //       past the end of a stream get the image's NaN sentinel record;
-//   MMA warp (one elected thread): eight tcgen05.mma.kind::f16 per chunk (M = 128, N = 64, K = 16 each), f32
+//   MMA warp (one elected thread): eight tcgen05.mma.kind::f16 per chunk (M = 128, N = 64, K = 16 each; N = 128
+//       for whole-image batches, whose chunks would otherwise be bound by the issue of the MMAs), f32
 //       accumulation into one of four tensor-memory buffers.  Products are integers of magnitude <= 2^14 and partial
 //       sums <= 2^21 < 2^24, so the accumulator holds the exact integer dot product a'.b';
 //   epilogue warps (8 = 4 lane quadrants x 2 column halves): each thread derives its query's FP32 line and
@@ -43,23 +45,20 @@ namespace gm {
 namespace {
 
 constexpr int kM = 128;             // queries per group (tensor-memory lanes)
-constexpr int kN = 64;              // candidates per chunk
 constexpr int kAcc = 4;             // accumulator buffers in tensor memory
 constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
 constexpr int kEpiWarps = 8;
 constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;   // worker warps: 8, 10, 11
 constexpr int kWorkers = 3;
 constexpr int kThreads = 12 * 32;
-constexpr int kTmemCols = kAcc * kN;
 constexpr int kCounterShards = 64;
 constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
 
 constexpr int kAHalf = kM * 128;                    // one K half of a query tile (bytes)
-constexpr int kBHalf = kN * 128;                    // one K half of a candidate chunk
 
 // Pipeline geometry of one kernel instantiation: candidate chunks in flight (stages), query groups in flight
 // (slots) and the candidate positions a slot stages in shared memory.  The banded kernel comes in the geometries of
-// kTcPipes (gm_autotune times them; GM_OPT_TC_PIPE picks one); the whole-image kernel uses the first.
+// kTcPipes (gm_autotune times them; GM_OPT_TC_PIPE picks one); the whole-image kernel has its own (N = 128).
 //
 // Shared-memory layout.  Banded batches: the slots' A tiles, the candidate chunks, a 16-byte record per candidate of
 // every chunk, then the control block (with each slot's staged candidate positions).  Whole-image batches
@@ -68,6 +67,11 @@ constexpr int kBHalf = kN * 128;                    // one K half of a candidate
 template <bool W, int STG, int SLT, int POS>
 struct TcCfg {
     static constexpr bool kWhole = W;
+    // candidates per chunk: 64 for banded batches (the epilogue skips 32-column slices); 128 for whole-image ones,
+    // whose MMA thread would otherwise spend most of a chunk's time issuing instructions of N = 64
+    static constexpr int kN = W ? 128 : 64;
+    static constexpr int kBHalf = kN * 128;                 // one K half of a candidate chunk
+    static constexpr int kTmemCols = kAcc * kN;             // 256 or 512 columns of tensor memory
     static constexpr int kStages = STG, kSlots = SLT, kPosCap = POS;
     static constexpr int kOffA = 0;
     static constexpr int kOffB = kOffA + kSlots * 2 * kAHalf;
@@ -105,7 +109,7 @@ constexpr int smem_bytes() { return C::kOffCtl + (int)sizeof(CtlT<C>) + 1024; }
 using TcPipe0 = TcCfg<false, 6, 3, 1024>;
 using TcPipe1 = TcCfg<false, 8, 2, 1024>;
 using TcPipe2 = TcCfg<false, 4, 4, 512>;
-using TcWhole = TcCfg<true, 6, 3, 1024>;
+using TcWhole = TcCfg<true, 4, 2, 1024>;   // N = 128 chunks: four stages of 36 KB, two query slots
 static_assert(smem_bytes<TcPipe0>() <= 227 * 1024, "shared memory per CTA");
 static_assert(smem_bytes<TcPipe1>() <= 227 * 1024, "shared memory per CTA");
 static_assert(smem_bytes<TcPipe2>() <= 227 * 1024, "shared memory per CTA");
@@ -259,10 +263,10 @@ __device__ __forceinline__ uint64_t smem_desc32(uint32_t addr)
 
 // Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A = B = f16, K-major, N >> 3 (bits 17-22), M >> 4
 // (bits 24-28).
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
-
+template <int N>
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
 {
+    constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
                  "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
@@ -368,6 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     using Ctl = CtlT<L>;
     constexpr bool kWhole = L::kWhole;
     constexpr int kStages = L::kStages, kSlots = L::kSlots, kPosCap = L::kPosCap;
+    constexpr int kN = L::kN, kBHalf = L::kBHalf, kTmemCols = L::kTmemCols;
     const uint64_t t_start = globaltimer();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -471,13 +476,18 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                     // contiguous rows: TMA tile loads by worker 0 (rows past the image come back as NaN records)
                     if (wk == 0 && lane == 0) {
                         mbar_expect_tx(&cl.stage_full[sb], 2u * kBHalf + (uint32_t)kRecStage);
-                        tma_tile(bstage, dmap, 0, c * kN, &cl.stage_full[sb], 1024u, &ctr->errors);
-                        tma_tile(bstage + kBHalf, dmap, 64, c * kN, &cl.stage_full[sb], 1024u, &ctr->errors);
-                        if (kWhole)   // the norm rows (zeros past the image's end)
-                            tma_tile(rstage, &maps[dg.b_slot].ext_tile, 0, c * kN, &cl.stage_full[sb], 256u,
+#pragma unroll
+                        for (int t = 0; t < kN / 64; ++t) {   // 64-row boxes
+                            const int r0 = c * kN + 64 * t;
+                            tma_tile(bstage + 8192 * t, dmap, 0, r0, &cl.stage_full[sb], 1024u, &ctr->errors);
+                            tma_tile(bstage + kBHalf + 8192 * t, dmap, 64, r0, &cl.stage_full[sb], 1024u,
                                      &ctr->errors);
-                        else
-                            tma_tile(rstage, rmap, 0, c * kN, &cl.stage_full[sb], 128u, &ctr->errors);
+                            if (kWhole)   // the norm rows (zeros past the image's end)
+                                tma_tile(rstage + 2048 * t, &maps[dg.b_slot].ext_tile, 0, r0, &cl.stage_full[sb],
+                                         256u, &ctr->errors);
+                            else
+                                tma_tile(rstage + 1024 * t, rmap, 0, r0, &cl.stage_full[sb], 128u, &ctr->errors);
+                        }
                     } else {
                         mbar_arrive(&cl.stage_full[sb]);
                     }
@@ -529,11 +539,11 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
 #pragma unroll
                     for (int ks = 0; ks < 8; ++ks) {
                         const uint32_t off = (uint32_t)((ks & 3) * 32);
-                        mma_f16(tmem + b * kN, smem_desc(abase + (ks >> 2) * kAHalf + off),
+                        mma_f16<kN>(tmem + b * kN, smem_desc(abase + (ks >> 2) * kAHalf + off),
                                 smem_desc(bbase + (ks >> 2) * kBHalf + off), ks > 0 ? 1u : 0u);
                     }
                     if (kWhole)   // + 2^22 - |b'|^2 / 2: the constant A block against the chunk's norm rows
-                        mma_f16(tmem + b * kN, smem_desc32(smem_u32(base + L::kOffAExt)),
+                        mma_f16<kN>(tmem + b * kN, smem_desc32(smem_u32(base + L::kOffAExt)),
                                 smem_desc32(smem_u32(base + kOffRec + s * kRecStage)), 1u);
                     mma_commit(&cl.stage_empty[s]);
                     mma_commit(&cl.acc_full[b]);
@@ -547,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         // ---------------------------------------------------------------- epilogue warps
         const int quadrant = warp & 3, h = warp >> 2;
         const int row = 32 * quadrant + lane;
-        const uint32_t tmem_lane = tmem + ((uint32_t)(32 * quadrant) << 16) + 32 * h;
+        const uint32_t tmem_lane = tmem + ((uint32_t)(32 * quadrant) << 16) + (kN / 2) * h;   // its column half
         int ck = 0;
         for (int gk = 0; gk < n_groups && !cl.abort_flag; ++gk) {
             const int g = gk % kSlots;
@@ -599,56 +609,64 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                     }
                 }
                 tc_fence_after();
-                uint32_t v[32];
+                uint32_t v[32], v2[kN == 128 ? 32 : 1];
                 tmem_ld32(tmem_lane + b * kN, v);
+                if constexpr (kN == 128) tmem_ld32(tmem_lane + b * kN + 32, v2);   // the half's second 32 columns
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&cl.acc_empty[b]);
                 const int k1_before = k1;
-                const int nvalid = total - c * kN - 32 * h;   // real columns of this half-chunk (may exceed 32)
+                const int nvalid = total - c * kN - (kN / 2) * h;   // real columns of this half-chunk (may exceed 32)
                 if (kWhole) {
                     // the accumulator holds 2^22 + a'.b' - |b'|^2 / 2 = 2^22 + (|a'|^2 - D) / 2, exactly (half-
                     // integers below 2^23) and positive, so its bits order like its values: the two smallest
                     // distances are the two largest bit patterns.  No records are read: the column of a new best
                     // gives its position (whole-image groups read the image's rows in order).
-                    if (nvalid >= 32) {
-                        // two independent top-2 chains (column pairs 4t, 4t + 1 and 4t + 2, 4t + 3), merged after
-                        int b1 = -1, b2 = -1;
+                    // one 32-column block: nv real columns (may exceed 32) starting at chunk column col0
+                    auto whole_block = [&](const uint32_t (&vv)[32], int nv, int col0) {
+                        const int kb = k1;
+                        if (nv >= 32) {
+                            // two independent top-2 chains (column pairs 4t, 4t + 1 and 4t + 2, 4t + 3), merged after
+                            int b1 = -1, b2 = -1;
 #pragma unroll
-                        for (int jj = 0; jj < 32; jj += 4) {
-                            const int u = (int)v[jj], w = (int)v[jj + 1], x = (int)v[jj + 2], y = (int)v[jj + 3];
-                            const int lo = min(u, w), hi = max(u, w), lo2 = min(x, y), hi2 = max(x, y);
-                            k2 = __vimax3_s32(k2, lo, min(k1, hi));
-                            k1 = max(k1, hi);
-                            b2 = __vimax3_s32(b2, lo2, min(b1, hi2));
-                            b1 = max(b1, hi2);
-                        }
-                        k2 = __vimax3_s32(k2, b2, min(k1, b1));
-                        k1 = max(k1, b1);
-                        cnt += 32;
-                    } else if (nvalid > 0) {
-#pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            if (jj < nvalid) {
-                                const int x = (int)v[jj];
-                                k2 = max(k2, min(k1, x));
-                                k1 = max(k1, x);
+                            for (int jj = 0; jj < 32; jj += 4) {
+                                const int u = (int)vv[jj], w = (int)vv[jj + 1], x = (int)vv[jj + 2],
+                                          y = (int)vv[jj + 3];
+                                const int lo = min(u, w), hi = max(u, w), lo2 = min(x, y), hi2 = max(x, y);
+                                k2 = __vimax3_s32(k2, lo, min(k1, hi));
+                                k1 = max(k1, hi);
+                                b2 = __vimax3_s32(b2, lo2, min(b1, hi2));
+                                b1 = max(b1, hi2);
                             }
-                        }
-                        cnt += nvalid;
-                    }
-                    if (k1 > k1_before) {   // the column of the new best (the lowest one if several are equal)
-                        int col = 0;
-                        if (nvalid >= 32) {
+                            k2 = __vimax3_s32(k2, b2, min(k1, b1));
+                            k1 = max(k1, b1);
+                            cnt += 32;
+                        } else if (nv > 0) {
 #pragma unroll
-                            for (int jj = 31; jj >= 0; --jj) col = (int)v[jj] == k1 ? jj : col;
-                        } else {
-#pragma unroll
-                            for (int jj = 31; jj >= 0; --jj)
-                                if ((int)v[jj] == k1 && jj < nvalid) col = jj;
+                            for (int jj = 0; jj < 32; ++jj) {
+                                if (jj < nv) {
+                                    const int x = (int)vv[jj];
+                                    k2 = max(k2, min(k1, x));
+                                    k1 = max(k1, x);
+                                }
+                            }
+                            cnt += nv;
                         }
-                        j1 = c * kN + 32 * h + col;
-                    }
+                        if (k1 > kb) {   // the column of the new best (the lowest one if several are equal)
+                            int col = 0;
+                            if (nv >= 32) {
+#pragma unroll
+                                for (int jj = 31; jj >= 0; --jj) col = (int)vv[jj] == k1 ? jj : col;
+                            } else {
+#pragma unroll
+                                for (int jj = 31; jj >= 0; --jj)
+                                    if ((int)vv[jj] == k1 && jj < nv) col = jj;
+                            }
+                            j1 = c * kN + col0 + col;
+                        }
+                    };
+                    whole_block(v, nvalid, (kN / 2) * h);
+                    if constexpr (kN == 128) whole_block(v2, nvalid - 32, 64 * h + 32);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&cl.stage_empty[s]);
                     continue;

@@ -17,7 +17,7 @@
 // order of a row's candidates never changes its result (the top-2 keys are unique up to equal distances, which the
 // strict ratio test rejects).
 //
-// One warp per group, four groups per block.  Space is reserved with one atomic per block; a stream that would
+// One warp per group, four groups per block.  Space is reserved with one atomic per warp; a stream that would
 // overflow the buffer marks its group (the caller grows the buffer and runs the batch again).  Groups that contain
 // a whole-image query (d = inf) or an FP64-only line use the whole image and store no stream.
 #include <cstdint>
@@ -36,9 +36,19 @@ constexpr int kBinInts = 48;   // per warp: bin counts [16], bin starts [16], bi
 constexpr int kSortCap = 1024; // per warp: walked keypoints that are sorted by quadrant mask (longer walks keep walk order)
 
 // Stream order of the 15 nonzero quadrant masks (by the centre, then the width of the quadrant range they span):
-// bin r holds the keypoints whose mask is c_mask_of_bin[r]; c_bin[m] is the bin of mask m (15: dropped).
-__constant__ int8_t c_bin[16] = {15, 0, 2, 1, 10, 3, 5, 4, 14, 6, 11, 7, 13, 8, 12, 9};
-__constant__ int8_t c_mask_of_bin[16] = {1, 3, 2, 5, 7, 6, 9, 11, 13, 15, 4, 10, 14, 12, 8, 0};
+// bin r holds the keypoints whose mask is mask_of_bin(r); bin_of(m) is the bin of mask m (15: dropped).  Both
+// tables are 16 nibbles of one 64-bit constant, so that a lookup with a different index in every lane is a shift.
+constexpr int kBinOfMask[16] = {15, 0, 2, 1, 10, 3, 5, 4, 14, 6, 11, 7, 13, 8, 12, 9};
+constexpr int kMaskOfBin[16] = {1, 3, 2, 5, 7, 6, 9, 11, 13, 15, 4, 10, 14, 12, 8, 0};
+constexpr unsigned long long pack_nibbles(const int (&t)[16])
+{
+    unsigned long long v = 0ull;
+    for (int i = 0; i < 16; ++i) v |= (unsigned long long)t[i] << (4 * i);
+    return v;
+}
+constexpr unsigned long long kBinPacked = pack_nibbles(kBinOfMask), kMaskPacked = pack_nibbles(kMaskOfBin);
+__device__ __forceinline__ int bin_of(unsigned m) { return (int)((kBinPacked >> (4 * m)) & 15ull); }
+__device__ __forceinline__ unsigned mask_of_bin(int r) { return (unsigned)((kMaskPacked >> (4 * r)) & 15ull); }
 
 // The pair that owns work item t (the largest k with item_off[k] <= t), found by the whole warp: each round the 32
 // lanes probe 32 evenly spaced offsets of the remaining range, so a batch of n pairs takes about log32(n) rounds of
@@ -89,8 +99,6 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
     int32_t *const run_excl_w = run_start_w + max_lines;
     int32_t *const bin_cnt = run_excl_w + max_lines + 1, *const bin_start = bin_cnt + 16, *const bin_cur = bin_cnt + 32;
     int32_t *const ent = bin_cnt + kBinInts;
-    __shared__ int32_t wtotal[kWarps];
-    __shared__ unsigned long long wbase[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t item = item_begin + (int64_t)blockIdx.x * kWarps + warp;
     const bool active = item < item_end;
@@ -297,7 +305,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
                             const unsigned m = colwise
                                                    ? quad_mask(pt[u].x, pt[u].y, inv_ulim, qtop0, qdtop, qbot0, qdbot)
                                                    : quad_mask(pt[u].y, pt[u].x, inv_ulim, qtop0, qdtop, qbot0, qdbot);
-                            bin = c_bin[m];
+                            bin = bin_of(m);
                             ent[e] = idx[u] | (bin << 28);
                         }
                         const unsigned grp = __match_any_sync(0xffffffffu, bin);
@@ -325,23 +333,14 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
             __syncwarp();
         }
     }
-    // reserve the block's space with one atomic; every stream starts on a 16-byte boundary (positions and mask
-    // words are each rounded up to four entries) so that the matcher can stage it with 16-byte copies
-    if (lane == 0) wtotal[warp] = (active && !full) ? ((kept + 3) & ~3) + ((n_words + 3) & ~3) : 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long sum = 0;
-        for (int w = 0; w < kWarps; ++w) sum += (unsigned long long)wtotal[w];
-        unsigned long long b = sum ? atomicAdd(used, sum) : 0ull;
-        for (int w = 0; w < kWarps; ++w) {
-            wbase[w] = b;
-            b += (unsigned long long)wtotal[w];
-        }
-    }
-    __syncthreads();
+    // reserve the warp's space with one atomic (no wait for the block's other warps, whose walks differ in
+    // length); every stream starts on a 16-byte boundary (positions and mask words are each rounded up to four
+    // entries) so that the matcher can stage it with 16-byte copies
     if (!active) return;
-    const unsigned long long off = wbase[warp];
     const int reserve = ((kept + 3) & ~3) + ((n_words + 3) & ~3);
+    unsigned long long off = 0ull;
+    if (lane == 0 && !full && reserve > 0) off = atomicAdd(used, (unsigned long long)reserve);
+    off = __shfl_sync(0xffffffffu, off, 0);
     const bool overflow = !full && off + (unsigned long long)reserve > (unsigned long long)capacity;
     if (lane == 0) {
         const PairDev &P = *Pp;
@@ -403,20 +402,21 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
     unsigned long long elems = 0;
     uint32_t *words = reinterpret_cast<uint32_t *>(dst + ((kept + 3) & ~3));
     for (int w = lane; w < n_words; w += 32) {
+        // the word's eight slices [8 w, 8 w + 8): every bin ORs its mask into the slices its range overlaps
+        const int s_end = min(8 * w + 8, n_slices);
         uint32_t word = 0u;
-        for (int j = 0; j < 8; ++j) {
-            const int sl = 8 * w + j;
-            if (sl >= n_slices) break;
-            const int lo = 32 * sl, hi = min(32 * sl + 32, kept);
-            unsigned m = sorted ? 0u : 0xfu;
-            if (sorted)
-                for (int bin = 0; bin < 15; ++bin) {
-                    const int b0 = bin_start[bin], b1 = b0 + bin_cnt[bin];
-                    if (b0 < hi && b1 > lo) m |= (unsigned)c_mask_of_bin[bin];
-                }
-            word |= m << (4 * j);
-            elems += (unsigned long long)__popc(m) * 32ull * 32ull;
+        if (!sorted) {
+            for (int sl = 8 * w; sl < s_end; ++sl) word |= 0xfu << (4 * (sl - 8 * w));
+        } else {
+            for (int bin = 0; bin < 15; ++bin) {
+                const int b0 = bin_start[bin], n = bin_cnt[bin];
+                if (n == 0) continue;
+                const int s0 = max(b0 >> 5, 8 * w), s1 = min((b0 + n - 1) >> 5, s_end - 1);
+                for (int sl = s0; sl <= s1; ++sl) word |= mask_of_bin(bin) << (4 * (sl - 8 * w));
+            }
         }
+        for (int sl = 8 * w; sl < s_end; ++sl)
+            elems += (unsigned long long)__popc((word >> (4 * (sl - 8 * w))) & 0xfu) * 32ull * 32ull;
         words[w] = word;
     }
 #pragma unroll
