@@ -391,7 +391,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         cl.stat[0] = cl.stat[1] = cl.stat[2] = 0ull;
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&cl.stage_full[s], 32 * kWorkers);   // every lane of every worker (+ tile bytes)
-            mbar_init(&cl.stage_empty[s], 1 + kEpiWarps);  // the MMA commit, the epilogue warps (records read)
+            // the MMA commit and the epilogue warps (records read); whole-image epilogues read no stage, so the MMA
+            // alone frees it and the loads run ahead of the epilogue by the accumulator buffers
+            mbar_init(&cl.stage_empty[s], kWhole ? 1 : 1 + kEpiWarps);
         }
         for (int b = 0; b < kAcc; ++b) {
             mbar_init(&cl.acc_full[b], 1);
@@ -667,8 +669,6 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                     };
                     whole_block(v, nvalid, (kN / 2) * h);
                     if constexpr (kN == 128) whole_block(v2, nvalid - 32, 64 * h + 32);
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&cl.stage_empty[s]);
                     continue;
                 }
                 if (!mbar_wait_warp(&cl.stage_full[s], (ck / kStages) & 1)) { ok = false; break; }   // records
