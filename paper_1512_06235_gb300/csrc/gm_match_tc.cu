@@ -20,7 +20,8 @@
 //       for whole-image batches, whose chunks would otherwise be bound by the issue of the MMAs), f32
 //       accumulation into one of four tensor-memory buffers.  Products are integers of magnitude <= 2^14 and partial
 //       sums <= 2^21 < 2^24, so the accumulator holds the exact integer dot product a'.b';
-//   epilogue warps (8 = 4 lane quadrants x 2 column halves): each thread derives its query's FP32 line and
+//   epilogue warps (4 lane quadrants x the chunk's 32-column blocks: 8, or 16 for whole-image batches): each thread
+//       derives its query's FP32 line and
 //       exact-decision thresholds (gm_band.cuh), then per chunk tcgen05.ld of 32 accumulator columns and per element
 //       the FP32 band test, D = |a'|^2 + |b'|^2 - 2 a'.b' packed with the column into one int32 key and a masked
 //       running top-2 (two interleaved accumulators, no branch in the loop); the rare elements inside the FP32 error
@@ -47,10 +48,6 @@ namespace {
 constexpr int kM = 128;             // queries per group (tensor-memory lanes)
 constexpr int kAcc = 4;             // accumulator buffers in tensor memory
 constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
-constexpr int kEpiWarps = 8;
-constexpr int kLoaderWarp = 8, kMmaWarp = 9, kSetupWarp0 = 10;   // worker warps: 8, 10, 11
-constexpr int kWorkers = 3;
-constexpr int kThreads = 12 * 32;
 constexpr int kCounterShards = 64;
 constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
 
@@ -72,6 +69,14 @@ struct TcCfg {
     static constexpr int kN = W ? 128 : 64;
     static constexpr int kBHalf = kN * 128;                 // one K half of a candidate chunk
     static constexpr int kTmemCols = kAcc * kN;             // 256 or 512 columns of tensor memory
+    // warp roles: epilogue warps 0 .. kEpiWarps - 1 (4 lane quadrants x kN / 32 column blocks of 32), then the
+    // first worker, the MMA warp and the other two workers.  Whole-image batches: 16 epilogue warps, 20 warps of at
+    // most 102 registers; banded: 8, 12 warps of at most 168 registers
+    static constexpr int kEpiWarps = 4 * (kN / 32);
+    static constexpr int kWorkers = 3;
+    static constexpr int kLoaderWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kSetupWarp0 = kEpiWarps + 2;
+    static constexpr int kThreads = 32 * (kEpiWarps + 1 + kWorkers);
+    static constexpr int kMergeParts = kEpiWarps / 4 - 1;   // column blocks that hand their top-2 to block 0
     static constexpr int kStages = STG, kSlots = SLT, kPosCap = POS;
     static constexpr int kOffA = 0;
     static constexpr int kOffB = kOffA + kSlots * 2 * kAHalf;
@@ -91,7 +96,7 @@ struct CtlT {
     float2 qxy[C::kSlots][kM];          // query coordinates
     int32_t rinfo[C::kSlots][kM][2];    // original A index (-1: no query), |a'|^2 * 256
     alignas(16) int32_t aidx[C::kSlots][kM];   // A rows to gather
-    int32_t merge[C::kSlots][kM][4];
+    int32_t merge[C::kSlots][kM][C::kMergeParts][4];
     alignas(16) int32_t pos[C::kSlots][C::kPos];   // the group's candidate positions (staged)
     // their 32-position slices' quadrant masks, 8 per word; a row is at least 16 bytes (the set-up copies the
     // words with one 16-byte cp.async, which needs a 16-byte-aligned destination of that size)
@@ -109,7 +114,7 @@ constexpr int smem_bytes() { return C::kOffCtl + (int)sizeof(CtlT<C>) + 1024; }
 using TcPipe0 = TcCfg<false, 6, 3, 1024>;
 using TcPipe1 = TcCfg<false, 8, 2, 1024>;
 using TcPipe2 = TcCfg<false, 4, 4, 512>;
-using TcWhole = TcCfg<true, 4, 2, 1024>;   // N = 128 chunks: four stages of 36 KB, two query slots
+using TcWhole = TcCfg<true, 3, 2, 1024>;   // N = 128 chunks: three stages of 36 KB, two query slots
 static_assert(smem_bytes<TcPipe0>() <= 227 * 1024, "shared memory per CTA");
 static_assert(smem_bytes<TcPipe1>() <= 227 * 1024, "shared memory per CTA");
 static_assert(smem_bytes<TcPipe2>() <= 227 * 1024, "shared memory per CTA");
@@ -364,7 +369,7 @@ __device__ __forceinline__ void setup_store(Ctl &cl, const SetupData &sd, int g,
 
 // ------------------------------------------------------------------------------------------------ kernel
 template <class L>
-__global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
+__global__ void __launch_bounds__(L::kThreads, 1) match_tc_kernel(
     const TmaMaps *__restrict__ maps, const GroupDesc *__restrict__ gdesc, const int32_t *__restrict__ grows,
     const int32_t *__restrict__ stream, int64_t item_begin, int64_t item_end, int32_t *__restrict__ match_j,
     BatchCounters *__restrict__ ctr, unsigned long long *__restrict__ cta_time)
@@ -373,6 +378,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
     constexpr bool kWhole = L::kWhole;
     constexpr int kStages = L::kStages, kSlots = L::kSlots, kPosCap = L::kPosCap;
     constexpr int kN = L::kN, kBHalf = L::kBHalf, kTmemCols = L::kTmemCols;
+    constexpr int kEpiWarps = L::kEpiWarps, kWorkers = L::kWorkers, kLoaderWarp = L::kLoaderWarp,
+                  kMmaWarp = L::kMmaWarp, kSetupWarp0 = L::kSetupWarp0;
     const uint64_t t_start = globaltimer();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -403,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
             mbar_init(&cl.pos_full[g], 33);   // the setup warp's 32 cp.async arrivals + its release
             mbar_init(&cl.grp_full[g], kWorkers);   // each worker's arrival with its share of the A tile's bytes
             mbar_init(&cl.grp_empty[g], 1 + kEpiWarps + kWorkers);   // MMA commit, epilogue warps, workers
-            mbar_init(&cl.merge_ready[g], kEpiWarps / 2);
+            mbar_init(&cl.merge_ready[g], 4 * L::kMergeParts);   // the warps of column blocks 1 ..
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -454,8 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 const int nops = (2 * kM / 4 - wk + kWorkers - 1) / kWorkers;
                 if (lane == 0) mbar_expect_tx(&cl.grp_full[g], (uint32_t)nops * 512u);
                 __syncwarp();
-                const int o = wk + kWorkers * lane;
-                if (o < 2 * kM / 4) {
+                for (int o = wk + kWorkers * lane; o < 2 * kM / 4; o += 32 * kWorkers) {
                     const int q = o & 31, hh = o >> 5;
                     const int4 r4 = *reinterpret_cast<const int4 *>(cl.aidx[g] + 4 * q);
                     tma_gather4(smem_u32(base + kOffA + g * 2 * kAHalf + hh * kAHalf + q * 512),
@@ -559,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
         // ---------------------------------------------------------------- epilogue warps
         const int quadrant = warp & 3, h = warp >> 2;
         const int row = 32 * quadrant + lane;
-        const uint32_t tmem_lane = tmem + ((uint32_t)(32 * quadrant) << 16) + (kN / 2) * h;   // its column half
+        const uint32_t tmem_lane = tmem + ((uint32_t)(32 * quadrant) << 16) + 32 * h;   // its 32-column block
         int ck = 0;
         for (int gk = 0; gk < n_groups && !cl.abort_flag; ++gk) {
             const int g = gk % kSlots;
@@ -600,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 const int s = ck % kStages, b = ck % kAcc;
                 if (!mbar_wait_warp(&cl.acc_full[b], (ck / kAcc) & 1)) { ok = false; break; }
                 if (sliced) {
-                    const int sl = 2 * c + h;
+                    const int sl = (kN / 32) * c + h;
                     if (sl >= n_slices || ((mwords[sl >> 3] >> (4 * (sl & 7) + quadrant)) & 1u) == 0u) {
                         __syncwarp();
                         if (lane == 0) {
@@ -611,14 +617,13 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                     }
                 }
                 tc_fence_after();
-                uint32_t v[32], v2[kN == 128 ? 32 : 1];
+                uint32_t v[32];
                 tmem_ld32(tmem_lane + b * kN, v);
-                if constexpr (kN == 128) tmem_ld32(tmem_lane + b * kN + 32, v2);   // the half's second 32 columns
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&cl.acc_empty[b]);
                 const int k1_before = k1;
-                const int nvalid = total - c * kN - (kN / 2) * h;   // real columns of this half-chunk (may exceed 32)
+                const int nvalid = total - c * kN - 32 * h;   // real columns of this block (may exceed 32)
                 if (kWhole) {
                     // the accumulator holds 2^22 + a'.b' - |b'|^2 / 2 = 2^22 + (|a'|^2 - D) / 2, exactly (half-
                     // integers below 2^23) and positive, so its bits order like its values: the two smallest
@@ -667,8 +672,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                             j1 = c * kN + col0 + col;
                         }
                     };
-                    whole_block(v, nvalid, (kN / 2) * h);
-                    if constexpr (kN == 128) whole_block(v2, nvalid - 32, 64 * h + 32);
+                    whole_block(v, nvalid, 32 * h);
                     continue;
                 }
                 if (!mbar_wait_warp(&cl.stage_full[s], (ck / kStages) & 1)) { ok = false; break; }   // records
@@ -756,32 +760,39 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(
                 if (lane == 0) mbar_arrive(&cl.stage_empty[s]);
             }
             if (!ok) { raise_abort(cl, ctr); break; }
-            // merge the two column halves of every row, then the ratio test
-            if (h == 1) {
-                int32_t *mg = cl.merge[g][row];
+            // merge the column blocks of every row (block 0 takes the others' top-2 in column order), then the
+            // ratio test
+            if (h > 0) {
+                int32_t *mg = cl.merge[g][row][h - 1];
                 mg[0] = k1; mg[1] = k2; mg[2] = j1; mg[3] = cnt;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&cl.merge_ready[g]);
             } else {
                 if (!mbar_wait_warp(&cl.merge_ready[g], (gk / kSlots) & 1)) { raise_abort(cl, ctr); break; }
-                const int32_t *mg = cl.merge[g][row];
-                const int ok1 = mg[0], ok2 = mg[1], oj1 = mg[2];
+#pragma unroll
+                for (int part = 0; part < L::kMergeParts; ++part) {
+                    const int32_t *mg = cl.merge[g][row][part];
+                    const int ok1 = mg[0], ok2 = mg[1], oj1 = mg[2];
+                    if (kWhole) {   // largest bits first
+                        const int nk2 = max(min(k1, ok1), max(k2, ok2));
+                        if (ok1 > k1) { k1 = ok1; j1 = oj1; }
+                        k2 = nk2;
+                    } else {
+                        const int nk2 = min(max(k1, ok1), min(k2, ok2));
+                        if (ok1 < k1) { k1 = ok1; j1 = oj1; }
+                        k2 = nk2;
+                    }
+                    cnt += mg[3];
+                }
                 int64_t D1, D2;
-                if (kWhole) {   // largest bits first; D = |a'|^2 + 2^23 - 2 (the accumulator's value)
-                    const int nk2 = max(min(k1, ok1), max(k2, ok2));
-                    if (ok1 > k1) { k1 = ok1; j1 = oj1; }
-                    k2 = nk2;
+                if (kWhole) {   // D = |a'|^2 + 2^23 - 2 (the accumulator's value)
                     const int64_t na = cl.rinfo[g][row][1] >> 8;
                     D1 = na + 8388608 - (int64_t)(2.0f * __int_as_float(k1));
                     D2 = na + 8388608 - (int64_t)(2.0f * __int_as_float(k2));
                 } else {
-                    const int nk2 = min(max(k1, ok1), min(k2, ok2));
-                    if (ok1 < k1) { k1 = ok1; j1 = oj1; }
-                    k2 = nk2;
                     D1 = k1 >> 8;
                     D2 = k2 >> 8;
                 }
-                cnt += mg[3];
                 if (out_i >= 0) {
                     const int64_t pp = gd.p, qq = gd.q;
                     int outj = -1;
@@ -845,7 +856,7 @@ cudaError_t launch_cfg(const TmaMaps *maps, const GroupDesc *gdesc, const int32_
 {
     const cudaError_t e = prepare<L>();
     if (e != cudaSuccess) return e;
-    match_tc_kernel<L><<<(unsigned)g, kThreads, smem_bytes<L>(), st>>>(maps, gdesc, grows, stream, item_begin, item_end,
+    match_tc_kernel<L><<<(unsigned)g, L::kThreads, smem_bytes<L>(), st>>>(maps, gdesc, grows, stream, item_begin, item_end,
                                                                      match_j, ctr, cta_time);
     return cudaGetLastError();
 }

@@ -29,7 +29,7 @@ namespace gm {
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kMinBlocks = 1;   // resident blocks per SM that __launch_bounds__ asks the register allocation for
+constexpr int kMinBlocks = 6;   // resident blocks per SM that __launch_bounds__ asks the register allocation for (80 registers)
 constexpr int kG = kTcQueriesPerItem;   // queries per group
 constexpr int kMaxLines = 1024;
 constexpr int kBinInts = 48;   // per warp: bin counts [16], bin starts [16], bin cursors [16]
