@@ -170,6 +170,8 @@ __global__ void batch_scatter_kernel(const BucketJob *__restrict__ jobs, const i
 
 // Descriptors in cell order: eight lanes per keypoint, 16 bytes each (a warp moves four rows per load, so that
 // more bytes are in flight when the rows are read from page-locked host memory), recentred int8, fp16 and the norms.
+// The input rows are read in their own order (sequential reads over the host link when they are read in place) and
+// written to their cell-order positions (inv_perm, from the scatter before).
 __global__ void batch_desc_kernel(const BucketJob *__restrict__ jobs, const int64_t *__restrict__ kp_prefix, int K,
                                   int64_t n_total)
 {
@@ -182,8 +184,8 @@ __global__ void batch_desc_kernel(const BucketJob *__restrict__ jobs, const int6
     if (live) {
         const int k = find_job(kp_prefix, K, g);
         J = &jobs[k];
-        row = (int)(g - J->kp_base);
-        const int src = J->perm[row];
+        const int src = (int)(g - J->kp_base);
+        row = J->inv_perm[src];
         uint4 w = reinterpret_cast<const uint4 *>(J->desc_raw + (int64_t)src * kDim)[part];
         w.x ^= 0x80808080u; w.y ^= 0x80808080u; w.z ^= 0x80808080u; w.w ^= 0x80808080u;
         reinterpret_cast<uint4 *>(J->desc + (int64_t)row * kDim)[part] = w;
