@@ -50,6 +50,7 @@ constexpr int kAcc = 4;             // accumulator buffers in tensor memory
 constexpr int kMaxGridLines = 1024; // grid lines a group walk may cross (gm_stream.cu)
 constexpr int kCounterShards = 64;
 constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
+constexpr int kFilterMinTotal = 4096;   // whole-image targets from this size test each block's maximum first
 
 constexpr int kAHalf = kM * 128;                    // one K half of a query tile (bytes)
 
@@ -632,7 +633,20 @@ __global__ void __launch_bounds__(L::kThreads, 1) match_tc_kernel(
                     // one 32-column block: nv real columns (may exceed 32) starting at chunk column col0
                     auto whole_block = [&](const uint32_t (&vv)[32], int nv, int col0) {
                         const int kb = k1;
-                        if (nv >= 32) {
+                        // large targets: the block's largest value first; when no row of the warp beats its best
+                        // with it, the block can only raise the second best (0.5 operations per element instead of
+                        // 2.5).  A row's best improves in about 32 / t of its t-th block, so the test pays once a row
+                        // has many blocks (small targets, such as the coarse stage's views, skip it)
+                        const bool filter = total >= kFilterMinTotal;
+                        int bm = -1;
+                        if (filter && nv >= 32) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; jj += 2) bm = __vimax3_s32(bm, (int)vv[jj], (int)vv[jj + 1]);
+                        }
+                        if (filter && nv >= 32 && !__any_sync(0xffffffffu, bm > k1)) {
+                            k2 = max(k2, bm);
+                            cnt += 32;
+                        } else if (nv >= 32) {
                             // two independent top-2 chains (column pairs 4t, 4t + 1 and 4t + 2, 4t + 3), merged after
                             int b1 = -1, b2 = -1;
 #pragma unroll
