@@ -29,6 +29,7 @@ namespace gm {
 namespace {
 
 constexpr int kWarps = 4;
+constexpr int kCounterShards = 64;   // the batch's counters are 64 shards (the host sums them): one per block mod 64
 constexpr int kMinBlocks = 6;   // resident blocks per SM that __launch_bounds__ asks the register allocation for (80 registers)
 constexpr int kG = kTcQueriesPerItem;   // queries per group
 constexpr int kMaxLines = 1024;
@@ -367,9 +368,10 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
         r.H = (float)B.height;
         r.qoff = P.qoff;
         gdesc[item] = r;
-        if (overflow) atomicAdd(&ctr->overflow, 1ull);
-        else if (!full && kept > kTcStagedPositions) atomicAdd(&ctr->unstaged, 1ull);
-        if (full) atomicAdd(&ctr->examined, (unsigned long long)total * kG);
+        BatchCounters *const cs = ctr + (blockIdx.x % kCounterShards);
+        if (overflow) atomicAdd(&cs->overflow, 1ull);
+        else if (!full && kept > kTcStagedPositions) atomicAdd(&cs->unstaged, 1ull);
+        if (full) atomicAdd(&cs->examined, (unsigned long long)total * kG);
     }
     if (full || overflow || kept == 0) return;
     const ImageDev &B = *Bp;
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) stream_kernel(
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) elems += __shfl_xor_sync(0xffffffffu, elems, o);
-    if (lane == 0) atomicAdd(&ctr->examined, elems);
+    if (lane == 0) atomicAdd(&ctr[blockIdx.x % kCounterShards].examined, elems);
 }
 
 }  // namespace
