@@ -454,3 +454,33 @@ def test_tc_pipeline_geometries_equal(gm):
     wants = oracle.match_batch(sc.images, [sc.pairs[k] for k in sample])[0]
     for k, mj in zip(sample, wants):
         np.testing.assert_array_equal(got[0][0][k], oracle.matches_from_match_j(mj), err_msg=f"pair {k}")
+
+
+@pytest.mark.parametrize("levels", [3, 256])
+def test_whole_image_ragged_sizes(gm, levels):
+    """A batch in which every pair is at d = inf runs the whole-image kernel (128-candidate chunks, 16 epilogue
+    warps of one 32-column block each, the block-maximum test on targets of 4096 keypoints or more).  Targets of
+    1, 31, 33, 127, 129, 4095, 4096, 4097 and 6000 keypoints (partial 32-column blocks, partial chunks, both sides
+    of the test's threshold) against sources of 1 to 300 queries (partial 128-query groups), with a three-level
+    descriptor alphabet (many equal distances) and a full one; every pair's rows equal the oracle's."""
+    rng = np.random.default_rng(4096 + levels)
+    W, H = 800, 600
+    n_b = [1, 31, 33, 127, 129, 4095, 4096, 4097, 6000]
+    n_a = [1, 127, 129, 300]
+    alphabet = np.array([0, 128, 255], np.uint8) if levels == 3 else np.arange(256, dtype=np.uint8)
+
+    def image(n):
+        xy = np.stack([rng.uniform(0, W, n), rng.uniform(0, H, n)], 1).astype(np.float32)
+        desc = alphabet[rng.integers(0, len(alphabet), (n, 128))]
+        return scenes.Image(W, H, xy, np.ones(n, np.float32), desc, np.full(n, -1, np.int32))
+
+    images = [image(n) for n in n_a] + [image(n) for n in n_b]
+    F = scenes.random_small(3, 4, 4, w=W, h=H).pairs[0].F
+    pairs = [scenes.Pair(a, len(n_a) + b, F, math.inf, 4, 5) for a in range(len(n_a)) for b in range(len(n_b))]
+    sc = scenes.Scene("whole_ragged", images, pairs)
+    rows, st = _gpu_rows(gm, sc)
+    assert st["path_used"] == gm.GM_PATH_TC and st["n_device_errors"] == 0
+    for k, pr in enumerate(pairs):
+        want, nc = _oracle_rows(sc, pr)
+        np.testing.assert_array_equal(rows[k], want, err_msg=f"pair {k}: {images[pr.a].n} x {images[pr.b].n}")
+    assert st["n_candidates"] == sum(images[p.a].n * images[p.b].n for p in pairs)
