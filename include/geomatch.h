@@ -196,9 +196,10 @@ GM_API gm_status gm_image_cache_stats(gm_ctx *ctx, int64_t *images, int64_t *byt
  * (|Points(C_q) & Points(C_i)| > T); only the `top_k` of them with the most co-visible points are kept (ties: the
  * lower image index first), and the result is the set of unique unordered pairs over all queries.
  *   n_cams:     images 0 .. n_cams-1, at most 49152 (each image's co-visible counts are one row of n_cams uint32 in
- *               shared memory; device memory holds only the inputs, their camera -> points transpose and O(n_cams));
+ *               shared memory; device memory holds the inputs, their camera -> points transpose, O(n_cams) and, per
+ *               image q, the images b > q with more than T co-visible points (8 bytes each; T = -1: every pair));
  *   point_off:  int64 [n_points + 1], nondecreasing from 0; point p is seen by point_cams[point_off[p] ..
- *               point_off[p+1]-1] (distinct cameras; GM_ERR_INVALID otherwise);
+ *               point_off[p+1]-1] (distinct cameras in [0, n_cams); GM_ERR_INVALID otherwise);
  *   point_cams: int32 [point_off[n_points]];  both host or both device memory;
  *   pairs:      int32 [cap][3] rows (a, b, count), a < b, sorted by (a, b); host or device;
  *   *n_written: number of rows; if it exceeds cap, nothing is written and the call returns GM_ERR_NOMEM.
