@@ -98,6 +98,7 @@ struct Workspace {
     // plan of the batch being run
     std::vector<PairDev> pd;
     std::vector<int32_t> proc;   // processing order of the pairs (grouped by image B)
+    std::vector<int32_t> sort_tmp, sort_cnt;   // scratch of the counting sorts that build it
     int64_t Q = 0, nitems = 0;
     int32_t n_pairs = 0;
     int32_t launches = 0;
