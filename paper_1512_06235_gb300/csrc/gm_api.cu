@@ -286,10 +286,15 @@ gm_status engine_plan(gm_ctx *ctx, Workspace &ws, int32_t n_pairs, const gm_pair
     ws.n_pairs = n_pairs;
     ws.Q = 0;
     ws.nitems = 0;
+    ws.max_lines = 1;
+    ws.whole_image = n_pairs > 0;
     for (int32_t k = 0; k < n_pairs; ++k) {
         gm_status st = prepare_pair(ctx, pairs[k], k, ws.pd[k], internal);
         if (st != GM_OK) return st;
-        ctx->slots[ws.pd[k].a]->last_use = ctx->slots[ws.pd[k].b]->last_use = ++ctx->use_tick;
+        ImageSlot *sa = ctx->slots[ws.pd[k].a], *sb = ctx->slots[ws.pd[k].b];
+        sa->last_use = sb->last_use = ++ctx->use_tick;
+        ws.max_lines = std::max(ws.max_lines, std::max(sb->dev.gx, sb->dev.gy));
+        ws.whole_image = ws.whole_image && std::isinf(ws.pd[k].d);
         ws.pd[k].qoff = ws.Q;
         ws.Q += ws.pd[k].n_a;
         ws.nitems += (ws.pd[k].n_a + kQueriesPerItem - 1) / kQueriesPerItem;
@@ -319,16 +324,11 @@ gm_status engine_launch(gm_ctx *ctx, Workspace &ws, int32_t *rows_dst)
 
     // distance path and work-item size
     int path = ctx->path == GM_PATH_AUTO ? GM_PATH_TC : ctx->path;
-    int32_t max_lines = 1;   // longest grid line count of the batch's target images
-    for (const PairDev &pd : ws.pd) {
-        const ImageDev &B = ctx->slots[pd.b]->dev;
-        max_lines = std::max(max_lines, std::max(B.gx, B.gy));
-    }
+    const int32_t max_lines = ws.max_lines;   // longest grid line count of the batch's target images (planned)
     // the tcgen05 kernel's run table holds match_tc_max_grid_lines() grid lines
     if (path == GM_PATH_TC && max_lines > match_tc_max_grid_lines()) path = GM_PATH_MMA;
     // every pair with d = inf: the whole-image specialisation of the tcgen05 kernel
-    bool whole_image = P > 0;
-    for (const PairDev &pd : ws.pd) whole_image = whole_image && std::isinf(pd.d);
+    const bool whole_image = ws.whole_image;
     const int mt = ctx->mma_mt;
     const int qpi = path == GM_PATH_SIMT ? kQueriesPerItem : path == GM_PATH_TC ? kTcQueriesPerItem : 16 * mt;
 

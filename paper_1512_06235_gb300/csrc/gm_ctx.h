@@ -101,6 +101,8 @@ struct Workspace {
     std::vector<int32_t> sort_tmp, sort_cnt;   // scratch of the counting sorts that build it
     int64_t Q = 0, nitems = 0;
     int32_t n_pairs = 0;
+    int32_t max_lines = 1;       // longest grid line count of the planned batch's target images
+    bool whole_image = false;    // every pair of the planned batch has d = inf
     int32_t launches = 0;
     int32_t path_used = 0;
     // CUDA graph of the last batch shape (GM_OPT_GRAPH): captured the second time a shape is seen
