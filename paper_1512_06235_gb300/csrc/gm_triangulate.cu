@@ -184,49 +184,117 @@ __global__ void trk_scatter_kernel(const int2 *__restrict__ rows, int64_t n_rows
     }
 }
 
-// Pass 1 (kSolve = false): flag[v] = 1 if node v matched in any pair of its image.  Pass 2 (kSolve = true): for every
-// flagged node, the normal equations of its track -- its own observation, then one per pair of its image (in the
-// caller's order) in which it matched -- solved into the track's slot track_of[v].  Consecutive nodes read
-// consecutive entries of each pair's dense query index.
-template <bool kSolve>
-__global__ void trk_node_kernel(int64_t n_nodes, const TriImage *__restrict__ imgs, int n_images,
-                                const int32_t *__restrict__ img_poff, const int32_t *__restrict__ img_pairs,
-                                const TrkPair *__restrict__ pairs, const int64_t *__restrict__ pbase,
-                                const int32_t *__restrict__ slot, const int2 *__restrict__ rows,
-                                const double *__restrict__ P, int32_t *__restrict__ flag,
-                                const int32_t *__restrict__ track_of, double *__restrict__ X,
-                                int64_t *__restrict__ nodes, int32_t *__restrict__ n_views)
+// Pass 1: per node v, the number of pairs of its image in which it matched, cnt[v], and flag[v] = (cnt[v] > 0).
+// Consecutive nodes read consecutive entries of each pair's dense query index.
+__global__ void trk_count_kernel(int64_t n_nodes, const TriImage *__restrict__ imgs, int n_images,
+                                 const int32_t *__restrict__ img_poff, const int32_t *__restrict__ img_pairs,
+                                 const int64_t *__restrict__ pbase, const int32_t *__restrict__ slot,
+                                 int32_t *__restrict__ flag, int32_t *__restrict__ cnt)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_nodes; v += (int64_t)gridDim.x * blockDim.x) {
         const int k = find_image(imgs, n_images, v);
         const int f = (int)(v - imgs[k].base);
-        if (!kSolve) {
-            int found = 0;
-            for (int t = img_poff[k]; t < img_poff[k + 1] && !found; ++t)
-                found = __ldg(slot + pbase[img_pairs[t]] + f) >= 0;
-            flag[v] = found;
-            continue;
+        int c = 0;
+        for (int t = img_poff[k]; t < img_poff[k + 1]; ++t) c += __ldg(slot + pbase[img_pairs[t]] + f) >= 0;
+        flag[v] = c > 0;
+        cnt[v] = c;
+    }
+}
+
+// Pass 2: the node of every track, nodes[track_of[v]] = v for each flagged node v.
+__global__ void trk_list_kernel(int64_t n_nodes, const int32_t *__restrict__ track_of, int64_t *__restrict__ nodes)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_nodes; v += (int64_t)gridDim.x * blockDim.x)
+        if (track_of[v + 1] != track_of[v]) nodes[track_of[v]] = v;
+}
+
+constexpr int kSolveThreads = 256;
+constexpr int kCntBins = 64;   // match counts from kCntBins - 1 up share the last bin
+
+// Pass 3: the normal equations of every track -- its node's own observation, then one per pair of its image (in
+// the caller's order) in which the node matched -- solved into X[t].  The FP64 pipe bounds this pass (it runs at a
+// small fraction of the FP32 rate on this part), so its work runs in rounds: in each round every lane walks its
+// image's pairs (integer loads only) to its next match, then the warp adds one observation per lane together.  A
+// warp takes as many rounds as its longest track has matches; each block first orders its 256 tracks by match
+// count (a counting sort in shared memory), so a warp's tracks have nearly equal counts.  Which lane takes a track
+// changes nothing in its result: each track adds its observations in its own order, deterministically.
+__global__ void __launch_bounds__(kSolveThreads)
+    trk_solve_kernel(int32_t n_tracks, const int64_t *__restrict__ nodes, const int32_t *__restrict__ cnt,
+                     const TriImage *__restrict__ imgs, int n_images, const int32_t *__restrict__ img_poff,
+                     const int32_t *__restrict__ img_pairs, const TrkPair *__restrict__ pairs,
+                     const int64_t *__restrict__ pbase, const int32_t *__restrict__ slot,
+                     const int2 *__restrict__ rows, const double *__restrict__ P, double *__restrict__ X,
+                     int32_t *__restrict__ n_views)
+{
+    __shared__ int bin_off[kCntBins];
+    __shared__ int64_t s_node[kSolveThreads];
+    __shared__ int32_t s_cnt[kSolveThreads], s_track[kSolveThreads];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < kCntBins) bin_off[tid] = 0;
+    __syncthreads();
+    const int64_t t_in = (int64_t)blockIdx.x * kSolveThreads + tid;
+    int64_t v_in = 0;
+    int c_in = 0;
+    if (t_in < n_tracks) {
+        v_in = nodes[t_in];
+        c_in = cnt[v_in];
+    }
+    const int bin = min(c_in, kCntBins - 1);
+    atomicAdd(&bin_off[bin], 1);
+    __syncthreads();
+    if (tid < 32) {   // exclusive scan of the 64 bins, two per lane
+        const int h0 = bin_off[2 * lane], h1 = bin_off[2 * lane + 1];
+        int x = h0 + h1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        if (track_of[v + 1] == track_of[v]) continue;   // no match: no track
-        double a[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        bin_off[2 * lane] = x - h0 - h1;
+        bin_off[2 * lane + 1] = x - h1;
+    }
+    __syncthreads();
+    const int pos = atomicAdd(&bin_off[bin], 1);
+    s_node[pos] = v_in;
+    s_cnt[pos] = t_in < n_tracks ? c_in : 0;
+    s_track[pos] = t_in < n_tracks ? tid : -1;
+    __syncthreads();
+    const int64_t v = s_node[tid];
+    const int need = s_cnt[tid];
+    const bool live = s_track[tid] >= 0;
+    const int64_t t = (int64_t)blockIdx.x * kSolveThreads + s_track[tid];
+    double a[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int f = 0, pt = 0, pe = 0;
+    if (live) {
+        const int k = find_image(imgs, n_images, v);
         const TriImage &Q = imgs[k];
+        f = (int)(v - Q.base);
         const float2 q = Q.xy[Q.inv_perm[f]];
         tri_add(a, P + 12 * (int64_t)k, (double)q.x, (double)q.y);
-        int nv = 1;
-        for (int t = img_poff[k]; t < img_poff[k + 1]; ++t) {
-            const int p = img_pairs[t];
-            const int32_t m = __ldg(slot + pbase[p] + f);
-            if (m < 0) continue;
+        pt = img_poff[k];
+        pe = img_poff[k + 1];
+    }
+    const int rounds = __reduce_max_sync(0xffffffffu, need);
+    for (int r = 0; r < rounds; ++r) {
+        int32_t m = -1;
+        int p = 0;
+        if (r < need) {
+            while (pt < pe) {
+                p = img_pairs[pt++];
+                m = __ldg(slot + pbase[p] + f);
+                if (m >= 0) break;
+            }
+        }
+        if (m >= 0) {
             const int kb = pairs[p].kb;
             const TriImage &B = imgs[kb];
             const float2 b = B.xy[B.inv_perm[__ldg(&rows[m].y)]];
             tri_add(a, P + 12 * (int64_t)kb, (double)b.x, (double)b.y);
-            ++nv;
         }
-        const int32_t tr = track_of[v];
-        tri_solve(a, X + 3 * (int64_t)tr);
-        nodes[tr] = v;
-        n_views[tr] = nv;
+    }
+    if (live) {
+        tri_solve(a, X + 3 * t);
+        n_views[t] = 1 + need;
     }
 }
 
@@ -417,8 +485,8 @@ gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32
     for (int32_t p = 0; p < n_pairs; ++p) pbase[p + 1] = pbase[p] + imgs[pairs[p].ka].n;
     const size_t pb_b = align_up(sizeof(int64_t) * (n_pairs + 1), 256);
     const size_t sl_b = align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(pbase[n_pairs], 1), 256);
-    gm_status st = ensure_dev(ctx, ctx->d_tri,
-                              img_b + p_b + off_b + pr_b + ip_b + il_b + m_b + fl_b + tr_b + bs_b + 256 + pb_b + sl_b);
+    gm_status st = ensure_dev(ctx, ctx->d_tri, img_b + p_b + off_b + pr_b + ip_b + il_b + m_b + fl_b + tr_b + bs_b +
+                                                   256 + pb_b + sl_b + fl_b);
     if (st != GM_OK) return st;
     char *w = static_cast<char *>(ctx->d_tri.p);
     TriImage *d_imgs = reinterpret_cast<TriImage *>(w);
@@ -447,6 +515,7 @@ gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32
     unsigned long long *bad = reinterpret_cast<unsigned long long *>(w + fl_b + tr_b + bs_b);
     int64_t *d_pbase = reinterpret_cast<int64_t *>(w + fl_b + tr_b + bs_b + 256);
     int32_t *slot = reinterpret_cast<int32_t *>(w + fl_b + tr_b + bs_b + 256 + pb_b);
+    int32_t *cnt = reinterpret_cast<int32_t *>(w + fl_b + tr_b + bs_b + 256 + pb_b + sl_b);
     GM_CUDA_R(cudaMemcpyAsync(d_pbase, pbase.data(), sizeof(int64_t) * (n_pairs + 1), cudaMemcpyHostToDevice, s));
     GM_CUDA_R(cudaMemsetAsync(slot, 0xff, sizeof(int32_t) * (size_t)pbase[n_pairs], s));
     GM_CUDA_R(cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(TriImage) * n_images, cudaMemcpyHostToDevice, s));
@@ -459,18 +528,17 @@ gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32
     GM_CUDA_R(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
     const int grid = std::max(1, ctx->num_sms * 8);
     trk_scatter_kernel<<<grid, 256, 0, s>>>(d_rows, M, d_off, n_pairs, d_pairs, d_imgs, d_pbase, slot, bad);
+    trk_count_kernel<<<grid, 256, 0, s>>>(total, d_imgs, n_images, d_ipoff, d_ipairs, d_pbase, slot, flag, cnt);
+    GM_CUDA_R(launch_exclusive_scan(flag, (int32_t)total, track_of, bsum, s));
+    // one host read for the row check and the track count (the passes above only follow valid rows)
     unsigned long long h_bad = 0;
+    int32_t nt = 0;
     GM_CUDA_R(cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_R(cudaMemcpyAsync(&nt, track_of + total, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     GM_CUDA_R(cudaStreamSynchronize(s));
     if (h_bad)
         return fail(GM_ERR_INVALID,
                     "gm_triangulate_image_tracks: %llu match rows outside their images or not sorted by query", h_bad);
-    trk_node_kernel<false><<<grid, 256, 0, s>>>(total, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_pbase, slot,
-                                                d_rows, d_P, flag, nullptr, nullptr, nullptr, nullptr);
-    GM_CUDA_R(launch_exclusive_scan(flag, (int32_t)total, track_of, bsum, s));
-    int32_t nt = 0;
-    GM_CUDA_R(cudaMemcpyAsync(&nt, track_of + total, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    GM_CUDA_R(cudaStreamSynchronize(s));
     *n_tracks = nt;
     if (nt > cap) return fail(GM_ERR_NOMEM, "gm_triangulate_image_tracks: %d tracks exceed cap %lld", nt, (long long)cap);
     if (nt == 0) return GM_OK;
@@ -485,8 +553,9 @@ gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32
     double *dX = dev_o ? X : reinterpret_cast<double *>(o);
     int64_t *dN = dev_o ? nodes : reinterpret_cast<int64_t *>(o + x_b);
     int32_t *dV = dev_o ? n_views : reinterpret_cast<int32_t *>(o + x_b + r_b);
-    trk_node_kernel<true><<<grid, 256, 0, s>>>(total, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_pbase, slot,
-                                               d_rows, d_P, nullptr, track_of, dX, dN, dV);
+    trk_list_kernel<<<grid, 256, 0, s>>>(total, track_of, dN);
+    trk_solve_kernel<<<(unsigned)((nt + kSolveThreads - 1) / kSolveThreads), kSolveThreads, 0, s>>>(
+        nt, dN, cnt, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_pbase, slot, d_rows, d_P, dX, dV);
     GM_CUDA_R(cudaGetLastError());
     if (!dev_o) {
         GM_CUDA_R(cudaMemcpyAsync(X, dX, sizeof(double) * 3 * nt, cudaMemcpyDeviceToHost, s));
