@@ -11,8 +11,9 @@
 // solves the normal equations (A3^T A3) X = -A3^T a4 (FP64; a singular system gives NaN).
 //   sizes:   component sizes (atomics);
 //   number:  flags of the roots of tracks, scanned into track numbers;
-//   accum:   one thread per node adds its two rows to its track's six distinct entries of A3^T A3 and three of
-//            -A3^T a4 (FP64 atomics; the order of the additions varies from run to run in the last bits);
+//   accum:   every node of a track adds its two rows to its track's six distinct entries of A3^T A3 and three of
+//            -A3^T a4, a warp's track nodes 32 at a time (FP64 atomics; the order of the additions varies from run
+//            to run in the last bits);
 //   solve:   one thread per track, Cramer's rule.
 #include <cuda_runtime.h>
 
@@ -66,42 +67,79 @@ __device__ __forceinline__ int find_image(const TriImage *__restrict__ imgs, int
     return lo;
 }
 
-__global__ void tri_accum_kernel(const int64_t *__restrict__ labels, const int32_t *__restrict__ size,
-                                 const int32_t *__restrict__ track_of, int64_t n_nodes,
-                                 const TriImage *__restrict__ imgs, int n_images, const double *__restrict__ P,
-                                 double *__restrict__ acc, int64_t *__restrict__ roots, int32_t *__restrict__ n_views)
+// One observation (node v of track t = track_of[r], r its root) into its track's sums.
+__device__ __forceinline__ void tri_accum_one(int64_t v, const int64_t *__restrict__ labels,
+                                              const int32_t *__restrict__ size, const int32_t *__restrict__ track_of,
+                                              const TriImage *__restrict__ imgs, int n_images,
+                                              const double *__restrict__ P, double *__restrict__ acc,
+                                              int64_t *__restrict__ roots, int32_t *__restrict__ n_views)
 {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_nodes; v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = labels[v];
-        if (r < 0 || r > v || size[r] < 2) continue;
-        const int32_t t = track_of[r];
-        const int k = find_image(imgs, n_images, v);
-        const TriImage &I = imgs[k];
-        const int f = (int)(v - I.base);
-        const float2 p = I.xy[I.inv_perm[f]];
-        const double x = (double)p.x, y = (double)p.y;
-        const double *Pk = P + 12 * (int64_t)k;
-        double r1[4], r2[4];
+    const int64_t r = labels[v];
+    const int32_t t = track_of[r];
+    const int k = find_image(imgs, n_images, v);
+    const TriImage &I = imgs[k];
+    const int f = (int)(v - I.base);
+    const float2 p = I.xy[I.inv_perm[f]];
+    const double x = (double)p.x, y = (double)p.y;
+    const double *Pk = P + 12 * (int64_t)k;
+    double r1[4], r2[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            r1[c] = x * Pk[8 + c] - Pk[c];
-            r2[c] = y * Pk[8 + c] - Pk[4 + c];
+    for (int c = 0; c < 4; ++c) {
+        r1[c] = x * Pk[8 + c] - Pk[c];
+        r2[c] = y * Pk[8 + c] - Pk[4 + c];
+    }
+    double *a = acc + 9 * (int64_t)t;   // M00 M01 M02 M11 M12 M22, b0 b1 b2
+    atomicAdd(&a[0], r1[0] * r1[0] + r2[0] * r2[0]);
+    atomicAdd(&a[1], r1[0] * r1[1] + r2[0] * r2[1]);
+    atomicAdd(&a[2], r1[0] * r1[2] + r2[0] * r2[2]);
+    atomicAdd(&a[3], r1[1] * r1[1] + r2[1] * r2[1]);
+    atomicAdd(&a[4], r1[1] * r1[2] + r2[1] * r2[2]);
+    atomicAdd(&a[5], r1[2] * r1[2] + r2[2] * r2[2]);
+    atomicAdd(&a[6], -(r1[0] * r1[3] + r2[0] * r2[3]));
+    atomicAdd(&a[7], -(r1[1] * r1[3] + r2[1] * r2[3]));
+    atomicAdd(&a[8], -(r1[2] * r1[3] + r2[2] * r2[3]));
+    if (r == v) {
+        roots[t] = r;
+        n_views[t] = size[r];
+    }
+}
+
+constexpr int kAccumThreads = 256;
+
+// Every node of a track adds its observation.  The FP64 pipe bounds this pass (it runs at a small fraction of the
+// FP32 rate on this part), and many nodes belong to no track, so each warp queues its nodes that do in shared memory
+// and adds them 32 at a time: every FP64 instruction runs on a full warp (the last round of each warp excepted).
+__global__ void __launch_bounds__(kAccumThreads)
+    tri_accum_kernel(const int64_t *__restrict__ labels, const int32_t *__restrict__ size,
+                     const int32_t *__restrict__ track_of, int64_t n_nodes, const TriImage *__restrict__ imgs,
+                     int n_images, const double *__restrict__ P, double *__restrict__ acc,
+                     int64_t *__restrict__ roots, int32_t *__restrict__ n_views)
+{
+    __shared__ int64_t queue[kAccumThreads / 32][64];
+    const int lane = threadIdx.x & 31;
+    int64_t *q = queue[threadIdx.x >> 5];
+    int n = 0;   // queued nodes (the same in every lane)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_nodes; base += stride) {
+        const int64_t v = base + lane;
+        bool obs = false;
+        if (v < n_nodes) {
+            const int64_t r = labels[v];
+            obs = r >= 0 && r <= v && size[r] >= 2;
         }
-        double *a = acc + 9 * (int64_t)t;   // M00 M01 M02 M11 M12 M22, b0 b1 b2
-        atomicAdd(&a[0], r1[0] * r1[0] + r2[0] * r2[0]);
-        atomicAdd(&a[1], r1[0] * r1[1] + r2[0] * r2[1]);
-        atomicAdd(&a[2], r1[0] * r1[2] + r2[0] * r2[2]);
-        atomicAdd(&a[3], r1[1] * r1[1] + r2[1] * r2[1]);
-        atomicAdd(&a[4], r1[1] * r1[2] + r2[1] * r2[2]);
-        atomicAdd(&a[5], r1[2] * r1[2] + r2[2] * r2[2]);
-        atomicAdd(&a[6], -(r1[0] * r1[3] + r2[0] * r2[3]));
-        atomicAdd(&a[7], -(r1[1] * r1[3] + r2[1] * r2[3]));
-        atomicAdd(&a[8], -(r1[2] * r1[3] + r2[2] * r2[3]));
-        if (r == v) {
-            roots[t] = r;
-            n_views[t] = size[r];
+        const uint32_t bal = __ballot_sync(0xffffffffu, obs);
+        if (obs) q[n + __popc(bal & ((1u << lane) - 1u))] = v;
+        n += __popc(bal);
+        __syncwarp();
+        if (n >= 32) {
+            tri_accum_one(q[lane], labels, size, track_of, imgs, n_images, P, acc, roots, n_views);
+            __syncwarp();
+            if (lane < n - 32) q[lane] = q[lane + 32];
+            n -= 32;
+            __syncwarp();
         }
     }
+    if (lane < n) tri_accum_one(q[lane], labels, size, track_of, imgs, n_images, P, acc, roots, n_views);
 }
 
 // Cramer's rule on the normal equations a = (M00 M01 M02 M11 M12 M22, b0 b1 b2); NaN if singular.
@@ -394,7 +432,9 @@ gm_status gm_triangulate(gm_ctx *ctx, int32_t n_images, const int32_t *image_ids
     int64_t *dR = dev_o ? roots : reinterpret_cast<int64_t *>(o + acc_b + x_b);
     int32_t *dV = dev_o ? n_views : reinterpret_cast<int32_t *>(o + acc_b + x_b + r_b);
     GM_CUDA_R(cudaMemsetAsync(acc, 0, sizeof(double) * 9 * nt, s));
-    tri_accum_kernel<<<grid, 256, 0, s>>>(d_lab, size, track_of, n_nodes, d_imgs, n_images, d_P, acc, dR, dV);
+    // four blocks per SM: each warp then sees enough nodes that most of its rounds are full
+    tri_accum_kernel<<<std::max(1, ctx->num_sms * 4), kAccumThreads, 0, s>>>(d_lab, size, track_of, n_nodes, d_imgs,
+                                                                            n_images, d_P, acc, dR, dV);
     tri_solve_kernel<<<std::max(1, std::min(grid, (nt + 255) / 256)), 256, 0, s>>>(acc, nt, dX);
     GM_CUDA_R(cudaGetLastError());
     if (!dev_o) {

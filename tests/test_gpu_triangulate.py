@@ -333,6 +333,45 @@ def test_image_tracks_noise_free(gm):
     assert np.abs(X - Xw[pid]).max() < 2e-3
 
 
+
+def test_image_tracks_many_views(gm):
+    """Tracks of up to 70 views: query image 0 paired with 69 images and image 1 with 29, each true correspondence
+    kept with a per-point probability, so one block of tracks mixes match counts from a few to 69 (past the solve
+    pass's last count bin).  Every track against the oracle, and noise-free recovery."""
+    rng = np.random.default_rng(70)
+    K = scenes.intrinsics(1000.0, 1280, 960)
+    cams = []
+    for k in range(70):
+        th = -1.0 + 2.0 * k / 69
+        c = np.array([15.0 * np.sin(th), 0.5 * np.sin(3 * th), -15.0 * np.cos(th)])
+        cams.append(scenes.camera_at(K, scenes.look_at(c, [0.0, 0.0, 0.0]), c))
+    Xw = rng.uniform(-2.0, 2.0, (60, 3))
+    keep_p = rng.uniform(0.05, 1.0, len(Xw))
+    images = []
+    for cam in cams:
+        uv, z = scenes.project(cam, Xw)
+        assert scenes.inside(uv, 1280, 960).all() and (z > 0).all()
+        images.append(scenes.Image(1280, 960, uv.astype(np.float32), np.ones(len(Xw), np.float32),
+                                   np.zeros((len(Xw), 128), np.uint8), np.arange(len(Xw), dtype=np.int32)))
+    pairs, rows = [], []
+    for a, bs in ((0, range(1, 70)), (1, range(2, 31))):
+        for b in bs:
+            keep = np.nonzero(rng.uniform(size=len(Xw)) < keep_p)[0]
+            rows.append(np.stack([keep, keep], 1).astype(np.int32))
+            pairs.append(scenes.Pair(a, b, np.zeros(9, np.float32)))
+    off = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    m = np.concatenate(rows)
+    Ps = [otri.camera_matrix(c) for c in cams]
+    with gm.Context(device=0) as ctx:
+        ctx.put_images({k: im for k, im in enumerate(images)})
+        X, nodes, nv = ctx.triangulate_image_tracks(list(range(70)), np.array(Ps),
+                                                    np.array([[p.a, p.b] for p in pairs]), off, m)
+    assert nv.max() >= 65 and nv.min() <= 10
+    _check_image_tracks(images, Ps, pairs, off, m, X, nodes, nv)
+    base = np.concatenate([[0], np.cumsum([im.n for im in images])])
+    img = np.searchsorted(base, nodes, side="right") - 1
+    assert np.abs(X - Xw[nodes - base[img]]).max() < 1e-4
+
 def test_image_tracks_errors(gm):
     sc = scenes.facade(n_images=6, n_kp=800, n_points=4000, n_pairs=10, min_covis=20)
     Ps = np.array([otri.camera_matrix(c) for c in sc.cameras]).reshape(-1, 12)
