@@ -594,7 +594,7 @@ gm_status gm_triangulate_image_tracks(gm_ctx *ctx, int32_t n_images, const int32
     int64_t *dN = dev_o ? nodes : reinterpret_cast<int64_t *>(o + x_b);
     int32_t *dV = dev_o ? n_views : reinterpret_cast<int32_t *>(o + x_b + r_b);
     trk_list_kernel<<<grid, 256, 0, s>>>(total, track_of, dN);
-    trk_solve_kernel<<<(unsigned)((nt + kSolveThreads - 1) / kSolveThreads), kSolveThreads, 0, s>>>(
+    trk_solve_kernel<<<(unsigned)(((int64_t)nt + kSolveThreads - 1) / kSolveThreads), kSolveThreads, 0, s>>>(
         nt, dN, cnt, d_imgs, n_images, d_ipoff, d_ipairs, d_pairs, d_pbase, slot, d_rows, d_P, dX, dV);
     GM_CUDA_R(cudaGetLastError());
     if (!dev_o) {
