@@ -881,7 +881,7 @@ def run_triangulate(args, gm, dev, local, peaks, peak_kind):
     n_obs = int(nv[:nt].sum().item())
     n_obs_i = nti + int(m.shape[0])   # per-image: the query's own view plus one per match row
     # FP64 work: 26 FMAs per observation (its two rows, then their products into the nine sums) and 42 FLOPs per
-    # track (Cramer's rule); the FP64 pipe is the bound (2 FMAs per SM per clock on this part)
+    # track (Cramer's rule); the FP64 pipe is the bound (2 FMAs per SM per clock on GB300)
     flop = 52.0 * n_obs + 42.0 * nt
     flop_i = 52.0 * n_obs_i + 42.0 * nti
     fp64_peak = FP64_TFLOPS

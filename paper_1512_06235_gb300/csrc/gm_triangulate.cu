@@ -107,7 +107,7 @@ __device__ __forceinline__ void tri_accum_one(int64_t v, const int64_t *__restri
 constexpr int kAccumThreads = 256;
 
 // Every node of a track adds its observation.  The FP64 pipe bounds this pass (it runs at a small fraction of the
-// FP32 rate on this part), and many nodes belong to no track, so each warp queues its nodes that do in shared memory
+// FP32 rate on GB300), and many nodes belong to no track, so each warp queues its nodes that do in shared memory
 // and adds them 32 at a time: every FP64 instruction runs on a full warp (the last round of each warp excepted).
 __global__ void __launch_bounds__(kAccumThreads)
     tri_accum_kernel(const int64_t *__restrict__ labels, const int32_t *__restrict__ size,
@@ -251,7 +251,7 @@ constexpr int kCntBins = 64;   // match counts from kCntBins - 1 up share the la
 
 // Pass 3: the normal equations of every track -- its node's own observation, then one per pair of its image (in
 // the caller's order) in which the node matched -- solved into X[t].  The FP64 pipe bounds this pass (it runs at a
-// small fraction of the FP32 rate on this part), so its work runs in rounds: in each round every lane walks its
+// small fraction of the FP32 rate on GB300), so its work runs in rounds: in each round every lane walks its
 // image's pairs (integer loads only) to its next match, then the warp adds one observation per lane together.  A
 // warp takes as many rounds as its longest track has matches; each block first orders its 256 tracks by match
 // count (a counting sort in shared memory), so a warp's tracks have nearly equal counts.  Which lane takes a track
